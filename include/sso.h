@@ -1,0 +1,198 @@
+/*
+ * sso.h -- C-ABI of the GB300 structural-FEM hot path (arXiv 2407.20026,
+ * "JAX-SSO: Differentiable Finite Element Analysis Solver for Structural
+ * Optimization").
+ *
+ * What the library computes, with the passage that defines it:
+ *   - element stiffness matrices k_e(x) of 3D beam-columns and MITC-4 quad
+ *     shells from nodal coordinates and section/material data (Sec. 2.2.1;
+ *     the beam's six numbers E, G, Iy, Iz, J, A are those of Listing 1, the
+ *     quad's t, E, nu, kappa_x, kappa_y those of the attribute vector a_quad);
+ *   - their assembly into the global stiffness K of K u = f (Eq. 1), stored as
+ *     6x6-block sparse rows (one block row per node);
+ *   - the supports V u = b with b = 0 (Eqs. 2-3), imposed by eliminating the
+ *     fixed DOFs (identity rows/columns in K, zero load), which gives the same
+ *     u as the Lagrange-multiplier system K_aug u_aug = f_aug;
+ *   - the solve of K u = f by Jacobi / block-Jacobi preconditioned CG, in FP64
+ *     or in FP32 inside FP64 iterative refinement;
+ *   - compliance C = f^T u and the adjoint sensitivity of
+ *     J = w C + g^T u (Eqs. 5-6): K^T lambda = dJ/du,
+ *     dJ/dp = dJ/dp|explicit - lambda^T (dK/dp u - df/dp), for p = the z
+ *     coordinate of every node (NodeParameter(node, 2), Listing 2) and the
+ *     thickness of every quad (Sec. 3.3).
+ *
+ * Conventions shared by every call:
+ *   - DOF order per node is (ux, uy, uz, rx, ry, rz) (Listing 1); vectors of
+ *     DOFs are node-major, length 6 * n_nodes, FP64.
+ *   - Input arrays may live in host memory or in device memory of the current
+ *     CUDA device; the library detects which (cudaPointerGetAttributes) and
+ *     copies what it needs.  Inputs stay owned by the caller and are not
+ *     referenced after the call returns.  Outputs are caller-allocated and may
+ *     also be host or device memory.
+ *   - Every call returns an sso_status and never aborts.  A description of
+ *     the last failure on the calling thread is available from
+ *     sso_last_error().  A handle whose call failed with SSO_ERR_CUDA may hold
+ *     inconsistent device state and should be destroyed.
+ *   - A model or batch runs all its work on the CUDA stream given at creation.
+ *     Calls that return results to the caller synchronise that stream; the
+ *     element-level calls (sso_*_stiffness) only enqueue work.
+ *   - Handles are not thread-safe; use one handle from one thread at a time.
+ */
+#ifndef SSO_H_
+#define SSO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SSO_OK = 0,
+  SSO_ERR_INVALID = 1,       /* bad argument, index out of range, degenerate element */
+  SSO_ERR_OOM = 2,           /* device allocation failed or over the memory budget */
+  SSO_ERR_SINGULAR = 3,      /* CG breakdown: p^T K p <= 0 or non-finite (K not SPD, e.g. a mechanism) */
+  SSO_ERR_NOT_CONVERGED = 4, /* iteration or refinement-sweep cap reached before rtol */
+  SSO_ERR_TIMEOUT = 5,       /* wall-clock cap reached */
+  SSO_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  SSO_ERR_NOT_READY = 7      /* result not available yet (serving poll) */
+} sso_status;
+
+/* A structural model (Listing 1: nodes, elements, supports, loads). */
+typedef struct {
+  int32_t n_nodes;
+  const double* xyz;          /* [n_nodes*3] node coordinates (m) */
+  int32_t n_beams;
+  const int32_t* beam_conn;   /* [n_beams*2] end nodes i, j */
+  const double* beam_props;   /* [n_beams*6] E, G, Iy, Iz, J, A */
+  int32_t n_quads;
+  const int32_t* quad_conn;   /* [n_quads*4] counter-clockwise about the normal */
+  const double* quad_props;   /* [n_quads*5] t, E, nu, kappa_x, kappa_y */
+  const uint8_t* fixed;       /* [n_nodes*6] 1 = DOF fixed (b = 0) */
+  const double* nodal_load;   /* [n_nodes*6] applied nodal forces/moments */
+  double pressure;            /* area load on every quad (Pa), along -Z */
+  double gamma;               /* self-weight density (N/m^3); quad e carries gamma*t_e along -Z */
+} sso_mesh;
+
+typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1 } sso_precision;
+typedef enum { SSO_JACOBI = 0, SSO_BLOCK_JACOBI = 1 } sso_precond;
+
+/* Solver options.  Convergence is ||f - K u||_2 <= rtol ||f||_2 over all DOFs,
+ * with the residual recomputed in FP64 from the FP64 K. */
+typedef struct {
+  int32_t precision;         /* sso_precision */
+  int32_t precond;           /* sso_precond */
+  double rtol;               /* outer relative residual target */
+  double inner_rtol;         /* FP32 inner CG: residual reduction per refinement sweep */
+  int32_t max_iter;          /* cap on CG iterations summed over sweeps */
+  int32_t max_sweeps;        /* cap on refinement sweeps (FP64 residual recomputations) */
+  int32_t iters_per_launch;  /* CG iterations per captured CUDA-graph launch */
+  int32_t warm_start;        /* 1: start from the model's current u instead of 0 */
+  double timeout_ms;         /* wall-clock cap, <= 0 for none */
+} sso_options;
+
+typedef struct {
+  int32_t status;            /* sso_status of this system */
+  int32_t iterations;        /* CG iterations, all sweeps */
+  int32_t sweeps;            /* FP64 residual recomputations */
+  double rel_residual;       /* ||f - K u|| / ||f|| at exit, from the FP64 K */
+  double ms;                 /* wall-clock of the call (same for every system of a batch) */
+} sso_stats;
+
+typedef struct sso_model sso_model;
+typedef struct sso_batch sso_batch;
+
+/* Defaults: FP32_IR, block-Jacobi, rtol 1e-10, inner_rtol 1e-5,
+ * max_iter 200000, max_sweeps 40, iters_per_launch 32, cold start, no timeout. */
+void sso_default_options(sso_options* opts);
+
+/* Message of the last failure on this thread ("" if none).  Valid until the
+ * next failing call on the same thread. */
+const char* sso_last_error(void);
+
+/* Library version string. */
+const char* sso_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Element-level kernels (Sec. 2.2.1, element_K_bc_local / element_K_quad_local).
+ * All pointers are DEVICE pointers; work is enqueued on `stream`
+ * (cudaStream_t, NULL = legacy default stream) and not waited for.
+ *
+ * Output layout: node-pair blocks, ke[e][a][b][r][c] = k_e[6a+r][6b+c] in
+ * global axes, row-major, FP64.  Beams: a, b in {0,1} (144 doubles per
+ * element); quads: a, b in {0..3} (576 doubles per element).
+ */
+sso_status sso_beam_stiffness(int32_t n_beams, const double* d_xyz, const int32_t* d_beam_conn,
+                              const double* d_beam_props, double* d_ke, void* stream);
+sso_status sso_quad_stiffness(int32_t n_quads, const double* d_xyz, const int32_t* d_quad_conn,
+                              const double* d_quad_props, double* d_ke, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Models.  A model owns the device copy of one structure, its block-sparse
+ * pattern (built once on the host from the connectivity: K's block rows are
+ * nodes, a block (i, j) exists when some element joins nodes i and j, and the
+ * list of element blocks summed into every K block is sorted by element so
+ * that assembly is a fixed-order sum, bit-reproducible without atomics), and
+ * the solver state.  Device memory is allocated with cudaMalloc at creation.
+ */
+sso_status sso_model_create(const sso_mesh* mesh, void* stream, sso_model** out);
+void sso_model_destroy(sso_model* model);
+
+/* Replace the design: z [n_nodes] node z coordinates and/or t [n_quads]
+ * thicknesses (either may be NULL to keep the current values). */
+sso_status sso_model_set_design(sso_model* model, const double* z, const double* t);
+
+/* Element matrices -> K (FP64, and its FP32 rounding) -> supports ->
+ * preconditioner -> loads -> CG / iterative refinement.  Results stay on the
+ * device; read them with sso_model_get.  `stats` may be NULL. */
+sso_status sso_model_solve(sso_model* model, const sso_options* opts, sso_stats* stats);
+
+/* Adjoint sensitivity of J = w C + g^T u after a successful solve (Eqs. 5-6).
+ * g is NULL or [6*n_nodes] (host or device).  With g == NULL, lambda = w u and
+ * no second solve is made (K is symmetric); otherwise K lambda = w f + g is
+ * solved with the same options as the last solve.  Fills dJ/dz and dJ/dt. */
+sso_status sso_model_gradient(sso_model* model, double w, const double* g, sso_stats* stats);
+
+/* Copy results out; any pointer may be NULL.  u [6*n_nodes], C [1],
+ * dz [n_nodes], dt [n_quads], lam [6*n_nodes] (adjoint vector). */
+sso_status sso_model_get(sso_model* model, double* u, double* C, double* dz, double* dt,
+                         double* lam);
+
+/* Sizes of the model: n_blocks of K and the number of element blocks. */
+sso_status sso_model_info(const sso_model* model, int32_t* n_nodes, int32_t* n_blocks,
+                          int32_t* n_elem_blocks);
+
+/* Copy the assembled K (after a solve), supports applied: row_ptr
+ * [n_nodes+1], col [n_blocks], K64 [n_blocks*36] and K32 [n_blocks*36],
+ * blocks row-major.  Any pointer may be NULL. */
+sso_status sso_model_get_stiffness(sso_model* model, int32_t* row_ptr, int32_t* col,
+                                   double* K64, float* K32);
+
+/* The full load vector f [6*n_nodes] (nodal + consistent area loads, zero on
+ * fixed DOFs) after a solve. */
+sso_status sso_model_get_load(sso_model* model, double* f);
+
+/* ---------------------------------------------------------------------------
+ * Batches: several models (any mix of sizes and topologies, all on the same
+ * device) solved together.  Every CG iteration is one pass of two kernels over
+ * all systems that are still iterating; each system keeps its own scalars,
+ * refinement state and convergence test, and its reductions follow a fixed
+ * tiling of its own rows, so its result does not depend on which other systems
+ * share the batch.  The batch runs on the stream of models[0].
+ */
+sso_status sso_batch_create(sso_model* const* models, int32_t n_models, sso_batch** out);
+void sso_batch_destroy(sso_batch* batch);
+/* Solve every model; stats is NULL or [n_models].  Returns the first
+ * non-OK per-system status (if any) after all systems finished. */
+sso_status sso_batch_solve(sso_batch* batch, const sso_options* opts, sso_stats* stats);
+/* Gradients of J_i = w[i] C_i + g[i]^T u_i for every model.  w NULL means
+ * all 1; g NULL, or g[i] NULL, means no g term for that system. */
+sso_status sso_batch_gradient(sso_batch* batch, const double* w, const double* const* g,
+                              sso_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSO_H_ */
