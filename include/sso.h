@@ -114,6 +114,10 @@ const char* sso_last_error(void);
 /* Library version string. */
 const char* sso_version(void);
 
+/* Number of CUDA kernel launches this library has issued in this process
+ * (graph launches count every kernel node they run).  For accounting only. */
+unsigned long long sso_kernel_launches(void);
+
 /* ---------------------------------------------------------------------------
  * Element-level kernels (Sec. 2.2.1, element_K_bc_local / element_K_quad_local).
  * All pointers are DEVICE pointers; work is enqueued on `stream`

@@ -1,0 +1,996 @@
+// C-ABI of libsso (include/sso.h): models, batches, the host-side scatter-map
+// builder and the batched CG driver.
+//
+// Streams: every model owns an internal non-blocking stream.  Each call first
+// makes that stream wait for the caller's stream (event), does its work there
+// and, before returning, makes the caller's stream wait for it.  The internal
+// stream is what CUDA-graph capture needs (the legacy default stream cannot be
+// captured).
+//
+// Memory: one cudaMalloc arena per model, carved into the arrays listed in
+// ModelLayout; one per batch for its tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sso_internal.cuh"
+
+using namespace sso;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+
+sso_status fail(sso_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+sso_status cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(SSO_ERR_OOM, buf);
+  }
+  return fail(SSO_ERR_CUDA, buf);
+}
+
+#define CK(expr)                                         \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);  \
+  } while (0)
+
+#define CL(expr, n)                                      \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);  \
+    g_launches += (n);                                   \
+  } while (0)
+
+// True when p is device (or managed) memory.  A pointer CUDA does not know,
+// or a machine without a usable device, means host memory.
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy from a host or device source into host memory.
+cudaError_t to_host(void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return cudaSuccess;
+  if (!is_device_ptr(src)) {
+    std::memcpy(dst, src, bytes);
+    return cudaSuccess;
+  }
+  return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves typed arrays out of one allocation (256-byte aligned).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+struct HostMesh {
+  int n_nodes = 0, n_beams = 0, n_quads = 0;
+  std::vector<double> xyz, beam_props, quad_props, nodal_load;
+  std::vector<int> beam_conn, quad_conn;
+  std::vector<uint8_t> fixed;
+  double pressure = 0.0, gamma = 0.0;
+};
+
+struct HostTopo {
+  std::vector<int> row_ptr, col, brow, diag, cptr, csrc, nptr, nsrc;
+};
+
+}  // namespace
+
+struct sso_model {
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int n_nodes = 0, n_beams = 0, n_quads = 0, n_blocks = 0, n_eb = 0, n_slots = 0, n_tiles = 0;
+  double pressure = 0.0, gamma = 0.0;
+  std::vector<int> h_row_ptr, h_col;
+  void* arena = nullptr;
+  // topology
+  int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_brow, *d_diag, *d_cptr, *d_csrc,
+      *d_nptr, *d_nsrc;
+  uint8_t* d_fixed;
+  // design
+  double *d_xyz, *d_beam_props, *d_quad_props, *d_nodal_load;
+  // element and global arrays
+  double *d_ke, *d_fslot, *d_gslot, *d_K64, *d_M64, *d_f, *d_u, *d_lam, *d_rhs, *d_r64;
+  float *d_K32, *d_M32;
+  void *d_r, *d_z, *d_p0, *d_p1, *d_q;
+  double *d_part_a, *d_part_b, *d_dz, *d_dt, *d_C;
+  int* d_err;
+  bool assembled = false, solved = false;
+  int assembled_precond = -1;
+  sso_options last_opts;
+  sso_batch* self_batch = nullptr;
+};
+
+struct sso_batch {
+  std::vector<sso_model*> models;
+  cudaStream_t stream = nullptr;  // models[0]'s internal stream
+  int n_sys = 0, n_tiles = 0;
+  void* arena = nullptr;
+  SysDesc* d_sys = nullptr;
+  SysScalars* d_sc = nullptr;
+  int2* d_tiles = nullptr;
+  int* d_n_tiles = nullptr;
+  int* d_n_active = nullptr;
+  double* d_dots = nullptr;
+  std::vector<SysDesc> h_sys;
+  SysScalars* h_sc = nullptr;   // pinned, n_sys
+  int* h_flag = nullptr;        // pinned, 2 ints
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int exec_iters[2] = {0, 0};
+  int grid[2] = {0, 0};
+  cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Validation and the scatter map (Sec. 2.2.1 element_K_*_indices, as a sorted
+// gather list).
+sso_status validate(const HostMesh& m) {
+  const int n = m.n_nodes;
+  for (size_t k = 0; k < m.xyz.size(); ++k)
+    if (!std::isfinite(m.xyz[k])) return fail(SSO_ERR_INVALID, "non-finite node coordinate");
+  for (size_t k = 0; k < m.nodal_load.size(); ++k)
+    if (!std::isfinite(m.nodal_load[k])) return fail(SSO_ERR_INVALID, "non-finite nodal load");
+  if (!std::isfinite(m.pressure) || !std::isfinite(m.gamma))
+    return fail(SSO_ERR_INVALID, "non-finite area load");
+  char buf[200];
+  for (int e = 0; e < m.n_beams; ++e) {
+    const int i = m.beam_conn[2 * e], j = m.beam_conn[2 * e + 1];
+    if (i < 0 || i >= n || j < 0 || j >= n) {
+      snprintf(buf, sizeof(buf), "beam %d: node index out of range", e);
+      return fail(SSO_ERR_INVALID, buf);
+    }
+    double L2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double d = m.xyz[3 * j + k] - m.xyz[3 * i + k];
+      L2 += d * d;
+    }
+    if (i == j || !(L2 > 0.0)) {
+      snprintf(buf, sizeof(buf), "beam %d: zero length", e);
+      return fail(SSO_ERR_INVALID, buf);
+    }
+    for (int k = 0; k < 6; ++k)
+      if (!(m.beam_props[6 * e + k] > 0.0) || !std::isfinite(m.beam_props[6 * e + k])) {
+        snprintf(buf, sizeof(buf), "beam %d: section/material value %d must be > 0", e, k);
+        return fail(SSO_ERR_INVALID, buf);
+      }
+  }
+  for (int e = 0; e < m.n_quads; ++e) {
+    int nd[4];
+    for (int a = 0; a < 4; ++a) {
+      nd[a] = m.quad_conn[4 * e + a];
+      if (nd[a] < 0 || nd[a] >= n) {
+        snprintf(buf, sizeof(buf), "quad %d: node index out of range", e);
+        return fail(SSO_ERR_INVALID, buf);
+      }
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (nd[a] == nd[b]) {
+          snprintf(buf, sizeof(buf), "quad %d: repeated node", e);
+          return fail(SSO_ERR_INVALID, buf);
+        }
+    const double* p = &m.quad_props[5 * e];
+    if (!(p[0] > 0.0) || !(p[1] > 0.0) || !(p[2] > -1.0 && p[2] < 0.5) || !(p[3] > 0.0) ||
+        !(p[4] > 0.0)) {
+      snprintf(buf, sizeof(buf), "quad %d: need t > 0, E > 0, -1 < nu < 0.5, kappa > 0", e);
+      return fail(SSO_ERR_INVALID, buf);
+    }
+    // convex, consistently oriented about the diagonal normal
+    double X[4][3];
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) X[a][k] = m.xyz[3 * nd[a] + k];
+    double d13[3], d24[3], nrm[3];
+    for (int k = 0; k < 3; ++k) {
+      d13[k] = X[2][k] - X[0][k];
+      d24[k] = X[3][k] - X[1][k];
+    }
+    nrm[0] = d13[1] * d24[2] - d13[2] * d24[1];
+    nrm[1] = d13[2] * d24[0] - d13[0] * d24[2];
+    nrm[2] = d13[0] * d24[1] - d13[1] * d24[0];
+    for (int a = 0; a < 4; ++a) {
+      const double* P0 = X[a];
+      const double* P1 = X[(a + 1) % 4];
+      const double* P2 = X[(a + 2) % 4];
+      double u[3], v[3];
+      for (int k = 0; k < 3; ++k) {
+        u[k] = P1[k] - P0[k];
+        v[k] = P2[k] - P1[k];
+      }
+      const double c = (u[1] * v[2] - u[2] * v[1]) * nrm[0] + (u[2] * v[0] - u[0] * v[2]) * nrm[1] +
+                       (u[0] * v[1] - u[1] * v[0]) * nrm[2];
+      if (!(c > 0.0)) {
+        snprintf(buf, sizeof(buf), "quad %d: not convex or degenerate", e);
+        return fail(SSO_ERR_INVALID, buf);
+      }
+    }
+  }
+  return SSO_OK;
+}
+
+// Element-block eb -> (row node, col node).
+void build_topology(const HostMesh& m, HostTopo& T) {
+  const int n = m.n_nodes;
+  std::vector<std::vector<int>> adj(n);
+  for (int i = 0; i < n; ++i) adj[i].push_back(i);
+  for (int e = 0; e < m.n_beams; ++e)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) adj[m.beam_conn[2 * e + a]].push_back(m.beam_conn[2 * e + b]);
+  for (int e = 0; e < m.n_quads; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) adj[m.quad_conn[4 * e + a]].push_back(m.quad_conn[4 * e + b]);
+  T.row_ptr.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    std::sort(adj[i].begin(), adj[i].end());
+    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+    T.row_ptr[i + 1] = T.row_ptr[i] + (int)adj[i].size();
+  }
+  const int nb = T.row_ptr[n];
+  T.col.resize(nb);
+  T.brow.resize(nb);
+  T.diag.resize(n);
+  for (int i = 0; i < n; ++i) {
+    std::copy(adj[i].begin(), adj[i].end(), T.col.begin() + T.row_ptr[i]);
+    for (int k = T.row_ptr[i]; k < T.row_ptr[i + 1]; ++k) {
+      T.brow[k] = i;
+      if (T.col[k] == i) T.diag[i] = k;
+    }
+  }
+  auto block_of = [&](int i, int j) {
+    const int* b = T.col.data() + T.row_ptr[i];
+    const int* e = T.col.data() + T.row_ptr[i + 1];
+    return (int)(std::lower_bound(b, e, j) - T.col.data());
+  };
+  const int n_eb = 4 * m.n_beams + 16 * m.n_quads;
+  std::vector<int> target(n_eb);
+  for (int e = 0; e < m.n_beams; ++e)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        target[4 * e + 2 * a + b] = block_of(m.beam_conn[2 * e + a], m.beam_conn[2 * e + b]);
+  const int q0 = 4 * m.n_beams;
+  for (int e = 0; e < m.n_quads; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        target[q0 + 16 * e + 4 * a + b] = block_of(m.quad_conn[4 * e + a], m.quad_conn[4 * e + b]);
+  // counting sort by target block, stable in element-block order
+  T.cptr.assign(nb + 1, 0);
+  for (int k = 0; k < n_eb; ++k) T.cptr[target[k] + 1]++;
+  for (int b = 0; b < nb; ++b) T.cptr[b + 1] += T.cptr[b];
+  T.csrc.resize(n_eb);
+  {
+    std::vector<int> fill(T.cptr.begin(), T.cptr.end() - 1);
+    for (int k = 0; k < n_eb; ++k) T.csrc[fill[target[k]]++] = k;
+  }
+  // node incidence: slots 2e+a (beams), 2 n_beams + 4e + a (quads), by node, stable
+  const int n_slots = 2 * m.n_beams + 4 * m.n_quads;
+  std::vector<int> slot_node(n_slots);
+  for (int e = 0; e < m.n_beams; ++e)
+    for (int a = 0; a < 2; ++a) slot_node[2 * e + a] = m.beam_conn[2 * e + a];
+  for (int e = 0; e < m.n_quads; ++e)
+    for (int a = 0; a < 4; ++a) slot_node[2 * m.n_beams + 4 * e + a] = m.quad_conn[4 * e + a];
+  T.nptr.assign(n + 1, 0);
+  for (int s = 0; s < n_slots; ++s) T.nptr[slot_node[s] + 1]++;
+  for (int i = 0; i < n; ++i) T.nptr[i + 1] += T.nptr[i];
+  T.nsrc.resize(n_slots);
+  {
+    std::vector<int> fill(T.nptr.begin(), T.nptr.end() - 1);
+    for (int s = 0; s < n_slots; ++s) T.nsrc[fill[slot_node[s]]++] = s;
+  }
+}
+
+// Lays out (base == nullptr: sizes only) every device array of a model.
+size_t layout_model(sso_model* M, void* base) {
+  Carver c(base);
+  const size_t n = M->n_nodes, ndof = 6 * n;
+  M->d_beam_conn = c.take<int>(2 * (size_t)M->n_beams);
+  M->d_quad_conn = c.take<int>(4 * (size_t)M->n_quads);
+  M->d_row_ptr = c.take<int>(n + 1);
+  M->d_col = c.take<int>(M->n_blocks);
+  M->d_brow = c.take<int>(M->n_blocks);
+  M->d_diag = c.take<int>(n);
+  M->d_cptr = c.take<int>((size_t)M->n_blocks + 1);
+  M->d_csrc = c.take<int>(M->n_eb);
+  M->d_nptr = c.take<int>(n + 1);
+  M->d_nsrc = c.take<int>(M->n_slots);
+  M->d_fixed = c.take<uint8_t>(ndof);
+  M->d_xyz = c.take<double>(3 * n);
+  M->d_beam_props = c.take<double>(6 * (size_t)M->n_beams);
+  M->d_quad_props = c.take<double>(5 * (size_t)M->n_quads);
+  M->d_nodal_load = c.take<double>(ndof);
+  M->d_ke = c.take<double>((size_t)M->n_eb * 36);
+  M->d_fslot = c.take<double>(M->n_slots);
+  M->d_gslot = c.take<double>(M->n_slots);
+  M->d_K64 = c.take<double>((size_t)M->n_blocks * 36);
+  M->d_K32 = c.take<float>((size_t)M->n_blocks * 36);
+  M->d_M64 = c.take<double>(36 * n);
+  M->d_M32 = c.take<float>(36 * n);
+  M->d_f = c.take<double>(ndof);
+  M->d_u = c.take<double>(ndof);
+  M->d_lam = c.take<double>(ndof);
+  M->d_rhs = c.take<double>(ndof);
+  M->d_r64 = c.take<double>(ndof);
+  M->d_r = c.take<double>(ndof);
+  M->d_z = c.take<double>(ndof);
+  M->d_p0 = c.take<double>(ndof);
+  M->d_p1 = c.take<double>(ndof);
+  M->d_q = c.take<double>(ndof);
+  M->d_part_a = c.take<double>(2 * (size_t)M->n_tiles);
+  M->d_part_b = c.take<double>(2 * (size_t)M->n_tiles);
+  M->d_dz = c.take<double>(n);
+  M->d_dt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
+  M->d_C = c.take<double>(1);
+  M->d_err = c.take<int>(1);
+  return align_up(c.off, 256);
+}
+
+sso_status check_options(const sso_options* o) {
+  if (!o) return fail(SSO_ERR_INVALID, "options is NULL");
+  if (o->precision != SSO_FP64 && o->precision != SSO_FP32_IR)
+    return fail(SSO_ERR_INVALID, "precision must be SSO_FP64 or SSO_FP32_IR");
+  if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI)
+    return fail(SSO_ERR_INVALID, "precond must be SSO_JACOBI or SSO_BLOCK_JACOBI");
+  if (!(o->rtol > 0.0) || !(o->inner_rtol >= 0.0) || o->inner_rtol >= 1.0)
+    return fail(SSO_ERR_INVALID, "need rtol > 0 and 0 <= inner_rtol < 1");
+  if (o->max_iter <= 0 || o->max_sweeps <= 0)
+    return fail(SSO_ERR_INVALID, "max_iter and max_sweeps must be > 0");
+  if (o->iters_per_launch <= 0 || o->iters_per_launch > 4096)
+    return fail(SSO_ERR_INVALID, "iters_per_launch must be in [1, 4096]");
+  return SSO_OK;
+}
+
+// Work on the model's internal stream ordered after the caller's stream.
+sso_status enter(sso_model* M) {
+  CK(cudaSetDevice(M->device));
+  CK(cudaEventRecord(M->ev_in, M->user_stream));
+  CK(cudaStreamWaitEvent(M->stream, M->ev_in, 0));
+  return SSO_OK;
+}
+sso_status leave(sso_model* M) {
+  CK(cudaEventRecord(M->ev_out, M->stream));
+  CK(cudaStreamWaitEvent(M->user_stream, M->ev_out, 0));
+  return SSO_OK;
+}
+
+// Element matrices, K, preconditioner and loads of one model.
+sso_status setup_model(sso_model* M, int precond, cudaStream_t s) {
+  CL(launch_beam_stiffness(M->n_beams, M->d_xyz, M->d_beam_conn, M->d_beam_props, M->d_ke, s),
+     M->n_beams > 0);
+  CL(launch_quad_stiffness(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props, M->pressure,
+                           M->gamma, M->d_ke + (size_t)4 * M->n_beams * 36,
+                           M->d_fslot + 2 * (size_t)M->n_beams, s),
+     M->n_quads > 0);
+  CL(launch_assemble(M->n_blocks, M->d_cptr, M->d_csrc, M->d_ke, M->d_brow, M->d_col,
+                     M->d_fixed, M->d_K64, M->d_K32, s),
+     1);
+  CK(cudaMemsetAsync(M->d_err, 0, sizeof(int), s));
+  CL(launch_precond(M->n_nodes, precond, M->d_diag, M->d_K64, M->d_M64, M->d_M32, M->d_err, s),
+     1);
+  CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, M->d_fslot, nullptr,
+                        M->d_nodal_load, M->d_fixed, M->d_f, nullptr, s),
+     1);
+  M->assembled = true;
+  M->assembled_precond = precond;
+  return SSO_OK;
+}
+
+sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
+  const int k = fp64 ? 1 : 0;
+  if (B->exec[k] && B->exec_iters[k] == iters) return SSO_OK;
+  if (B->exec[k]) {
+    cudaGraphExecDestroy(B->exec[k]);
+    B->exec[k] = nullptr;
+  }
+  if (B->grid[k] == 0) {
+    const int lim = pcg_grid_limit(fp64);
+    B->grid[k] = std::max(1, std::min(B->n_tiles, lim));
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int it = 0; it < iters && err == cudaSuccess; ++it) {
+    err = launch_pcg_a(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid[k],
+                       B->stream);
+    if (err == cudaSuccess)
+      err = launch_pcg_b(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid[k],
+                         B->stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
+  if (err != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(err, "capturing the CG graph");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  err = cudaGraphInstantiate(&B->exec[k], g, 0);
+  cudaGraphDestroy(g);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGraphInstantiate");
+  B->exec_iters[k] = iters;
+  return SSO_OK;
+}
+
+// Runs the batched CG over the systems with active[s] != 0, solving
+// K x = b with b = (adjoint ? rhs : f), x = (adjoint ? lam : u).
+sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
+                     const std::vector<char>& active, sso_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const bool fp64 = o->precision == SSO_FP64;
+  const double inner = fp64 ? 0.0 : o->inner_rtol;
+  int n_act = 0;
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    SysDesc& D = B->h_sys[s];
+    D.precond = o->precond;
+    D.b = adjoint ? M->d_rhs : M->d_f;
+    D.x = adjoint ? M->d_lam : M->d_u;
+    SysScalars& S = B->h_sc[s];
+    std::memset(&S, 0, sizeof(S));
+    const bool warm = !adjoint && o->warm_start && M->solved;
+    S.state = active[s] ? (warm ? ST_RESID : ST_INIT) : ST_DONE;
+    S.status = active[s] ? SSO_ERR_NOT_CONVERGED : SSO_OK;
+    S.rtol2 = o->rtol * o->rtol;
+    S.inner_rtol2 = inner * inner;
+    S.max_iter = o->max_iter;
+    S.max_sweeps = o->max_sweeps;
+    if (active[s]) {
+      ++n_act;
+      if (!warm) CK(cudaMemsetAsync(D.x, 0, sizeof(double) * 6 * (size_t)M->n_nodes, B->stream));
+    }
+  }
+  CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * B->n_sys,
+                     cudaMemcpyHostToDevice, B->stream));
+  CK(cudaMemcpyAsync(B->d_sc, B->h_sc, sizeof(SysScalars) * B->n_sys, cudaMemcpyHostToDevice,
+                     B->stream));
+  B->h_flag[0] = n_act;
+  CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  if (n_act > 0) {
+    sso_status st = batch_graph(B, fp64, o->iters_per_launch);
+    if (st != SSO_OK) return st;
+    const int k = fp64 ? 1 : 0;
+    const long long max_launches = (long long)o->max_iter * 2 / o->iters_per_launch + 4LL * o->max_sweeps + 8;
+    long long launches = 0;
+    for (;;) {
+      CK(cudaGraphLaunch(B->exec[k], B->stream));
+      g_launches += 2ull * (unsigned long long)o->iters_per_launch;
+      CK(cudaMemcpyAsync(B->h_flag + 1, B->d_n_active, sizeof(int), cudaMemcpyDeviceToHost,
+                         B->stream));
+      CK(cudaEventRecord(B->ev, B->stream));
+      CK(cudaEventSynchronize(B->ev));
+      ++launches;
+      if (B->h_flag[1] <= 0) break;
+      if (o->timeout_ms > 0.0) {
+        const double ms = std::chrono::duration<double, std::milli>(
+                              std::chrono::steady_clock::now() - t0).count();
+        if (ms > o->timeout_ms) break;
+      }
+      if (launches > max_launches) break;  // caps are enforced on the device; belt and braces
+    }
+  }
+  CK(cudaMemcpyAsync(B->h_sc, B->d_sc, sizeof(SysScalars) * B->n_sys, cudaMemcpyDeviceToHost,
+                     B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  sso_status first_bad = SSO_OK;
+  for (int s = 0; s < B->n_sys; ++s) {
+    const SysScalars& S = B->h_sc[s];
+    int st = S.state == ST_DONE ? S.status : SSO_ERR_TIMEOUT;
+    if (!active[s]) st = SSO_OK;
+    if (st != SSO_OK && first_bad == SSO_OK) first_bad = (sso_status)st;
+    if (stats && active[s]) {
+      stats[s].status = st;
+      stats[s].iterations = S.iters;
+      stats[s].sweeps = S.sweeps;
+      stats[s].rel_residual = S.ff > 0.0 ? std::sqrt(S.rr64 / S.ff) : 0.0;
+      stats[s].ms = ms;
+    }
+  }
+  if (first_bad != SSO_OK) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "CG finished with status %d in at least one system",
+             (int)first_bad);
+    g_last_error = buf;
+  }
+  return first_bad;
+}
+
+sso_status ensure_self_batch(sso_model* M) {
+  if (M->self_batch) return SSO_OK;
+  sso_model* ms[1] = {M};
+  return sso_batch_create(ms, 1, &M->self_batch);
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void sso_default_options(sso_options* o) {
+  if (!o) return;
+  o->precision = SSO_FP32_IR;
+  o->precond = SSO_BLOCK_JACOBI;
+  o->rtol = 1e-10;
+  o->inner_rtol = 1e-5;
+  o->max_iter = 200000;
+  o->max_sweeps = 40;
+  o->iters_per_launch = 32;
+  o->warm_start = 0;
+  o->timeout_ms = 0.0;
+}
+
+const char* sso_last_error(void) { return g_last_error.c_str(); }
+
+const char* sso_version(void) { return "sso 0.1 (sm_103a)"; }
+
+unsigned long long sso_kernel_launches(void) { return g_launches.load(); }
+
+sso_status sso_beam_stiffness(int32_t n_beams, const double* d_xyz, const int32_t* d_beam_conn,
+                              const double* d_beam_props, double* d_ke, void* stream) {
+  if (n_beams < 0) return fail(SSO_ERR_INVALID, "n_beams < 0");
+  if (n_beams > 0 && (!d_xyz || !d_beam_conn || !d_beam_props || !d_ke))
+    return fail(SSO_ERR_INVALID, "NULL pointer");
+  CL(launch_beam_stiffness(n_beams, d_xyz, d_beam_conn, d_beam_props, d_ke,
+                           (cudaStream_t)stream),
+     n_beams > 0);
+  return SSO_OK;
+}
+
+sso_status sso_quad_stiffness(int32_t n_quads, const double* d_xyz, const int32_t* d_quad_conn,
+                              const double* d_quad_props, double* d_ke, void* stream) {
+  if (n_quads < 0) return fail(SSO_ERR_INVALID, "n_quads < 0");
+  if (n_quads > 0 && (!d_xyz || !d_quad_conn || !d_quad_props || !d_ke))
+    return fail(SSO_ERR_INVALID, "NULL pointer");
+  CL(launch_quad_stiffness(n_quads, d_xyz, d_quad_conn, d_quad_props, 0.0, 0.0, d_ke, nullptr,
+                           (cudaStream_t)stream),
+     n_quads > 0);
+  return SSO_OK;
+}
+
+sso_status sso_model_create(const sso_mesh* mesh, void* stream, sso_model** out) {
+  if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(SSO_ERR_INVALID, "mesh is NULL");
+  if (mesh->n_nodes <= 0 || mesh->n_beams < 0 || mesh->n_quads < 0)
+    return fail(SSO_ERR_INVALID, "need n_nodes > 0, n_beams >= 0, n_quads >= 0");
+  if (mesh->n_beams + mesh->n_quads == 0) return fail(SSO_ERR_INVALID, "no elements");
+  if (!mesh->xyz || !mesh->fixed || !mesh->nodal_load)
+    return fail(SSO_ERR_INVALID, "xyz, fixed and nodal_load are required");
+  if (mesh->n_beams > 0 && (!mesh->beam_conn || !mesh->beam_props))
+    return fail(SSO_ERR_INVALID, "beam arrays missing");
+  if (mesh->n_quads > 0 && (!mesh->quad_conn || !mesh->quad_props))
+    return fail(SSO_ERR_INVALID, "quad arrays missing");
+  const long long eb = 4LL * mesh->n_beams + 16LL * mesh->n_quads;
+  if (eb >= (1LL << 31) || 6LL * mesh->n_nodes >= (1LL << 31))
+    return fail(SSO_ERR_INVALID, "mesh too large for 32-bit block indices");
+
+  HostMesh hm;
+  hm.n_nodes = mesh->n_nodes;
+  hm.n_beams = mesh->n_beams;
+  hm.n_quads = mesh->n_quads;
+  hm.pressure = mesh->pressure;
+  hm.gamma = mesh->gamma;
+  hm.xyz.resize(3 * (size_t)hm.n_nodes);
+  hm.nodal_load.resize(6 * (size_t)hm.n_nodes);
+  hm.fixed.resize(6 * (size_t)hm.n_nodes);
+  hm.beam_conn.resize(2 * (size_t)hm.n_beams);
+  hm.beam_props.resize(6 * (size_t)hm.n_beams);
+  hm.quad_conn.resize(4 * (size_t)hm.n_quads);
+  hm.quad_props.resize(5 * (size_t)hm.n_quads);
+  CK(to_host(hm.xyz.data(), mesh->xyz, hm.xyz.size() * sizeof(double)));
+  CK(to_host(hm.nodal_load.data(), mesh->nodal_load, hm.nodal_load.size() * sizeof(double)));
+  CK(to_host(hm.fixed.data(), mesh->fixed, hm.fixed.size()));
+  CK(to_host(hm.beam_conn.data(), mesh->beam_conn, hm.beam_conn.size() * sizeof(int)));
+  CK(to_host(hm.beam_props.data(), mesh->beam_props, hm.beam_props.size() * sizeof(double)));
+  CK(to_host(hm.quad_conn.data(), mesh->quad_conn, hm.quad_conn.size() * sizeof(int)));
+  CK(to_host(hm.quad_props.data(), mesh->quad_props, hm.quad_props.size() * sizeof(double)));
+  for (auto& f : hm.fixed) f = f ? 1 : 0;
+  sso_status st = validate(hm);
+  if (st != SSO_OK) return st;
+
+  HostTopo T;
+  build_topology(hm, T);
+
+  sso_model* M = new sso_model();
+  CK(cudaGetDevice(&M->device));
+  M->user_stream = (cudaStream_t)stream;
+  M->n_nodes = hm.n_nodes;
+  M->n_beams = hm.n_beams;
+  M->n_quads = hm.n_quads;
+  M->n_blocks = (int)T.col.size();
+  M->n_eb = (int)T.csrc.size();
+  M->n_slots = (int)T.nsrc.size();
+  M->n_tiles = (hm.n_nodes + TILE - 1) / TILE;
+  M->pressure = hm.pressure;
+  M->gamma = hm.gamma;
+  M->h_row_ptr = T.row_ptr;
+  M->h_col = T.col;
+  sso_default_options(&M->last_opts);
+  auto cleanup = [&](sso_status s) {
+    sso_model_destroy(M);
+    return s;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "stream/event creation"));
+  const size_t bytes = layout_model(M, nullptr);
+  e = cudaMalloc(&M->arena, bytes);
+  if (e != cudaSuccess) {
+    M->arena = nullptr;
+    return cleanup(cuda_fail(e, "cudaMalloc(model arena)"));
+  }
+  layout_model(M, M->arena);
+  cudaStream_t s = M->stream;
+  auto up = [&](void* dst, const void* src, size_t b) {
+    return b ? cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  e = cudaMemsetAsync(M->arena, 0, bytes, s);
+  if (e == cudaSuccess) e = up(M->d_beam_conn, hm.beam_conn.data(), hm.beam_conn.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_quad_conn, hm.quad_conn.data(), hm.quad_conn.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_row_ptr, T.row_ptr.data(), T.row_ptr.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_col, T.col.data(), T.col.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_brow, T.brow.data(), T.brow.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_diag, T.diag.data(), T.diag.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_cptr, T.cptr.data(), T.cptr.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_csrc, T.csrc.data(), T.csrc.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_nptr, T.nptr.data(), T.nptr.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_nsrc, T.nsrc.data(), T.nsrc.size() * 4);
+  if (e == cudaSuccess) e = up(M->d_fixed, hm.fixed.data(), hm.fixed.size());
+  if (e == cudaSuccess) e = up(M->d_xyz, hm.xyz.data(), hm.xyz.size() * 8);
+  if (e == cudaSuccess) e = up(M->d_beam_props, hm.beam_props.data(), hm.beam_props.size() * 8);
+  if (e == cudaSuccess) e = up(M->d_quad_props, hm.quad_props.data(), hm.quad_props.size() * 8);
+  if (e == cudaSuccess) e = up(M->d_nodal_load, hm.nodal_load.data(), hm.nodal_load.size() * 8);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "uploading the model"));
+  *out = M;
+  return SSO_OK;
+}
+
+void sso_model_destroy(sso_model* M) {
+  if (!M) return;
+  if (M->self_batch) sso_batch_destroy(M->self_batch);
+  if (M->stream) cudaStreamSynchronize(M->stream);
+  if (M->arena) cudaFree(M->arena);
+  if (M->ev_in) cudaEventDestroy(M->ev_in);
+  if (M->ev_out) cudaEventDestroy(M->ev_out);
+  if (M->stream) cudaStreamDestroy(M->stream);
+  delete M;
+}
+
+sso_status sso_model_set_design(sso_model* M, const double* z, const double* t) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  if (z)
+    CK(cudaMemcpy2DAsync(M->d_xyz + 2, 3 * sizeof(double), z, sizeof(double), sizeof(double),
+                         M->n_nodes, cudaMemcpyDefault, M->stream));
+  if (t && M->n_quads > 0)
+    CK(cudaMemcpy2DAsync(M->d_quad_props, 5 * sizeof(double), t, sizeof(double), sizeof(double),
+                         M->n_quads, cudaMemcpyDefault, M->stream));
+  if (z || t) M->assembled = false;
+  return leave(M);
+}
+
+sso_status sso_model_solve(sso_model* M, const sso_options* opts, sso_stats* stats) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  sso_status st = ensure_self_batch(M);
+  if (st != SSO_OK) return st;
+  return sso_batch_solve(M->self_batch, opts, stats);
+}
+
+sso_status sso_model_gradient(sso_model* M, double w, const double* g, sso_stats* stats) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  sso_status st = ensure_self_batch(M);
+  if (st != SSO_OK) return st;
+  const double* gs[1] = {g};
+  return sso_batch_gradient(M->self_batch, &w, gs, stats);
+}
+
+sso_status sso_model_get(sso_model* M, double* u, double* C, double* dz, double* dt,
+                         double* lam) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  const size_t ndof = 6 * (size_t)M->n_nodes;
+  if (u) CK(cudaMemcpyAsync(u, M->d_u, ndof * 8, cudaMemcpyDefault, M->stream));
+  if (C) CK(cudaMemcpyAsync(C, M->d_C, 8, cudaMemcpyDefault, M->stream));
+  if (dz) CK(cudaMemcpyAsync(dz, M->d_dz, M->n_nodes * 8, cudaMemcpyDefault, M->stream));
+  if (dt && M->n_quads > 0)
+    CK(cudaMemcpyAsync(dt, M->d_dt, M->n_quads * 8, cudaMemcpyDefault, M->stream));
+  if (lam) CK(cudaMemcpyAsync(lam, M->d_lam, ndof * 8, cudaMemcpyDefault, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  return leave(M);
+}
+
+sso_status sso_model_info(const sso_model* M, int32_t* n_nodes, int32_t* n_blocks,
+                          int32_t* n_elem_blocks) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  if (n_nodes) *n_nodes = M->n_nodes;
+  if (n_blocks) *n_blocks = M->n_blocks;
+  if (n_elem_blocks) *n_elem_blocks = M->n_eb;
+  return SSO_OK;
+}
+
+sso_status sso_model_get_stiffness(sso_model* M, int32_t* row_ptr, int32_t* col, double* K64,
+                                   float* K32) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  if ((K64 || K32) && !M->assembled) return fail(SSO_ERR_INVALID, "K not assembled yet");
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  if (row_ptr)
+    CK(cudaMemcpyAsync(row_ptr, M->h_row_ptr.data(), M->h_row_ptr.size() * 4, cudaMemcpyDefault,
+                       M->stream));
+  if (col)
+    CK(cudaMemcpyAsync(col, M->h_col.data(), M->h_col.size() * 4, cudaMemcpyDefault, M->stream));
+  if (K64)
+    CK(cudaMemcpyAsync(K64, M->d_K64, (size_t)M->n_blocks * 36 * 8, cudaMemcpyDefault,
+                       M->stream));
+  if (K32)
+    CK(cudaMemcpyAsync(K32, M->d_K32, (size_t)M->n_blocks * 36 * 4, cudaMemcpyDefault,
+                       M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  return leave(M);
+}
+
+sso_status sso_model_get_load(sso_model* M, double* f) {
+  if (!M || !f) return fail(SSO_ERR_INVALID, "NULL argument");
+  if (!M->assembled) return fail(SSO_ERR_INVALID, "loads not assembled yet");
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  CK(cudaMemcpyAsync(f, M->d_f, 6 * (size_t)M->n_nodes * 8, cudaMemcpyDefault, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  return leave(M);
+}
+
+sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out) {
+  if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!models || n <= 0) return fail(SSO_ERR_INVALID, "need at least one model");
+  for (int s = 0; s < n; ++s)
+    if (!models[s]) return fail(SSO_ERR_INVALID, "NULL model in batch");
+  for (int s = 1; s < n; ++s)
+    if (models[s]->device != models[0]->device)
+      return fail(SSO_ERR_INVALID, "models of a batch must be on one device");
+  sso_batch* B = new sso_batch();
+  B->models.assign(models, models + n);
+  B->stream = models[0]->stream;
+  B->n_sys = n;
+  std::vector<int2> tiles;
+  B->h_sys.resize(n);
+  for (int s = 0; s < n; ++s) {
+    sso_model* M = models[s];
+    SysDesc& D = B->h_sys[s];
+    D.n_nodes = M->n_nodes;
+    D.tile0 = (int)tiles.size();
+    D.n_tiles = M->n_tiles;
+    D.precond = SSO_BLOCK_JACOBI;
+    D.row_ptr = M->d_row_ptr;
+    D.col = M->d_col;
+    D.K32 = M->d_K32;
+    D.K64 = M->d_K64;
+    D.M32 = M->d_M32;
+    D.M64 = M->d_M64;
+    D.b = M->d_f;
+    D.x = M->d_u;
+    D.r64 = M->d_r64;
+    D.r = M->d_r;
+    D.z = M->d_z;
+    D.p0 = M->d_p0;
+    D.p1 = M->d_p1;
+    D.q = M->d_q;
+    D.part_a = M->d_part_a;
+    D.part_b = M->d_part_b;
+    for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_int2(s, k * TILE));
+  }
+  B->n_tiles = (int)tiles.size();
+  Carver c(nullptr);
+  c.take<SysDesc>(n);
+  c.take<SysScalars>(n);
+  c.take<int2>(tiles.size());
+  c.take<int>(1);
+  c.take<int>(1);
+  c.take<double>(n);
+  const size_t bytes = align_up(c.off, 256);
+  cudaError_t e = cudaMalloc(&B->arena, bytes);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "cudaMalloc(batch arena)");
+  }
+  Carver d(B->arena);
+  B->d_sys = d.take<SysDesc>(n);
+  B->d_sc = d.take<SysScalars>(n);
+  B->d_tiles = d.take<int2>(tiles.size());
+  B->d_n_tiles = d.take<int>(1);
+  B->d_n_active = d.take<int>(1);
+  B->d_dots = d.take<double>(n);
+  for (int s = 0; s < n; ++s) B->h_sys[s].sc = B->d_sc + s;
+  e = cudaMallocHost(&B->h_sc, sizeof(SysScalars) * n);
+  if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->arena, 0, bytes, B->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_tiles, tiles.data(), tiles.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_n_tiles, &B->n_tiles, sizeof(int), cudaMemcpyHostToDevice,
+                        B->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice,
+                        B->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) {
+    sso_batch_destroy(B);
+    return cuda_fail(e, "batch set-up");
+  }
+  *out = B;
+  return SSO_OK;
+}
+
+void sso_batch_destroy(sso_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  for (int k = 0; k < 2; ++k)
+    if (B->exec[k]) cudaGraphExecDestroy(B->exec[k]);
+  if (B->arena) cudaFree(B->arena);
+  if (B->h_sc) cudaFreeHost(B->h_sc);
+  if (B->h_flag) cudaFreeHost(B->h_flag);
+  if (B->ev) cudaEventDestroy(B->ev);
+  delete B;
+}
+
+sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* stats) {
+  if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  sso_status st = check_options(opts);
+  if (st != SSO_OK) return st;
+  sso_model* M0 = B->models[0];
+  st = enter(M0);
+  if (st != SSO_OK) return st;
+  // other models' callers' streams also order before this work
+  for (int s = 1; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    CK(cudaEventRecord(M->ev_in, M->user_stream));
+    CK(cudaStreamWaitEvent(B->stream, M->ev_in, 0));
+  }
+  for (int s = 0; s < B->n_sys; ++s) {
+    st = setup_model(B->models[s], opts->precond, B->stream);
+    if (st != SSO_OK) return st;
+  }
+  std::vector<char> active(B->n_sys, 1);
+  sso_status run = batch_run(B, opts, false, active, stats);
+  if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
+  // compliance C = f^T u, and the preconditioner check
+  CL(launch_dot(B->n_sys, B->d_sys, B->d_dots, B->stream), 1);
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    CK(cudaMemcpyAsync(M->d_C, B->d_dots + s, sizeof(double), cudaMemcpyDeviceToDevice,
+                       B->stream));
+  }
+  std::vector<int> errs(B->n_sys, 0);
+  for (int s = 0; s < B->n_sys; ++s)
+    CK(cudaMemcpyAsync(&errs[s], B->models[s]->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                       B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    M->solved = true;
+    M->last_opts = *opts;
+    if (errs[s]) {
+      if (stats) stats[s].status = SSO_ERR_SINGULAR;
+      if (run == SSO_OK) run = fail(SSO_ERR_SINGULAR, "a diagonal block of K is not positive "
+                                                      "definite (unsupported mechanism?)");
+    }
+  }
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    CK(cudaEventRecord(M->ev_out, B->stream));
+    CK(cudaStreamWaitEvent(M->user_stream, M->ev_out, 0));
+  }
+  return run;
+}
+
+sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const* g,
+                              sso_stats* stats) {
+  if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  for (int s = 0; s < B->n_sys; ++s)
+    if (!B->models[s]->solved || !B->models[s]->assembled)
+      return fail(SSO_ERR_INVALID, "gradient needs a current solve of every model");
+  sso_model* M0 = B->models[0];
+  sso_status st = enter(M0);
+  if (st != SSO_OK) return st;
+  for (int s = 1; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    CK(cudaEventRecord(M->ev_in, M->user_stream));
+    CK(cudaStreamWaitEvent(B->stream, M->ev_in, 0));
+  }
+  std::vector<char> active(B->n_sys, 0);
+  bool any = false;
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    const double ws = w ? w[s] : 1.0;
+    const double* gs = g ? g[s] : nullptr;
+    const int ndof = 6 * M->n_nodes;
+    if (gs) {
+      // rhs = w f + g, zero on fixed DOFs (g may be host memory)
+      CK(cudaMemcpyAsync(M->d_rhs, gs, (size_t)ndof * 8, cudaMemcpyDefault, B->stream));
+      CL(launch_axpby(ndof, ws, M->d_f, M->d_rhs, M->d_fixed, M->d_rhs, B->stream), 1);
+      active[s] = 1;
+      any = true;
+    }
+  }
+  sso_status run = SSO_OK;
+  if (any) {
+    // the adjoint solve reuses K, the preconditioner and the last options
+    sso_options o = B->models[0]->last_opts;
+    run = batch_run(B, &o, true, active, stats);
+    if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
+  }
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    const double ws = w ? w[s] : 1.0;
+    const bool has_g = active[s] != 0;
+    const double* lam = has_g ? M->d_lam : M->d_u;
+    const double lam_scale = has_g ? 1.0 : ws;
+    if (!has_g)
+      CL(launch_axpby(6 * M->n_nodes, ws, M->d_u, nullptr, M->d_fixed, M->d_lam, B->stream), 1);
+    CL(launch_beam_adjoint(M->n_beams, M->d_xyz, M->d_beam_conn, M->d_beam_props, M->d_u, lam,
+                           lam_scale, M->d_gslot, B->stream),
+       M->n_beams > 0);
+    CL(launch_quad_adjoint(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props, M->pressure,
+                           M->gamma, M->d_u, lam, lam_scale, ws,
+                           M->d_gslot + 2 * (size_t)M->n_beams, M->d_dt, B->stream),
+       M->n_quads > 0);
+    CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, nullptr, M->d_gslot,
+                          nullptr, M->d_fixed, nullptr, M->d_dz, B->stream),
+       1);
+    if (stats && !has_g) {
+      stats[s].status = SSO_OK;
+      stats[s].iterations = 0;
+      stats[s].sweeps = 0;
+      stats[s].rel_residual = 0.0;
+      stats[s].ms = 0.0;
+    }
+  }
+  CK(cudaStreamSynchronize(B->stream));
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    CK(cudaEventRecord(M->ev_out, B->stream));
+    CK(cudaStreamWaitEvent(M->user_stream, M->ev_out, 0));
+  }
+  return run;
+}
+
+}  // extern "C"

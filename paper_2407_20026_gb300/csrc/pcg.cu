@@ -1,0 +1,372 @@
+// Batched preconditioned CG with FP64 iterative refinement.
+//
+// One CG iteration over every system of a batch is two kernels, A then B,
+// each a grid-stride loop over tiles (TILE nodes of one system per tile, one
+// thread per scalar row).  Every system runs its own state machine, stored in
+// its SysScalars:
+//
+//   INIT   A: r64 = b, ||b||^2             B: start sweep 1 (or finish if b = 0)
+//   RESID  A: r64 = b - K64 x (FP64 SpMV), B: finish if ||r64|| <= rtol ||b||,
+//             ||r64||^2, ||b||^2              else r = r64 / ||r64||, z = M^-1 r,
+//                                             start a new inner sweep
+//   PCG    A: p = z + beta p (formed on    B: x += scale alpha p (FP64),
+//             the fly for every column       r -= alpha q, z = M^-1 r,
+//             read), q = K p, p^T q           r^T z, ||r||^2; beta; end the
+//                                             sweep when ||r||^2 <= inner_thr
+//   DONE   skipped
+//
+// In FP32_IR mode r, z, p, q and K are FP32 (K32 = round(K64)); x, r64 and
+// every dot product are FP64.  In FP64 mode everything is FP64 and the RESID
+// step only confirms the true residual.
+//
+// Reductions: each tile writes its partial sum, then increments the system's
+// completion counter (integer atomic); the CTA that completes the last tile
+// sums the partials in tile order and updates the scalars.  Tiles are aligned
+// to each system's own rows, so a system's iterates are bit-identical whether
+// it runs alone or inside any batch.  There are no spin-waits.
+#include <math.h>
+
+#include "sso_internal.cuh"
+
+namespace sso {
+namespace {
+
+__device__ __forceinline__ void load6(const float* p, float v[6]) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+  const float2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+__device__ __forceinline__ void load6(const double* p, double v[6]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename T> struct MatOf;
+template <> struct MatOf<float> {
+  static __device__ __forceinline__ const float* K(const SysDesc& S) { return S.K32; }
+  static __device__ __forceinline__ const float* M(const SysDesc& S) { return S.M32; }
+};
+template <> struct MatOf<double> {
+  static __device__ __forceinline__ const double* K(const SysDesc& S) { return S.K64; }
+  static __device__ __forceinline__ const double* M(const SysDesc& S) { return S.M64; }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the NT threads of the CTA in a fixed order; valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  }
+  __syncthreads();
+  return s;
+}
+
+// Ordered sum of n partials (stride `stride`, offset `off`); valid in thread 0.
+__device__ __forceinline__ double ordered_sum(const double* part, int n, int stride, int off,
+                                              double* red) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += NT) v += __ldcg(part + (size_t)k * stride + off);
+  return block_sum(v, red);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) pcg_a_kernel(const int2* __restrict__ tiles,
+                                                   const int* __restrict__ n_tiles_ptr,
+                                                   const SysDesc* __restrict__ sys,
+                                                   int* __restrict__ n_active) {
+  __shared__ double red[NT / 32];
+  __shared__ int s_last;
+  const int n_tiles = *n_tiles_ptr;
+  const int t = threadIdx.x;
+  const int ln = t / 6, rr = t - 6 * (t / 6);
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int2 tl = tiles[tile];
+    const SysDesc& S = sys[tl.x];
+    SysScalars* sc = S.sc;
+    const int state = *(volatile int*)&sc->state;
+    if (state == ST_DONE) continue;
+    const int node = tl.y + ln;
+    const bool act = node < S.n_nodes;
+    const int i = 6 * node + rr;
+    double part = 0.0, part_b = 0.0;
+    if (state == ST_PCG) {
+      const T* __restrict__ K = MatOf<T>::K(S);
+      const T* __restrict__ z = (const T*)S.z;
+      const int par = sc->parity;
+      const T* __restrict__ pold = (const T*)(par ? S.p1 : S.p0);
+      T* pnew = (T*)(par ? S.p0 : S.p1);
+      const bool first = sc->inner == 0;
+      const T beta = first ? T(0) : (T)sc->beta;
+      if (act) {
+        T acc = T(0);
+        const int j1 = __ldg(S.row_ptr + node + 1);
+        for (int j = __ldg(S.row_ptr + node); j < j1; ++j) {
+          const int c = __ldg(S.col + j);
+          T kv[6], zv[6];
+          load6(K + (size_t)j * 36 + rr * 6, kv);
+          load6(z + (size_t)c * 6, zv);
+          if (first) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc = fmaT(kv[k], zv[k], acc);
+          } else {
+            T pv[6];
+            load6(pold + (size_t)c * 6, pv);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc = fmaT(kv[k], fmaT(beta, pv[k], zv[k]), acc);
+          }
+        }
+        const T pi = first ? z[i] : fmaT(beta, pold[i], z[i]);
+        pnew[i] = pi;
+        ((T*)S.q)[i] = acc;
+        part = (double)pi * (double)acc;
+      }
+    } else {  // ST_INIT or ST_RESID: r64 = b - K64 x in FP64
+      if (act) {
+        const double bi = S.b[i];
+        double acc = bi;
+        part_b = bi * bi;
+        if (state == ST_RESID) {
+          const int j1 = __ldg(S.row_ptr + node + 1);
+          for (int j = __ldg(S.row_ptr + node); j < j1; ++j) {
+            const int c = __ldg(S.col + j);
+            double kv[6], xv[6];
+            load6(S.K64 + (size_t)j * 36 + rr * 6, kv);
+            load6(S.x + (size_t)c * 6, xv);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc = fma(-kv[k], xv[k], acc);
+          }
+        }
+        S.r64[i] = acc;
+        part = acc * acc;
+      }
+    }
+    const double tot = block_sum(part, red);
+    const double tot_b = state == ST_PCG ? 0.0 : block_sum(part_b, red);
+    if (t == 0) {
+      S.part_a[2 * (tile - S.tile0)] = tot;
+      S.part_a[2 * (tile - S.tile0) + 1] = tot_b;
+      __threadfence();
+      const unsigned prev = atomicAdd(&sc->cnt_a, 1u);
+      s_last = (prev == (unsigned)(S.n_tiles - 1));
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      const double sum = ordered_sum(S.part_a, S.n_tiles, 2, 0, red);
+      const double sum_b = state == ST_PCG ? 0.0 : ordered_sum(S.part_a, S.n_tiles, 2, 1, red);
+      if (t == 0) {
+        if (state == ST_PCG) {
+          sc->pq = sum;
+          if (!(sum > 0.0) || !isfinite(sum)) {
+            sc->status = SSO_ERR_SINGULAR;
+            sc->state = ST_DONE;
+            atomicSub(n_active, 1);
+          } else {
+            sc->alpha = sc->rz / sum;
+            sc->parity ^= 1;
+          }
+        } else {
+          sc->rr64 = sum;
+          sc->ff = sum_b;
+        }
+        sc->cnt_a = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) pcg_b_kernel(const int2* __restrict__ tiles,
+                                                   const int* __restrict__ n_tiles_ptr,
+                                                   const SysDesc* __restrict__ sys,
+                                                   int* __restrict__ n_active) {
+  __shared__ double red[NT / 32];
+  __shared__ T s_r[NT];
+  __shared__ int s_last;
+  const int n_tiles = *n_tiles_ptr;
+  const int t = threadIdx.x;
+  const int ln = t / 6, rr = t - 6 * (t / 6);
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int2 tl = tiles[tile];
+    const SysDesc& S = sys[tl.x];
+    SysScalars* sc = S.sc;
+    const int state = *(volatile int*)&sc->state;
+    if (state == ST_DONE) continue;
+    const int node = tl.y + ln;
+    const bool act = node < S.n_nodes;
+    const int i = 6 * node + rr;
+    T* r = (T*)S.r;
+    bool work = true;
+    T ri = T(0);
+    if (state == ST_PCG) {
+      const T alpha = (T)sc->alpha;
+      const double ua = sc->alpha * sc->scale;
+      const T* p = (const T*)(sc->parity ? S.p1 : S.p0);
+      if (act) {
+        S.x[i] = fma(ua, (double)p[i], S.x[i]);
+        ri = fmaT(-alpha, ((const T*)S.q)[i], r[i]);
+        r[i] = ri;
+      }
+    } else {
+      const double rr64 = sc->rr64;
+      work = isfinite(rr64) && !(rr64 <= sc->rtol2 * sc->ff);
+      if (work && act) {
+        ri = (T)(S.r64[i] * (1.0 / ::sqrt(rr64)));
+        r[i] = ri;
+      }
+    }
+    s_r[t] = ri;
+    __syncthreads();
+    double v1 = 0.0, v2 = 0.0;
+    if (work && act) {
+      const T* __restrict__ M = MatOf<T>::M(S);
+      T zi;
+      if (S.precond == SSO_BLOCK_JACOBI) {
+        T mv[6];
+        load6(M + (size_t)node * 36 + rr * 6, mv);
+        zi = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) zi = fmaT(mv[k], s_r[6 * ln + k], zi);
+      } else {
+        zi = M[i] * ri;
+      }
+      ((T*)S.z)[i] = zi;
+      v1 = (double)ri * (double)zi;
+      v2 = (double)ri * (double)ri;
+    }
+    const double t1 = block_sum(v1, red);
+    const double t2 = block_sum(v2, red);
+    if (t == 0) {
+      S.part_b[2 * (tile - S.tile0)] = t1;
+      S.part_b[2 * (tile - S.tile0) + 1] = t2;
+      __threadfence();
+      const unsigned prev = atomicAdd(&sc->cnt_b, 1u);
+      s_last = (prev == (unsigned)(S.n_tiles - 1));
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      const double s1 = ordered_sum(S.part_b, S.n_tiles, 2, 0, red);
+      const double s2 = ordered_sum(S.part_b, S.n_tiles, 2, 1, red);
+      if (t == 0) {
+        if (state == ST_PCG) {
+          sc->iters += 1;
+          sc->inner += 1;
+          if (!isfinite(s1) || !isfinite(s2)) {
+            sc->status = SSO_ERR_SINGULAR;
+            sc->state = ST_DONE;
+            atomicSub(n_active, 1);
+          } else {
+            sc->beta = s1 / sc->rz;
+            sc->rz = s1;
+            sc->rr = s2;
+            if (s2 <= sc->inner_thr || sc->iters >= sc->max_iter) sc->state = ST_RESID;
+          }
+        } else {
+          const double rr64 = sc->rr64;
+          if (!isfinite(rr64)) {
+            sc->status = SSO_ERR_INVALID;
+            sc->state = ST_DONE;
+            atomicSub(n_active, 1);
+          } else if (rr64 <= sc->rtol2 * sc->ff) {
+            sc->status = SSO_OK;
+            sc->state = ST_DONE;
+            atomicSub(n_active, 1);
+          } else if (sc->iters >= sc->max_iter || sc->sweeps >= sc->max_sweeps) {
+            sc->status = SSO_ERR_NOT_CONVERGED;
+            sc->state = ST_DONE;
+            atomicSub(n_active, 1);
+          } else if (!(s1 > 0.0)) {
+            sc->status = SSO_ERR_SINGULAR;  // preconditioner not positive definite
+            sc->state = ST_DONE;
+            atomicSub(n_active, 1);
+          } else {
+            sc->rz = s1;
+            sc->rr = s2;
+            sc->rr_start = s2;
+            sc->scale = ::sqrt(rr64);
+            sc->inner_thr = s2 * fmax(sc->inner_rtol2, 0.25 * sc->rtol2 * sc->ff / rr64);
+            sc->inner = 0;
+            sc->sweeps += 1;
+            sc->state = ST_PCG;
+          }
+        }
+        sc->cnt_b = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// out[s] = b_s^T x_s for every system, one CTA per system, fixed order.
+__global__ void __launch_bounds__(NT) dot_kernel(const SysDesc* __restrict__ sys,
+                                                 double* __restrict__ out) {
+  __shared__ double red[NT / 32];
+  const SysDesc& S = sys[blockIdx.x];
+  const int n = 6 * S.n_nodes;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) v = fma(S.b[i], S.x[i], v);
+  const double s = block_sum(v, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
+                         int* n_active, int grid, cudaStream_t s) {
+  if (fp64)
+    pcg_a_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+  else
+    pcg_a_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
+                         int* n_active, int grid, cudaStream_t s) {
+  if (fp64)
+    pcg_b_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+  else
+    pcg_b_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s) {
+  if (n_sys <= 0) return cudaSuccess;
+  dot_kernel<<<n_sys, NT, 0, s>>>(sys, out);
+  return cudaGetLastError();
+}
+
+// CTAs resident on the whole device for the PCG kernels (grid-stride loops
+// never need more).
+int pcg_grid_limit(bool fp64) {
+  int dev = 0, sms = 0, per_sm_a = 0, per_sm_b = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (fp64) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_kernel<double>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b_kernel<double>, NT, 0);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_kernel<float>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b_kernel<float>, NT, 0);
+  }
+  int per_sm = per_sm_a < per_sm_b ? per_sm_a : per_sm_b;
+  if (per_sm < 1) per_sm = 1;
+  if (sms < 1) sms = 1;
+  return sms * per_sm;
+}
+
+}  // namespace sso

@@ -1,0 +1,116 @@
+// Internal declarations shared by the CUDA translation units of libsso.
+//
+// Data layout in device memory (one structure = one "system"):
+//   DOF vectors      node-major, 6 entries per node, length 6 * n_nodes
+//   K (BSR)          one block row per node; row_ptr [n_nodes+1], col [n_blocks],
+//                    values [n_blocks][6][6] row-major (FP64 K64 and FP32 K32)
+//   element blocks   ke[eb][6][6] FP64, eb = 4 e + 2 a + b for beam e,
+//                    eb = 4 n_beams + 16 e + 4 a + b for quad e
+//   node slots       s = 2 e + a for beam e (node a), s = 2 n_beams + 4 e + a
+//                    for quad e; per-slot gradient and load values are summed
+//                    per node in slot order
+//   preconditioner   block-Jacobi: [n_nodes][6][6] inverse diagonal blocks;
+//                    Jacobi: [n_nodes*6] inverse diagonal entries
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sso.h"
+
+namespace sso {
+
+// PCG tiling: a tile is TILE consecutive nodes of one system, processed by one
+// CTA of 6*TILE threads (one thread per scalar row).
+constexpr int TILE = 32;
+constexpr int NT = 6 * TILE;
+
+enum SysState : int { ST_INIT = 0, ST_PCG = 1, ST_RESID = 2, ST_DONE = 3 };
+
+// Per-system solver scalars (device memory, one per system).
+struct SysScalars {
+  int state;        // SysState
+  int parity;       // which p buffer holds the current direction
+  int iters;        // CG iterations, all sweeps
+  int inner;        // CG iterations in the current sweep
+  int sweeps;       // FP64 residual recomputations after the first
+  int status;       // sso_status
+  unsigned int cnt_a, cnt_b;  // tile-completion counters (last-CTA reduction)
+  double rz;        // r^T z of the current iteration
+  double beta;      // rz_new / rz_old
+  double pq;        // p^T K p
+  double alpha;     // rz / pq
+  double rr;        // ||r||^2 of the recursive (inner) residual
+  double rr_start;  // ||r||^2 at the start of the sweep
+  double rr64;      // ||b - K64 x||^2, FP64
+  double ff;        // ||b||^2
+  double scale;     // ||b - K64 x|| at the start of the sweep (inner rhs scale)
+  double inner_thr; // inner stop: rr <= inner_thr
+  double rtol2;     // outer: rr64 <= rtol2 * ff
+  double inner_rtol2;
+  int max_iter;
+  int max_sweeps;
+};
+
+// Per-system pointers (device memory, one per system of a batch).
+struct SysDesc {
+  int n_nodes;
+  int tile0;        // first tile of this system in the batch tile list
+  int n_tiles;
+  int precond;      // sso_precond
+  const int* row_ptr;
+  const int* col;
+  const float* K32;
+  const double* K64;
+  const float* M32;
+  const double* M64;
+  const double* b;  // right-hand side (FP64)
+  double* x;        // solution (FP64)
+  double* r64;      // FP64 residual
+  void* r;          // inner vectors, float or double
+  void* z;
+  void* p0;
+  void* p1;
+  void* q;
+  double* part_a;   // [2 * n_tiles]
+  double* part_b;   // [2 * n_tiles]
+  SysScalars* sc;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (elements.cu)
+cudaError_t launch_beam_stiffness(int n_beams, const double* xyz, const int* conn,
+                                  const double* props, double* ke, cudaStream_t s);
+cudaError_t launch_quad_stiffness(int n_quads, const double* xyz, const int* conn,
+                                  const double* props, double pressure, double gamma,
+                                  double* ke, double* fslot, cudaStream_t s);
+cudaError_t launch_beam_adjoint(int n_beams, const double* xyz, const int* conn,
+                                const double* props, const double* u, const double* lam,
+                                double lam_scale, double* gslot, cudaStream_t s);
+cudaError_t launch_quad_adjoint(int n_quads, const double* xyz, const int* conn,
+                                const double* props, double pressure, double gamma,
+                                const double* u, const double* lam, double lam_scale,
+                                double w, double* gslot, double* dt, cudaStream_t s);
+
+// Launchers (assembly.cu)
+cudaError_t launch_assemble(int n_blocks, const int* cptr, const int* csrc, const double* ke,
+                            const int* brow, const int* col, const uint8_t* fixed,
+                            double* K64, float* K32, cudaStream_t s);
+cudaError_t launch_precond(int n_nodes, int kind, const int* diag_idx, const double* K64,
+                           double* M64, float* M32, int* err_flag, cudaStream_t s);
+cudaError_t launch_node_gather(int n_nodes, const int* nptr, const int* nsrc, int slot_quad0,
+                               const double* fslot, const double* gslot,
+                               const double* nodal_load, const uint8_t* fixed, double* f,
+                               double* dz, cudaStream_t s);
+cudaError_t launch_axpby(int n, double a, const double* x, const double* y, const uint8_t* fixed,
+                         double* out, cudaStream_t s);
+
+// Launchers (pcg.cu)
+cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
+                         int* n_active, int grid, cudaStream_t s);
+cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
+                         int* n_active, int grid, cudaStream_t s);
+cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
+int pcg_grid_limit(bool fp64);
+
+}  // namespace sso

@@ -1,0 +1,252 @@
+"""CUDA path (through the C-ABI) vs the FP64 oracle.
+
+Elements element by element; assembled K entry by entry (FP64 vs oracle, FP32
+bit-exact rounding of FP64, bit-reproducible); loads; solves and adjoint
+gradients in FP64 mode (1e-8) and FP32 + FP64 refinement (1e-6) on beam,
+shell and mixed models whose node counts are not multiples of the tile.
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+from gpu_util import (TOL_ELEMENT, TOL_FP32_IR, TOL_FP64, bsr_to_dense, mixed_model, rel,
+                      small_shell, with_supports)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sso():
+    import paper_2407_20026_gb300 as pkg
+    from paper_2407_20026_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available()
+    return pkg
+
+
+def _rand_quads(n, seed):
+    rng = np.random.default_rng(seed)
+    base = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], float)
+    X = np.empty((n, 4, 3))
+    for e in range(n):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        P = base * rng.uniform(0.3, 3.0, 3) + rng.uniform(-0.15, 0.15, (4, 3)) * [1, 1, 0]
+        P[:, 2] += rng.uniform(-0.08, 0.08, 4)  # warp
+        X[e] = P @ Q.T + rng.normal(size=3) * 5
+    props = np.stack([rng.uniform(0.05, 0.3, n), rng.uniform(1e9, 2e11, n),
+                      rng.uniform(0.0, 0.45, n), rng.uniform(0.5, 2.0, n),
+                      rng.uniform(0.5, 2.0, n)], 1)
+    return X, props
+
+
+def test_quad_element_matrices(sso, orc):
+    X, props = _rand_quads(300, 7)
+    xyz = torch.tensor(X.reshape(-1, 3), device="cuda")
+    conn = torch.arange(4 * len(X), dtype=torch.int32, device="cuda").reshape(-1, 4)
+    ke = sso.quad_stiffness(xyz, conn, torch.tensor(props, device="cuda")).cpu().numpy()
+    for e in range(len(X)):
+        ref = orc.quad_ke(X[e], props[e])
+        got = ke[e].transpose(0, 2, 1, 3).reshape(24, 24)
+        assert np.abs(got - ref).max() <= TOL_ELEMENT * np.abs(ref).max(), e
+
+
+def test_beam_element_matrices(sso, orc):
+    rng = np.random.default_rng(3)
+    n = 300
+    xi = rng.normal(size=(n, 3)) * 3
+    d = rng.normal(size=(n, 3))
+    d[:10, :2] = 0.0  # vertical members take the e_Y branch
+    xj = xi + d * rng.uniform(0.2, 4.0, (n, 1))
+    props = np.stack([rng.uniform(1e10, 3e11, n), rng.uniform(1e10, 1e11, n),
+                      rng.uniform(1e-6, 1e-4, n), rng.uniform(1e-6, 1e-4, n),
+                      rng.uniform(1e-6, 1e-4, n), rng.uniform(1e-4, 1e-2, n)], 1)
+    xyz = torch.tensor(np.stack([xi, xj], 1).reshape(-1, 3), device="cuda")
+    conn = torch.arange(2 * n, dtype=torch.int32, device="cuda").reshape(-1, 2)
+    ke = sso.beam_stiffness(xyz, conn, torch.tensor(props, device="cuda")).cpu().numpy()
+    for e in range(n):
+        ref = orc.beam_ke(xi[e], xj[e], props[e])
+        got = ke[e].transpose(0, 2, 1, 3).reshape(12, 12)
+        assert np.abs(got - ref).max() <= TOL_ELEMENT * np.abs(ref).max(), e
+
+
+MODELS = {
+    "gridshell10": lambda: meshgen.gridshell(),
+    "gridshell13": lambda: meshgen.gridshell(n_side=13, seed=5),
+    "shell5": lambda: small_shell(5),
+    "shell9_clamped": lambda: meshgen.shell(n_el=9, span=8.0, supports="clamped",
+                                            load="pressure", seed=4),
+    "mixed": lambda: mixed_model(5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MODELS))
+def test_assembled_stiffness_and_loads(sso, orc, name):
+    m = MODELS[name]()
+    mdl = sso.Model(m)
+    mdl.solve(precision="fp64")
+    rp, col, K64, K32 = mdl.stiffness()
+    Kg = bsr_to_dense(rp, col, K64)
+    Ko = with_supports(orc.assemble_dense(m), m["fixed"])
+    assert np.abs(Kg - Ko).max() <= 1e-12 * np.abs(Ko).max()
+    # K32 is exactly the round-to-nearest of K64
+    assert np.array_equal(K32, K64.astype(np.float32))
+    # assembly is bit-reproducible
+    mdl.solve(precision="fp64")
+    _, _, K64b, _ = mdl.stiffness()
+    assert np.array_equal(K64, K64b)
+    fo = orc.load_vector(m)
+    fo[m["fixed"].ravel().astype(bool)] = 0.0
+    np.testing.assert_allclose(mdl.load_vector(), fo, rtol=0, atol=1e-12 * np.abs(fo).max())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_ir", TOL_FP32_IR)])
+@pytest.mark.parametrize("name", sorted(MODELS))
+def test_solve_and_gradient(sso, orc, name, precision, tol):
+    m = MODELS[name]()
+    ref = orc.gradient(m, w=1.0)
+    mdl = sso.Model(m)
+    rtol = 1e-10 if precision == "fp64" else 1e-9
+    st = mdl.solve(precision=precision, rtol=rtol)
+    assert st["status"] == 0 and st["rel_residual"] <= rtol
+    mdl.gradient(1.0)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= tol
+    assert abs(r["C"] - ref["C"]) <= tol * abs(ref["C"])
+    assert rel(r["dz"], ref["dz"]) <= tol
+    if m["quad_conn"].shape[0]:
+        assert rel(r["dt"], ref["dt"]) <= tol
+    assert np.all(r["u"][m["fixed"].ravel().astype(bool)] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["gridshell10", "mixed"])
+def test_general_objective_adjoint(sso, orc, name):
+    """J = w C + g^T u: a real adjoint solve K lambda = w f + g (Eq. 5)."""
+    m = MODELS[name]()
+    rng = np.random.default_rng(11)
+    g = rng.normal(size=6 * m["xyz"].shape[0]) * 1e3
+    ref = orc.gradient(m, w=0.5, g=g)
+    mdl = sso.Model(m)
+    mdl.solve(precision="fp64", rtol=1e-11)
+    st = mdl.gradient(0.5, g)
+    assert st["status"] == 0
+    r = mdl.result()
+    free = ~m["fixed"].ravel().astype(bool)
+    assert rel(r["lam"][free], ref["lam"][free]) <= TOL_FP64
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP64
+    if m["quad_conn"].shape[0]:
+        assert rel(r["dt"], ref["dt"]) <= TOL_FP64
+
+
+def test_jacobi_preconditioner(sso, orc):
+    m = small_shell(5)
+    ref = orc.gradient(m)
+    mdl = sso.Model(m)
+    st = mdl.solve(precision="fp32_ir", precond="jacobi", rtol=1e-9)
+    assert st["status"] == 0
+    mdl.gradient(1.0)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= TOL_FP32_IR
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP32_IR
+
+
+def test_batch_equals_alone_bitwise(sso):
+    """Each system's result is bit-identical alone and inside a mixed batch."""
+    ms = [MODELS[k]() for k in ("gridshell13", "shell5", "mixed", "gridshell10")]
+    alone = []
+    for m in ms:
+        mdl = sso.Model(m)
+        mdl.solve(precision="fp32_ir", rtol=1e-9)
+        mdl.gradient(1.0)
+        alone.append(mdl.result())
+    models = [sso.Model(m) for m in ms]
+    batch = sso.Batch(models)
+    stats = batch.solve(precision="fp32_ir", rtol=1e-9)
+    assert all(s["status"] == 0 for s in stats)
+    batch.gradient()
+    for mdl, a in zip(models, alone):
+        r = mdl.result()
+        for k in ("u", "dz", "dt"):
+            assert np.array_equal(r[k], a[k]), k
+        assert r["C"] == a["C"]
+
+
+def test_set_design_matches_fresh_model(sso, orc):
+    m = small_shell(5)
+    mdl = sso.Model(m)
+    mdl.solve(precision="fp64")
+    rng = np.random.default_rng(2)
+    z = m["xyz"][:, 2] + rng.uniform(-0.1, 0.1, m["xyz"].shape[0])
+    t = m["quad_props"][:, 0] * rng.uniform(0.8, 1.2, m["quad_props"].shape[0])
+    mdl.set_design(torch.tensor(z, device="cuda"), t)
+    mdl.solve(precision="fp64", rtol=1e-11)
+    mdl.gradient(1.0)
+    m2 = dict(m)
+    m2["xyz"] = m["xyz"].copy()
+    m2["xyz"][:, 2] = z
+    m2["quad_props"] = m["quad_props"].copy()
+    m2["quad_props"][:, 0] = t
+    ref = orc.gradient(m2)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= TOL_FP64
+    assert rel(r["dt"], ref["dt"]) <= TOL_FP64
+
+
+def test_warm_start_converges_in_fewer_iterations(sso):
+    m = small_shell(7)
+    mdl = sso.Model(m)
+    a = mdl.solve(precision="fp32_ir", rtol=1e-9)
+    z = m["xyz"][:, 2] * 1.001
+    mdl.set_design(z, None)
+    cold = sso.Model(m)
+    cold.set_design(z, None)
+    c = cold.solve(precision="fp32_ir", rtol=1e-9)
+    w = mdl.solve(precision="fp32_ir", rtol=1e-9, warm_start=1)
+    assert w["status"] == 0 and a["status"] == 0
+    assert w["iterations"] < c["iterations"]
+    assert rel(mdl.result()["u"], cold.result()["u"]) <= 1e-7
+
+
+def test_zero_load_and_edge_cases(sso):
+    m = small_shell(3)
+    m["pressure"] = 0.0
+    m["gamma"] = 0.0
+    m["nodal_load"][:] = 0.0
+    mdl = sso.Model(m)
+    st = mdl.solve()
+    assert st["status"] == 0 and st["iterations"] == 0
+    r = mdl.result()
+    assert np.all(r["u"] == 0.0) and r["C"] == 0.0
+
+
+def test_iteration_cap_reports_not_converged(sso):
+    mdl = sso.Model(small_shell(6))
+    with pytest.raises(sso.SSOError) as ei:
+        mdl.solve(max_iter=5, rtol=1e-12)
+    assert ei.value.status == 4
+
+
+def test_mechanism_reports_error(sso):
+    """No supports: K is singular (6 rigid modes); the solve must not report OK."""
+    m = small_shell(3)
+    m["fixed"][:] = 0
+    mdl = sso.Model(m)
+    with pytest.raises(sso.SSOError) as ei:
+        mdl.solve(max_iter=3000, rtol=1e-12)
+    assert ei.value.status in (3, 4)
+
+
+def test_autograd_function(sso, orc):
+    from paper_2407_20026_gb300.autograd import SSOFunction
+    m = small_shell(5)
+    mdl = sso.Model(m)
+    z = torch.tensor(m["xyz"][:, 2], device="cuda", requires_grad=True)
+    t = torch.tensor(m["quad_props"][:, 0], device="cuda", requires_grad=True)
+    u, C = SSOFunction.apply(mdl, z, t, sso.options(precision="fp64", rtol=1e-11))
+    rng = np.random.default_rng(5)
+    gvec = torch.tensor(rng.normal(size=u.shape[0]), device="cuda")
+    J = 0.7 * C + (gvec * u).sum()
+    J.backward()
+    ref = orc.gradient(m, w=0.7, g=gvec.cpu().numpy())
+    assert rel(z.grad.cpu().numpy(), ref["dz"]) <= TOL_FP64
+    assert rel(t.grad.cpu().numpy(), ref["dt"]) <= TOL_FP64
