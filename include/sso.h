@@ -103,7 +103,7 @@ typedef struct {
 typedef struct sso_model sso_model;
 typedef struct sso_batch sso_batch;
 
-/* Defaults: FP32_IR, block-Jacobi, rtol 1e-10, inner_rtol 1e-5,
+/* Defaults: FP32_IR, block-Jacobi, rtol 1e-8, inner_rtol 1e-3,
  * max_iter 200000, max_sweeps 40, iters_per_launch 32, cold start, no timeout. */
 void sso_default_options(sso_options* opts);
 
@@ -194,6 +194,15 @@ sso_status sso_batch_solve(sso_batch* batch, const sso_options* opts, sso_stats*
  * all 1; g NULL, or g[i] NULL, means no g term for that system. */
 sso_status sso_batch_gradient(sso_batch* batch, const double* w, const double* const* g,
                               sso_stats* stats);
+
+/* Kernel timing of the CG engine, for roofline measurements: while enabled,
+ * every CG kernel launch of this batch (kernel A: SpMV + p^T K p or the FP64
+ * residual; kernel B: update + preconditioner) is bracketed by CUDA events on
+ * the batch's stream and the durations are summed.  Enabling resets the sums.
+ * launches counts the (A, B) pairs timed. */
+sso_status sso_batch_set_profiling(sso_batch* batch, int32_t enable);
+sso_status sso_batch_kernel_times(const sso_batch* batch, double* ms_a, double* ms_b,
+                                  int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -91,6 +91,9 @@ SIGNATURES = {
     "sso_batch_solve": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(Stats)], _i32),
     "sso_batch_gradient": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_vp),
                             ctypes.POINTER(Stats)], _i32),
+    "sso_batch_set_profiling": ([_vp, _i32], _i32),
+    "sso_batch_kernel_times": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64),
+                                ctypes.POINTER(ctypes.c_int64)], _i32),
 }
 
 _lib = None

@@ -152,8 +152,15 @@ struct sso_batch {
   int* h_flag = nullptr;        // pinned, 2 ints
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   int exec_iters[2] = {0, 0};
+  int exec_prof[2] = {0, 0};
   int grid[2] = {0, 0};
   cudaEvent_t ev = nullptr;
+  // kernel timing (sso_batch_set_profiling): events around every A and B
+  // launch inside the captured graph
+  int profiling = 0;
+  std::vector<cudaEvent_t> pev;
+  double prof_ms_a = 0.0, prof_ms_b = 0.0;
+  long long prof_launches = 0;
 };
 
 namespace {
@@ -411,7 +418,7 @@ sso_status setup_model(sso_model* M, int precond, cudaStream_t s) {
 
 sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
   const int k = fp64 ? 1 : 0;
-  if (B->exec[k] && B->exec_iters[k] == iters) return SSO_OK;
+  if (B->exec[k] && B->exec_iters[k] == iters && B->exec_prof[k] == B->profiling) return SSO_OK;
   if (B->exec[k]) {
     cudaGraphExecDestroy(B->exec[k]);
     B->exec[k] = nullptr;
@@ -420,15 +427,28 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
     const int lim = pcg_grid_limit(fp64);
     B->grid[k] = std::max(1, std::min(B->n_tiles, lim));
   }
+  if (B->profiling) {
+    while ((int)B->pev.size() < 2 * iters + 1) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      B->pev.push_back(e);
+    }
+  }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
+  if (B->profiling)
+    err = cudaEventRecordWithFlags(B->pev[0], B->stream, cudaEventRecordExternal);
   for (int it = 0; it < iters && err == cudaSuccess; ++it) {
     err = launch_pcg_a(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid[k],
                        B->stream);
+    if (err == cudaSuccess && B->profiling)
+      err = cudaEventRecordWithFlags(B->pev[2 * it + 1], B->stream, cudaEventRecordExternal);
     if (err == cudaSuccess)
       err = launch_pcg_b(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid[k],
                          B->stream);
+    if (err == cudaSuccess && B->profiling)
+      err = cudaEventRecordWithFlags(B->pev[2 * it + 2], B->stream, cudaEventRecordExternal);
   }
   cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
   if (err != cudaSuccess) {
@@ -440,6 +460,20 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
   cudaGraphDestroy(g);
   if (err != cudaSuccess) return cuda_fail(err, "cudaGraphInstantiate");
   B->exec_iters[k] = iters;
+  B->exec_prof[k] = B->profiling;
+  return SSO_OK;
+}
+
+// Adds the kernel durations of the last graph launch (after it completed).
+sso_status accumulate_profile(sso_batch* B, int iters) {
+  for (int it = 0; it < iters; ++it) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, B->pev[2 * it], B->pev[2 * it + 1]));
+    CK(cudaEventElapsedTime(&b, B->pev[2 * it + 1], B->pev[2 * it + 2]));
+    B->prof_ms_a += a;
+    B->prof_ms_b += b;
+  }
+  B->prof_launches += iters;
   return SSO_OK;
 }
 
@@ -490,6 +524,10 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
                          B->stream));
       CK(cudaEventRecord(B->ev, B->stream));
       CK(cudaEventSynchronize(B->ev));
+      if (B->profiling) {
+        sso_status ps = accumulate_profile(B, o->iters_per_launch);
+        if (ps != SSO_OK) return ps;
+      }
       ++launches;
       if (B->h_flag[1] <= 0) break;
       if (o->timeout_ms > 0.0) {
@@ -543,8 +581,8 @@ void sso_default_options(sso_options* o) {
   if (!o) return;
   o->precision = SSO_FP32_IR;
   o->precond = SSO_BLOCK_JACOBI;
-  o->rtol = 1e-10;
-  o->inner_rtol = 1e-5;
+  o->rtol = 1e-8;
+  o->inner_rtol = 1e-3;
   o->max_iter = 200000;
   o->max_sweeps = 40;
   o->iters_per_launch = 32;
@@ -865,11 +903,29 @@ void sso_batch_destroy(sso_batch* B) {
   if (B->stream) cudaStreamSynchronize(B->stream);
   for (int k = 0; k < 2; ++k)
     if (B->exec[k]) cudaGraphExecDestroy(B->exec[k]);
+  for (cudaEvent_t e : B->pev) cudaEventDestroy(e);
   if (B->arena) cudaFree(B->arena);
   if (B->h_sc) cudaFreeHost(B->h_sc);
   if (B->h_flag) cudaFreeHost(B->h_flag);
   if (B->ev) cudaEventDestroy(B->ev);
   delete B;
+}
+
+sso_status sso_batch_set_profiling(sso_batch* B, int32_t enable) {
+  if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  B->profiling = enable ? 1 : 0;
+  B->prof_ms_a = B->prof_ms_b = 0.0;
+  B->prof_launches = 0;
+  return SSO_OK;
+}
+
+sso_status sso_batch_kernel_times(const sso_batch* B, double* ms_a, double* ms_b,
+                                  int64_t* launches) {
+  if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  if (ms_a) *ms_a = B->prof_ms_a;
+  if (ms_b) *ms_b = B->prof_ms_b;
+  if (launches) *launches = B->prof_launches;
+  return SSO_OK;
 }
 
 sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* stats) {

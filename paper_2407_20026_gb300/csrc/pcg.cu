@@ -83,7 +83,7 @@ __device__ __forceinline__ double ordered_sum(const double* part, int n, int str
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) pcg_a_kernel(const int2* __restrict__ tiles,
+__global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const int2* __restrict__ tiles,
                                                    const int* __restrict__ n_tiles_ptr,
                                                    const SysDesc* __restrict__ sys,
                                                    int* __restrict__ n_active) {
@@ -106,29 +106,42 @@ __global__ void __launch_bounds__(NT) pcg_a_kernel(const int2* __restrict__ tile
       const T* __restrict__ K = MatOf<T>::K(S);
       const T* __restrict__ z = (const T*)S.z;
       const int par = sc->parity;
-      const T* __restrict__ pold = (const T*)(par ? S.p1 : S.p0);
+      const T* pold = (const T*)(par ? S.p1 : S.p0);
       T* pnew = (T*)(par ? S.p0 : S.p1);
+      // first iteration of a sweep: p = z, written as z + 0 * z (exact for
+      // finite z) so that one code path serves every iteration
       const bool first = sc->inner == 0;
       const T beta = first ? T(0) : (T)sc->beta;
+      if (first) pold = z;
       if (act) {
+        // Column indices of a chunk first, then every K row / z / p load of the
+        // chunk (indices past the row end are clamped to its last block and
+        // their FMAs skipped), then the FMAs in column order: the loads of a
+        // chunk are in flight together and the summation order is plain j.
+        constexpr int CH = sizeof(T) == 4 ? 3 : 2;
         T acc = T(0);
-        const int j1 = __ldg(S.row_ptr + node + 1);
-        for (int j = __ldg(S.row_ptr + node); j < j1; ++j) {
-          const int c = __ldg(S.col + j);
-          T kv[6], zv[6];
-          load6(K + (size_t)j * 36 + rr * 6, kv);
-          load6(z + (size_t)c * 6, zv);
-          if (first) {
+        const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
+        for (int jb = j0; jb < j1; jb += CH) {
+          int cc[CH];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc = fmaT(kv[k], zv[k], acc);
-          } else {
-            T pv[6];
-            load6(pold + (size_t)c * 6, pv);
+          for (int u = 0; u < CH; ++u) cc[u] = __ldg(S.col + min(jb + u, j1 - 1));
+          T kv[CH][6], zv[CH][6], pv[CH][6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc = fmaT(kv[k], fmaT(beta, pv[k], zv[k]), acc);
+          for (int u = 0; u < CH; ++u) {
+            load6(K + (size_t)min(jb + u, j1 - 1) * 36 + rr * 6, kv[u]);
+            load6(z + (size_t)cc[u] * 6, zv[u]);
+            load6(pold + (size_t)cc[u] * 6, pv[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < CH; ++u) {
+            if (jb + u < j1) {
+#pragma unroll
+              for (int k = 0; k < 6; ++k)
+                acc = fmaT(kv[u][k], fmaT(beta, pv[u][k], zv[u][k]), acc);
+            }
           }
         }
-        const T pi = first ? z[i] : fmaT(beta, pold[i], z[i]);
+        const T pi = fmaT(beta, pold[i], z[i]);
         pnew[i] = pi;
         ((T*)S.q)[i] = acc;
         part = (double)pi * (double)acc;
@@ -139,14 +152,24 @@ __global__ void __launch_bounds__(NT) pcg_a_kernel(const int2* __restrict__ tile
         double acc = bi;
         part_b = bi * bi;
         if (state == ST_RESID) {
-          const int j1 = __ldg(S.row_ptr + node + 1);
-          for (int j = __ldg(S.row_ptr + node); j < j1; ++j) {
-            const int c = __ldg(S.col + j);
-            double kv[6], xv[6];
-            load6(S.K64 + (size_t)j * 36 + rr * 6, kv);
-            load6(S.x + (size_t)c * 6, xv);
+          constexpr int CH = 2;
+          const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
+          for (int jb = j0; jb < j1; jb += CH) {
+            int cc[CH];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc = fma(-kv[k], xv[k], acc);
+            for (int u = 0; u < CH; ++u) cc[u] = __ldg(S.col + min(jb + u, j1 - 1));
+            double kv[CH][6], xv[CH][6];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+              load6(S.K64 + (size_t)min(jb + u, j1 - 1) * 36 + rr * 6, kv[u]);
+              load6(S.x + (size_t)cc[u] * 6, xv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u)
+              if (jb + u < j1) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) acc = fma(-kv[u][k], xv[u][k], acc);
+              }
           }
         }
         S.r64[i] = acc;
@@ -190,7 +213,7 @@ __global__ void __launch_bounds__(NT) pcg_a_kernel(const int2* __restrict__ tile
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) pcg_b_kernel(const int2* __restrict__ tiles,
+__global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ tiles,
                                                    const int* __restrict__ n_tiles_ptr,
                                                    const SysDesc* __restrict__ sys,
                                                    int* __restrict__ n_active) {
@@ -229,20 +252,28 @@ __global__ void __launch_bounds__(NT) pcg_b_kernel(const int2* __restrict__ tile
         r[i] = ri;
       }
     }
+    // preconditioner row, loaded before the barrier (independent of r)
+    const T* __restrict__ M = MatOf<T>::M(S);
+    const bool block = S.precond == SSO_BLOCK_JACOBI;
+    T mv[6];
+    if (work && act) {
+      if (block) {
+        load6(M + (size_t)node * 36 + rr * 6, mv);
+      } else {
+        mv[0] = M[i];
+      }
+    }
     s_r[t] = ri;
     __syncthreads();
     double v1 = 0.0, v2 = 0.0;
     if (work && act) {
-      const T* __restrict__ M = MatOf<T>::M(S);
       T zi;
-      if (S.precond == SSO_BLOCK_JACOBI) {
-        T mv[6];
-        load6(M + (size_t)node * 36 + rr * 6, mv);
+      if (block) {
         zi = T(0);
 #pragma unroll
         for (int k = 0; k < 6; ++k) zi = fmaT(mv[k], s_r[6 * ln + k], zi);
       } else {
-        zi = M[i] * ri;
+        zi = mv[0] * ri;
       }
       ((T*)S.z)[i] = zi;
       v1 = (double)ri * (double)zi;
@@ -286,7 +317,10 @@ __global__ void __launch_bounds__(NT) pcg_b_kernel(const int2* __restrict__ tile
             sc->status = SSO_OK;
             sc->state = ST_DONE;
             atomicSub(n_active, 1);
-          } else if (sc->iters >= sc->max_iter || sc->sweeps >= sc->max_sweeps) {
+          } else if (sc->iters >= sc->max_iter || sc->sweeps >= sc->max_sweeps ||
+                     (sc->sweeps >= 2 && rr64 > 0.0625 * sc->rr64_prev)) {
+            // cap reached, or the FP64 residual fell by less than 4x over the
+            // last sweep (rtol below what this K and FP64 can resolve)
             sc->status = SSO_ERR_NOT_CONVERGED;
             sc->state = ST_DONE;
             atomicSub(n_active, 1);
@@ -299,6 +333,7 @@ __global__ void __launch_bounds__(NT) pcg_b_kernel(const int2* __restrict__ tile
             sc->rr = s2;
             sc->rr_start = s2;
             sc->scale = ::sqrt(rr64);
+            sc->rr64_prev = rr64;
             sc->inner_thr = s2 * fmax(sc->inner_rtol2, 0.25 * sc->rtol2 * sc->ff / rr64);
             sc->inner = 0;
             sc->sweeps += 1;

@@ -43,6 +43,7 @@ struct SysScalars {
   double rr;        // ||r||^2 of the recursive (inner) residual
   double rr_start;  // ||r||^2 at the start of the sweep
   double rr64;      // ||b - K64 x||^2, FP64
+  double rr64_prev; // rr64 at the start of the previous sweep (stagnation test)
   double ff;        // ||b||^2
   double scale;     // ||b - K64 x|| at the start of the sweep (inner rhs scale)
   double inner_thr; // inner stop: rr <= inner_thr

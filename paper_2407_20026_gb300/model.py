@@ -186,6 +186,16 @@ class Batch:
             _lib.check(code)
         return [s.as_dict() for s in st]
 
+    def set_profiling(self, enable=True):
+        _lib.check(_lib.load().sso_batch_set_profiling(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """(ms in kernel A, ms in kernel B, timed (A, B) pairs) since profiling was enabled."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _lib.check(_lib.load().sso_batch_kernel_times(self._h, ctypes.byref(a), ctypes.byref(b),
+                                                      ctypes.byref(n)))
+        return a.value, b.value, n.value
+
     def gradient(self, w=None, g=None, raise_on_error=True):
         n = len(self.models)
         wa = (ctypes.c_double * n)(*([1.0] * n if w is None else [float(x) for x in w]))
