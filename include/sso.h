@@ -132,6 +132,17 @@ sso_status sso_beam_stiffness(int32_t n_beams, const double* d_xyz, const int32_
 sso_status sso_quad_stiffness(int32_t n_quads, const double* d_xyz, const int32_t* d_quad_conn,
                               const double* d_quad_props, double* d_ke, void* stream);
 
+/* y = K x and *xty = x^T y for a 6x6-block sparse K (the product K u of
+ * Eq. 1 for an assembled K, e.g. from sso_model_get_stiffness).  All pointers
+ * are DEVICE pointers: row_ptr [n_nodes+1], col [n_blocks], K [n_blocks*36]
+ * row-major FP64 blocks, x and y [6*n_nodes], xty [1].  x^T y is summed in a
+ * fixed order (bit-reproducible).  Scratch memory (8 bytes per 32 nodes) is
+ * allocated and freed stream-ordered on `stream` (cudaMallocAsync); the call
+ * only enqueues work.  Indices in col must be < n_nodes. */
+sso_status sso_bsr_spmv(int32_t n_nodes, const int32_t* d_row_ptr, const int32_t* d_col,
+                        const double* d_K, const double* d_x, double* d_y, double* d_xty,
+                        void* stream);
+
 /* ---------------------------------------------------------------------------
  * Models.  A model owns the device copy of one structure, its block-sparse
  * pattern (built once on the host from the connectivity: K's block rows are

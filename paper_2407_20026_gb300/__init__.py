@@ -6,12 +6,12 @@ call does, and fails loudly if the library has not been built.
 """
 from ._lib import SSOError  # noqa: F401
 
-__all__ = ["Model", "Batch", "options", "beam_stiffness", "quad_stiffness", "SSOError",
-           "SSOFunction", "kernel_launches"]
+__all__ = ["Model", "Batch", "options", "beam_stiffness", "quad_stiffness", "bsr_spmv",
+           "SSOError", "SSOFunction", "kernel_launches"]
 
 
 def __getattr__(name):
-    if name in ("Model", "Batch", "options", "beam_stiffness", "quad_stiffness",
+    if name in ("Model", "Batch", "options", "beam_stiffness", "quad_stiffness", "bsr_spmv",
                 "kernel_launches"):
         from . import model
         return getattr(model, name)

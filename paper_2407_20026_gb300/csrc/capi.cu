@@ -618,6 +618,29 @@ sso_status sso_quad_stiffness(int32_t n_quads, const double* d_xyz, const int32_
   return SSO_OK;
 }
 
+sso_status sso_bsr_spmv(int32_t n_nodes, const int32_t* d_row_ptr, const int32_t* d_col,
+                        const double* d_K, const double* d_x, double* d_y, double* d_xty,
+                        void* stream) {
+  if (n_nodes < 0) return fail(SSO_ERR_INVALID, "n_nodes < 0");
+  if (n_nodes == 0) return SSO_OK;
+  if (!d_row_ptr || !d_col || !d_K || !d_x || !d_y || !d_xty)
+    return fail(SSO_ERR_INVALID, "NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t tiles = (size_t)(n_nodes + TILE - 1) / TILE;
+  void* scratch = nullptr;
+  CK(cudaMallocAsync(&scratch, tiles * sizeof(double) + 256, s));
+  unsigned int* counter = (unsigned int*)((char*)scratch + align_up(tiles * sizeof(double), 16));
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess)
+    e = launch_bsr_spmv(n_nodes, d_row_ptr, d_col, d_K, d_x, d_y, d_xty, (double*)scratch,
+                        counter, s);
+  if (e == cudaSuccess) g_launches += 1;
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sso_bsr_spmv");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  return SSO_OK;
+}
+
 sso_status sso_model_create(const sso_mesh* mesh, void* stream, sso_model** out) {
   if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
   *out = nullptr;

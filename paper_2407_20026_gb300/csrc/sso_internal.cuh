@@ -112,6 +112,12 @@ cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const
 cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
                          int* n_active, int grid, cudaStream_t s);
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
+
+// Launchers (spmv.cu): y = K x, *xty = x^T y; partials [ceil(n_nodes/TILE)],
+// counter must be 0 on entry and is 0 again on exit.
+cudaError_t launch_bsr_spmv(int n_nodes, const int* row_ptr, const int* col, const double* K,
+                            const double* x, double* y, double* xty, double* partials,
+                            unsigned int* counter, cudaStream_t s);
 int pcg_grid_limit(bool fp64);
 
 }  // namespace sso

@@ -239,3 +239,18 @@ def quad_stiffness(xyz, conn, props, stream=None):
                                               props.data_ptr(), out.data_ptr(),
                                               ctypes.c_void_p(_stream_ptr(stream))))
     return out
+
+
+def bsr_spmv(row_ptr, col, K, x, stream=None):
+    """y = K x and x^T y for 6x6-block sparse K (CUDA tensors): returns (y, xty)."""
+    row_ptr = row_ptr.to(torch.int32).contiguous()
+    col = col.to(torch.int32).contiguous()
+    K = K.to(torch.float64).contiguous()
+    x = x.to(torch.float64).contiguous()
+    n = row_ptr.shape[0] - 1
+    y = torch.empty(6 * n, dtype=torch.float64, device=x.device)
+    xty = torch.empty(1, dtype=torch.float64, device=x.device)
+    _lib.check(_lib.load().sso_bsr_spmv(n, row_ptr.data_ptr(), col.data_ptr(), K.data_ptr(),
+                                        x.data_ptr(), y.data_ptr(), xty.data_ptr(),
+                                        ctypes.c_void_p(_stream_ptr(stream))))
+    return y, xty

@@ -250,3 +250,33 @@ def test_autograd_function(sso, orc):
     ref = orc.gradient(m, w=0.7, g=gvec.cpu().numpy())
     assert rel(z.grad.cpu().numpy(), ref["dz"]) <= TOL_FP64
     assert rel(t.grad.cpu().numpy(), ref["dt"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("name", ["gridshell13", "c1"])
+def test_bsr_spmv_entry_point(sso, name):
+    """y = K x and x^T y of the assembled K vs a plain FP64 product; the
+    fixed-order dot is bit-identical across calls."""
+    m = meshgen.shell(64) if name == "c1" else MODELS[name]()
+    mdl = sso.Model(m)
+    try:
+        mdl.solve(precision="fp64", max_iter=10)
+    except sso.SSOError:
+        pass  # only the assembled K is needed
+    rp, col, K64, _ = mdl.stiffness()
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=6 * mdl.n_nodes)
+    n = mdl.n_nodes
+    y_ref = np.zeros(6 * n)
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            y_ref[6 * i:6 * i + 6] += K64[k] @ x[6 * col[k]:6 * col[k] + 6]
+    dev = "cuda"
+    args = (torch.tensor(rp, device=dev), torch.tensor(col, device=dev),
+            torch.tensor(K64, device=dev), torch.tensor(x, device=dev))
+    y1, d1 = sso.bsr_spmv(*args)
+    y2, d2 = sso.bsr_spmv(*args)
+    torch.cuda.synchronize()
+    y1 = y1.cpu().numpy()
+    assert np.abs(y1 - y_ref).max() <= 1e-13 * np.abs(y_ref).max()
+    assert float(d1) == pytest.approx(float(x @ y_ref), rel=1e-12)
+    assert np.array_equal(y1, y2.cpu().numpy()) and float(d1) == float(d2)
