@@ -77,6 +77,7 @@ SIGNATURES = {
     "sso_beam_stiffness": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "sso_quad_stiffness": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "sso_bsr_spmv": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sso_bsr_spmv_noalloc": ([_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "sso_model_create": ([ctypes.POINTER(Mesh), _vp, ctypes.POINTER(_vp)], _i32),
     "sso_model_destroy": ([_vp], None),
     "sso_model_set_design": ([_vp, _vp, _vp], _i32),

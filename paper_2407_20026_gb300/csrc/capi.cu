@@ -574,6 +574,11 @@ sso_status ensure_self_batch(sso_model* M) {
 
 }  // namespace
 
+namespace sso {
+sso_status record_failure(sso_status st, const char* msg) { return fail(st, msg); }
+void count_launches(unsigned long long n) { g_launches += n; }
+}  // namespace sso
+
 // ===========================================================================
 extern "C" {
 
