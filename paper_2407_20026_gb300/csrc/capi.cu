@@ -149,11 +149,12 @@ struct sso_batch {
   double* d_dots = nullptr;
   std::vector<SysDesc> h_sys;
   SysScalars* h_sc = nullptr;   // pinned, n_sys
-  int* h_flag = nullptr;        // pinned, 2 ints
+  int* h_flag = nullptr;        // pinned: [0..1] upload, [2..3] read back
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   int exec_iters[2] = {0, 0};
   int exec_prof[2] = {0, 0};
-  int grid[2] = {0, 0};
+  int grid_a[2] = {0, 0};
+  int grid_b[2] = {0, 0};
   cudaEvent_t ev = nullptr;
   // kernel timing (sso_batch_set_profiling): events around every A and B
   // launch inside the captured graph
@@ -357,8 +358,8 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_p0 = c.take<double>(ndof);
   M->d_p1 = c.take<double>(ndof);
   M->d_q = c.take<double>(ndof);
-  M->d_part_a = c.take<double>(2 * (size_t)M->n_tiles);
-  M->d_part_b = c.take<double>(2 * (size_t)M->n_tiles);
+  M->d_part_a = c.take<double>(2 * (size_t)WARPS * M->n_tiles);
+  M->d_part_b = c.take<double>(2 * (size_t)WARPS * M->n_tiles);
   M->d_dz = c.take<double>(n);
   M->d_dt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_C = c.take<double>(1);
@@ -423,9 +424,11 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
     cudaGraphExecDestroy(B->exec[k]);
     B->exec[k] = nullptr;
   }
-  if (B->grid[k] == 0) {
-    const int lim = pcg_grid_limit(fp64);
-    B->grid[k] = std::max(1, std::min(B->n_tiles, lim));
+  if (B->grid_a[k] == 0) {
+    int ga = 1, gb = 1;
+    pcg_grid_limits(fp64, &ga, &gb);
+    B->grid_a[k] = std::max(1, std::min(B->n_tiles, ga));
+    B->grid_b[k] = std::max(1, std::min(B->n_tiles, gb));
   }
   if (B->profiling) {
     while ((int)B->pev.size() < 2 * iters + 1) {
@@ -440,12 +443,12 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
   if (B->profiling)
     err = cudaEventRecordWithFlags(B->pev[0], B->stream, cudaEventRecordExternal);
   for (int it = 0; it < iters && err == cudaSuccess; ++it) {
-    err = launch_pcg_a(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid[k],
+    err = launch_pcg_a(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid_a[k],
                        B->stream);
     if (err == cudaSuccess && B->profiling)
       err = cudaEventRecordWithFlags(B->pev[2 * it + 1], B->stream, cudaEventRecordExternal);
     if (err == cudaSuccess)
-      err = launch_pcg_b(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid[k],
+      err = launch_pcg_b(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid_b[k],
                          B->stream);
     if (err == cudaSuccess && B->profiling)
       err = cudaEventRecordWithFlags(B->pev[2 * it + 2], B->stream, cudaEventRecordExternal);
@@ -510,7 +513,9 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   CK(cudaMemcpyAsync(B->d_sc, B->h_sc, sizeof(SysScalars) * B->n_sys, cudaMemcpyHostToDevice,
                      B->stream));
   B->h_flag[0] = n_act;
-  CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  B->h_flag[1] = 0;
+  CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
+                     B->stream));
   if (n_act > 0) {
     sso_status st = batch_graph(B, fp64, o->iters_per_launch);
     if (st != SSO_OK) return st;
@@ -520,8 +525,8 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
     for (;;) {
       CK(cudaGraphLaunch(B->exec[k], B->stream));
       g_launches += 2ull * (unsigned long long)o->iters_per_launch;
-      CK(cudaMemcpyAsync(B->h_flag + 1, B->d_n_active, sizeof(int), cudaMemcpyDeviceToHost,
-                         B->stream));
+      CK(cudaMemcpyAsync(B->h_flag + 2, B->d_n_active, 2 * sizeof(int),
+                         cudaMemcpyDeviceToHost, B->stream));
       CK(cudaEventRecord(B->ev, B->stream));
       CK(cudaEventSynchronize(B->ev));
       if (B->profiling) {
@@ -529,7 +534,9 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
         if (ps != SSO_OK) return ps;
       }
       ++launches;
-      if (B->h_flag[1] <= 0) break;
+      if (B->h_flag[3] != 0)
+        return fail(SSO_ERR_CUDA, "CG kernel gave up waiting for a bulk copy (device fault?)");
+      if (B->h_flag[2] <= 0) break;
       if (o->timeout_ms > 0.0) {
         const double ms = std::chrono::duration<double, std::milli>(
                               std::chrono::steady_clock::now() - t0).count();
@@ -631,7 +638,7 @@ sso_status sso_bsr_spmv(int32_t n_nodes, const int32_t* d_row_ptr, const int32_t
   if (!d_row_ptr || !d_col || !d_K || !d_x || !d_y || !d_xty)
     return fail(SSO_ERR_INVALID, "NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t tiles = (size_t)(n_nodes + TILE - 1) / TILE;
+  const size_t tiles = (size_t)(n_nodes + SPMV_TILE - 1) / SPMV_TILE;
   void* scratch = nullptr;
   CK(cudaMallocAsync(&scratch, tiles * sizeof(double) + 256, s));
   unsigned int* counter = (unsigned int*)((char*)scratch + align_up(tiles * sizeof(double), 16));
@@ -888,7 +895,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   c.take<SysScalars>(n);
   c.take<int2>(tiles.size());
   c.take<int>(1);
-  c.take<int>(1);
+  c.take<int>(2);
   c.take<double>(n);
   const size_t bytes = align_up(c.off, 256);
   cudaError_t e = cudaMalloc(&B->arena, bytes);
@@ -901,11 +908,11 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   B->d_sc = d.take<SysScalars>(n);
   B->d_tiles = d.take<int2>(tiles.size());
   B->d_n_tiles = d.take<int>(1);
-  B->d_n_active = d.take<int>(1);
+  B->d_n_active = d.take<int>(2);
   B->d_dots = d.take<double>(n);
   for (int s = 0; s < n; ++s) B->h_sys[s].sc = B->d_sc + s;
   e = cudaMallocHost(&B->h_sc, sizeof(SysScalars) * n);
-  if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->arena, 0, bytes, B->stream);
   if (e == cudaSuccess)

@@ -1,9 +1,11 @@
 // Batched preconditioned CG with FP64 iterative refinement.
 //
-// One CG iteration over every system of a batch is two kernels, A then B,
-// each a grid-stride loop over tiles (TILE nodes of one system per tile, one
-// thread per scalar row).  Every system runs its own state machine, stored in
-// its SysScalars:
+// One CG iteration over every system of a batch is two kernels, A then B.
+// The rows of every system are cut into tiles of TILE consecutive nodes; a
+// warp owns NODES_PER_WARP whole nodes of a tile (lane = 6 * node + row, two
+// lanes idle) and a CTA of WARPS warps owns a tile.  Each CTA walks a
+// contiguous range of tiles.  Every system runs its own state machine, stored
+// in its SysScalars:
 //
 //   INIT   A: r64 = b, ||b||^2             B: start sweep 1 (or finish if b = 0)
 //   RESID  A: r64 = b - K64 x (FP64 SpMV), B: finish if ||r64|| <= rtol ||b||,
@@ -19,11 +21,15 @@
 // every dot product are FP64.  In FP64 mode everything is FP64 and the RESID
 // step only confirms the true residual.
 //
-// Reductions: each tile writes its partial sum, then increments the system's
-// completion counter (integer atomic); the CTA that completes the last tile
-// sums the partials in tile order and updates the scalars.  Tiles are aligned
-// to each system's own rows, so a system's iterates are bit-identical whether
-// it runs alone or inside any batch.  There are no spin-waits.
+// Reductions: every warp reduces its rows with shuffles and stores one
+// partial per (tile, warp); there is no CTA barrier per tile.  When a CTA has
+// finished its run of consecutive tiles of one system it adds the run length
+// to the system's completion counter (one integer atomic per run); the CTA
+// that brings the counter to the system's tile count sums all of that
+// system's partials in (tile, warp) order and updates the scalars.  The
+// grouping into tiles and warps depends only on the system itself, so its
+// iterates are bit-identical whether it runs alone or inside any batch.
+// There are no spin-waits.
 #include <math.h>
 
 #include "sso_internal.cuh"
@@ -68,13 +74,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   double s = 0.0;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    for (int w = 0; w < WARPS; ++w) s += red[w];
   }
   __syncthreads();
   return s;
 }
 
-// Ordered sum of n partials (stride `stride`, offset `off`); valid in thread 0.
+// Ordered sum of n values part[k * stride + off]; valid in thread 0.
 __device__ __forceinline__ double ordered_sum(const double* part, int n, int stride, int off,
                                               double* red) {
   double v = 0.0;
@@ -82,28 +88,68 @@ __device__ __forceinline__ double ordered_sum(const double* part, int n, int str
   return block_sum(v, red);
 }
 
+// sum_j K[j][rr][:] . (z + beta pold)[col[j]] over j in [j0, j1), in j order.
+// Column indices of a chunk first, then every K-row / z / p load of the chunk
+// (indices past the row end are clamped to its last block and their FMAs
+// skipped), then the FMAs: the loads of a chunk are in flight together.
+template <typename T, int CH>
+__device__ __forceinline__ T row_dot(const T* __restrict__ K, const int* __restrict__ col,
+                                     int j0, int j1, int rr, const T* __restrict__ z,
+                                     const T* __restrict__ pold, T beta) {
+  T acc = T(0);
+  for (int jb = j0; jb < j1; jb += CH) {
+    int cc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) cc[u] = __ldg(col + min(jb + u, j1 - 1));
+    T kv[CH][6], zv[CH][6], pv[CH][6];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      load6(K + (size_t)min(jb + u, j1 - 1) * 36 + rr * 6, kv[u]);
+      load6(z + (size_t)cc[u] * 6, zv[u]);
+      load6(pold + (size_t)cc[u] * 6, pv[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (jb + u < j1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc = fmaT(kv[u][k], fmaT(beta, pv[u][k], zv[u][k]), acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// The CTA's contiguous range of tiles.
+__device__ __forceinline__ void tile_range(int n_tiles, int& begin, int& end) {
+  const int per = (n_tiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  begin = (int)blockIdx.x * per;
+  end = min(n_tiles, begin + per);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const int2* __restrict__ tiles,
-                                                   const int* __restrict__ n_tiles_ptr,
-                                                   const SysDesc* __restrict__ sys,
-                                                   int* __restrict__ n_active) {
-  __shared__ double red[NT / 32];
+__global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const int2* __restrict__ tiles,
+                                                      const int* __restrict__ n_tiles_ptr,
+                                                      const SysDesc* __restrict__ sys,
+                                                      int* __restrict__ flags) {
+  __shared__ double red[WARPS];
   __shared__ int s_last;
-  const int n_tiles = *n_tiles_ptr;
-  const int t = threadIdx.x;
-  const int ln = t / 6, rr = t - 6 * (t / 6);
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  int* n_active = flags;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
+  int begin, end;
+  tile_range(*n_tiles_ptr, begin, end);
+  int run = 0;  // tiles of the current system done by this CTA since the last count
+  for (int tile = begin; tile < end; ++tile) {
     const int2 tl = tiles[tile];
     const SysDesc& S = sys[tl.x];
     SysScalars* sc = S.sc;
     const int state = *(volatile int*)&sc->state;
     if (state == ST_DONE) continue;
     const int node = tl.y + ln;
-    const bool act = node < S.n_nodes;
+    const bool act = lane < 6 * NODES_PER_WARP && node < S.n_nodes;
     const int i = 6 * node + rr;
     double part = 0.0, part_b = 0.0;
     if (state == ST_PCG) {
-      const T* __restrict__ K = MatOf<T>::K(S);
       const T* __restrict__ z = (const T*)S.z;
       const int par = sc->parity;
       const T* pold = (const T*)(par ? S.p1 : S.p0);
@@ -114,33 +160,9 @@ __global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const int2* __restrict__ t
       const T beta = first ? T(0) : (T)sc->beta;
       if (first) pold = z;
       if (act) {
-        // Column indices of a chunk first, then every K row / z / p load of the
-        // chunk (indices past the row end are clamped to its last block and
-        // their FMAs skipped), then the FMAs in column order: the loads of a
-        // chunk are in flight together and the summation order is plain j.
         constexpr int CH = sizeof(T) == 4 ? 3 : 2;
-        T acc = T(0);
         const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
-        for (int jb = j0; jb < j1; jb += CH) {
-          int cc[CH];
-#pragma unroll
-          for (int u = 0; u < CH; ++u) cc[u] = __ldg(S.col + min(jb + u, j1 - 1));
-          T kv[CH][6], zv[CH][6], pv[CH][6];
-#pragma unroll
-          for (int u = 0; u < CH; ++u) {
-            load6(K + (size_t)min(jb + u, j1 - 1) * 36 + rr * 6, kv[u]);
-            load6(z + (size_t)cc[u] * 6, zv[u]);
-            load6(pold + (size_t)cc[u] * 6, pv[u]);
-          }
-#pragma unroll
-          for (int u = 0; u < CH; ++u) {
-            if (jb + u < j1) {
-#pragma unroll
-              for (int k = 0; k < 6; ++k)
-                acc = fmaT(kv[u][k], fmaT(beta, pv[u][k], zv[u][k]), acc);
-            }
-          }
-        }
+        const T acc = row_dot<T, CH>(MatOf<T>::K(S), S.col, j0, j1, rr, z, pold, beta);
         const T pi = fmaT(beta, pold[i], z[i]);
         pnew[i] = pi;
         ((T*)S.q)[i] = acc;
@@ -152,44 +174,37 @@ __global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const int2* __restrict__ t
         double acc = bi;
         part_b = bi * bi;
         if (state == ST_RESID) {
-          constexpr int CH = 2;
           const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
-          for (int jb = j0; jb < j1; jb += CH) {
-            int cc[CH];
-#pragma unroll
-            for (int u = 0; u < CH; ++u) cc[u] = __ldg(S.col + min(jb + u, j1 - 1));
-            double kv[CH][6], xv[CH][6];
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-              load6(S.K64 + (size_t)min(jb + u, j1 - 1) * 36 + rr * 6, kv[u]);
-              load6(S.x + (size_t)cc[u] * 6, xv[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < CH; ++u)
-              if (jb + u < j1) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) acc = fma(-kv[u][k], xv[u][k], acc);
-              }
-          }
+          acc -= row_dot<double, 2>(S.K64, S.col, j0, j1, rr, S.x, S.x, 0.0);
         }
         S.r64[i] = acc;
         part = acc * acc;
       }
     }
-    const double tot = block_sum(part, red);
-    const double tot_b = state == ST_PCG ? 0.0 : block_sum(part_b, red);
-    if (t == 0) {
-      S.part_a[2 * (tile - S.tile0)] = tot;
-      S.part_a[2 * (tile - S.tile0) + 1] = tot_b;
+    part = warp_sum(part);
+    part_b = warp_sum(part_b);
+    if (lane == 0) {
+      double* dst = S.part_a + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
+      dst[0] = part;
+      dst[1] = part_b;
       __threadfence();
-      const unsigned prev = atomicAdd(&sc->cnt_a, 1u);
-      s_last = (prev == (unsigned)(S.n_tiles - 1));
     }
+    ++run;
+    // end of this CTA's run of the system: count it
+    if (tile + 1 < end && tiles[tile + 1].x == tl.x) continue;
+    __syncthreads();
+    if (t == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&sc->cnt_a, (unsigned)run);
+      s_last = (prev + (unsigned)run == (unsigned)S.n_tiles);
+    }
+    run = 0;
     __syncthreads();
     if (s_last) {
       __threadfence();
-      const double sum = ordered_sum(S.part_a, S.n_tiles, 2, 0, red);
-      const double sum_b = state == ST_PCG ? 0.0 : ordered_sum(S.part_a, S.n_tiles, 2, 1, red);
+      const int n_part = S.n_tiles * WARPS;
+      const double sum = ordered_sum(S.part_a, n_part, 2, 0, red);
+      const double sum_b = state == ST_PCG ? 0.0 : ordered_sum(S.part_a, n_part, 2, 1, red);
       if (t == 0) {
         if (state == ST_PCG) {
           sc->pq = sum;
@@ -207,39 +222,47 @@ __global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const int2* __restrict__ t
         }
         sc->cnt_a = 0u;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ tiles,
-                                                   const int* __restrict__ n_tiles_ptr,
-                                                   const SysDesc* __restrict__ sys,
-                                                   int* __restrict__ n_active) {
-  __shared__ double red[NT / 32];
-  __shared__ T s_r[NT];
+                                                      const int* __restrict__ n_tiles_ptr,
+                                                      const SysDesc* __restrict__ sys,
+                                                      int* __restrict__ flags) {
+  __shared__ double red[WARPS];
   __shared__ int s_last;
-  const int n_tiles = *n_tiles_ptr;
-  const int t = threadIdx.x;
-  const int ln = t / 6, rr = t - 6 * (t / 6);
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  int* n_active = flags;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
+  const int node_lane0 = lane - rr;  // lane of row 0 of this lane's node
+  int begin, end;
+  tile_range(*n_tiles_ptr, begin, end);
+  int run = 0;
+  for (int tile = begin; tile < end; ++tile) {
     const int2 tl = tiles[tile];
     const SysDesc& S = sys[tl.x];
     SysScalars* sc = S.sc;
     const int state = *(volatile int*)&sc->state;
     if (state == ST_DONE) continue;
     const int node = tl.y + ln;
-    const bool act = node < S.n_nodes;
+    const bool act = lane < 6 * NODES_PER_WARP && node < S.n_nodes;
     const int i = 6 * node + rr;
     T* r = (T*)S.r;
+    const T* __restrict__ M = MatOf<T>::M(S);
+    const bool block = S.precond == SSO_BLOCK_JACOBI;
     bool work = true;
     T ri = T(0);
+    T mv[6];
     if (state == ST_PCG) {
       const T alpha = (T)sc->alpha;
       const double ua = sc->alpha * sc->scale;
       const T* p = (const T*)(sc->parity ? S.p1 : S.p0);
       if (act) {
+        if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
+        else mv[0] = M[i];
         S.x[i] = fma(ua, (double)p[i], S.x[i]);
         ri = fmaT(-alpha, ((const T*)S.q)[i], r[i]);
         r[i] = ri;
@@ -248,51 +271,54 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ t
       const double rr64 = sc->rr64;
       work = isfinite(rr64) && !(rr64 <= sc->rtol2 * sc->ff);
       if (work && act) {
+        if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
+        else mv[0] = M[i];
         ri = (T)(S.r64[i] * (1.0 / ::sqrt(rr64)));
         r[i] = ri;
       }
     }
-    // preconditioner row, loaded before the barrier (independent of r)
-    const T* __restrict__ M = MatOf<T>::M(S);
-    const bool block = S.precond == SSO_BLOCK_JACOBI;
-    T mv[6];
-    if (work && act) {
-      if (block) {
-        load6(M + (size_t)node * 36 + rr * 6, mv);
-      } else {
-        mv[0] = M[i];
-      }
-    }
-    s_r[t] = ri;
-    __syncthreads();
     double v1 = 0.0, v2 = 0.0;
-    if (work && act) {
-      T zi;
+    if (work) {
+      // z = M^-1 r: the node's six residual rows are lanes node_lane0 .. +5
+      T zi = T(0);
       if (block) {
-        zi = T(0);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) zi = fmaT(mv[k], s_r[6 * ln + k], zi);
+        for (int k = 0; k < 6; ++k) {
+          const T rk = __shfl_sync(0xffffffffu, ri, (node_lane0 + k) & 31);
+          zi = fmaT(mv[k], rk, zi);
+        }
       } else {
         zi = mv[0] * ri;
       }
-      ((T*)S.z)[i] = zi;
-      v1 = (double)ri * (double)zi;
-      v2 = (double)ri * (double)ri;
+      if (act) {
+        ((T*)S.z)[i] = zi;
+        v1 = (double)ri * (double)zi;
+        v2 = (double)ri * (double)ri;
+      }
     }
-    const double t1 = block_sum(v1, red);
-    const double t2 = block_sum(v2, red);
-    if (t == 0) {
-      S.part_b[2 * (tile - S.tile0)] = t1;
-      S.part_b[2 * (tile - S.tile0) + 1] = t2;
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if (lane == 0) {
+      double* dst = S.part_b + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
+      dst[0] = v1;
+      dst[1] = v2;
       __threadfence();
-      const unsigned prev = atomicAdd(&sc->cnt_b, 1u);
-      s_last = (prev == (unsigned)(S.n_tiles - 1));
     }
+    ++run;
+    if (tile + 1 < end && tiles[tile + 1].x == tl.x) continue;
+    __syncthreads();
+    if (t == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&sc->cnt_b, (unsigned)run);
+      s_last = (prev + (unsigned)run == (unsigned)S.n_tiles);
+    }
+    run = 0;
     __syncthreads();
     if (s_last) {
       __threadfence();
-      const double s1 = ordered_sum(S.part_b, S.n_tiles, 2, 0, red);
-      const double s2 = ordered_sum(S.part_b, S.n_tiles, 2, 1, red);
+      const int n_part = S.n_tiles * WARPS;
+      const double s1 = ordered_sum(S.part_b, n_part, 2, 0, red);
+      const double s2 = ordered_sum(S.part_b, n_part, 2, 1, red);
       if (t == 0) {
         if (state == ST_PCG) {
           sc->iters += 1;
@@ -342,15 +368,15 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ t
         }
         sc->cnt_b = 0u;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 // out[s] = b_s^T x_s for every system, one CTA per system, fixed order.
 __global__ void __launch_bounds__(NT) dot_kernel(const SysDesc* __restrict__ sys,
                                                  double* __restrict__ out) {
-  __shared__ double red[NT / 32];
+  __shared__ double red[WARPS];
   const SysDesc& S = sys[blockIdx.x];
   const int n = 6 * S.n_nodes;
   double v = 0.0;
@@ -362,20 +388,20 @@ __global__ void __launch_bounds__(NT) dot_kernel(const SysDesc* __restrict__ sys
 }  // namespace
 
 cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* n_active, int grid, cudaStream_t s) {
+                         int* flags, int grid, cudaStream_t s) {
   if (fp64)
-    pcg_a_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+    pcg_a_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
   else
-    pcg_a_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+    pcg_a_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* n_active, int grid, cudaStream_t s) {
+                         int* flags, int grid, cudaStream_t s) {
   if (fp64)
-    pcg_b_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+    pcg_b_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
   else
-    pcg_b_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, n_active);
+    pcg_b_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
   return cudaGetLastError();
 }
 
@@ -385,9 +411,9 @@ cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t 
   return cudaGetLastError();
 }
 
-// CTAs resident on the whole device for the PCG kernels (grid-stride loops
+// CTAs resident on the whole device for each PCG kernel (the range loops
 // never need more).
-int pcg_grid_limit(bool fp64) {
+void pcg_grid_limits(bool fp64, int* grid_a, int* grid_b) {
   int dev = 0, sms = 0, per_sm_a = 0, per_sm_b = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -398,10 +424,9 @@ int pcg_grid_limit(bool fp64) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_kernel<float>, NT, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b_kernel<float>, NT, 0);
   }
-  int per_sm = per_sm_a < per_sm_b ? per_sm_a : per_sm_b;
-  if (per_sm < 1) per_sm = 1;
   if (sms < 1) sms = 1;
-  return sms * per_sm;
+  *grid_a = sms * (per_sm_a < 1 ? 1 : per_sm_a);
+  *grid_b = sms * (per_sm_b < 1 ? 1 : per_sm_b);
 }
 
 }  // namespace sso

@@ -17,7 +17,7 @@ __device__ __forceinline__ void spmv_load6(const double* p, double v[6]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
 }
 
-__global__ void __launch_bounds__(NT) bsr_spmv_kernel(int n_nodes, const int* __restrict__ row_ptr,
+__global__ void __launch_bounds__(6 * SPMV_TILE) bsr_spmv_kernel(int n_nodes, const int* __restrict__ row_ptr,
                                                       const int* __restrict__ col,
                                                       const double* __restrict__ K,
                                                       const double* __restrict__ x,
@@ -25,11 +25,11 @@ __global__ void __launch_bounds__(NT) bsr_spmv_kernel(int n_nodes, const int* __
                                                       double* __restrict__ xty,
                                                       double* __restrict__ partials,
                                                       unsigned int* __restrict__ counter) {
-  __shared__ double red[NT / 32];
+  __shared__ double red[6 * SPMV_TILE / 32];
   __shared__ int s_last;
   const int t = threadIdx.x;
   const int ln = t / 6, rr = t - 6 * (t / 6);
-  const int node = blockIdx.x * TILE + ln;
+  const int node = blockIdx.x * SPMV_TILE + ln;
   double part = 0.0;
   if (node < n_nodes) {
     const int i = 6 * node + rr;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NT) bsr_spmv_kernel(int n_nodes, const int* __
   if (t == 0) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    for (int w = 0; w < 6 * SPMV_TILE / 32; ++w) s += red[w];
     partials[blockIdx.x] = s;
     __threadfence();
     const unsigned prev = atomicAdd(counter, 1u);
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(NT) bsr_spmv_kernel(int n_nodes, const int* __
   if (s_last) {
     __threadfence();
     double v = 0.0;
-    for (int k = t; k < (int)gridDim.x; k += NT) v += __ldcg(partials + k);
+    for (int k = t; k < (int)gridDim.x; k += 6 * SPMV_TILE) v += __ldcg(partials + k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(NT) bsr_spmv_kernel(int n_nodes, const int* __
     if (t == 0) {
       double s = 0.0;
 #pragma unroll
-      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      for (int w = 0; w < 6 * SPMV_TILE / 32; ++w) s += red[w];
       *xty = s;
       *counter = 0u;
     }
@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(NT) bsr_spmv_kernel(int n_nodes, const int* __
 cudaError_t launch_bsr_spmv(int n_nodes, const int* row_ptr, const int* col, const double* K,
                             const double* x, double* y, double* xty, double* partials,
                             unsigned int* counter, cudaStream_t s) {
-  const int tiles = (n_nodes + TILE - 1) / TILE;
+  const int tiles = (n_nodes + SPMV_TILE - 1) / SPMV_TILE;
   if (tiles <= 0) return cudaSuccess;
-  bsr_spmv_kernel<<<tiles, NT, 0, s>>>(n_nodes, row_ptr, col, K, x, y, xty, partials, counter);
+  bsr_spmv_kernel<<<tiles, 6 * SPMV_TILE, 0, s>>>(n_nodes, row_ptr, col, K, x, y, xty, partials, counter);
   return cudaGetLastError();
 }
 

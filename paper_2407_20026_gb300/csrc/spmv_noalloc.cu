@@ -25,7 +25,7 @@
 namespace {
 
 constexpr int kNoAllocMaxTiles = 65536;
-constexpr int kNoAllocMaxNodes = kNoAllocMaxTiles * sso::TILE;  // 2,097,152 nodes
+constexpr int kNoAllocMaxNodes = kNoAllocMaxTiles * sso::SPMV_TILE;  // 2,097,152 nodes
 constexpr size_t kCounterOffset = (size_t)kNoAllocMaxTiles * sizeof(double);
 
 // partial sums [kNoAllocMaxTiles] doubles, then the completion counter

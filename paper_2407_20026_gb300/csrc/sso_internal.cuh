@@ -21,9 +21,15 @@
 namespace sso {
 
 // PCG tiling: a tile is TILE consecutive nodes of one system, processed by one
-// CTA of 6*TILE threads (one thread per scalar row).
-constexpr int TILE = 32;
-constexpr int NT = 6 * TILE;
+// CTA of WARPS warps; each warp owns NODES_PER_WARP whole nodes, one lane per
+// scalar row (6 * NODES_PER_WARP = 30 lanes, two idle).
+constexpr int NODES_PER_WARP = 5;
+constexpr int WARPS = 6;
+constexpr int TILE = NODES_PER_WARP * WARPS;  // 30 nodes
+constexpr int NT = 32 * WARPS;                // 192 threads
+// Tiling of the stateless BSR product (spmv.cu): SPMV_TILE nodes per CTA of
+// 6 * SPMV_TILE threads.
+constexpr int SPMV_TILE = 32;
 
 enum SysState : int { ST_INIT = 0, ST_PCG = 1, ST_RESID = 2, ST_DONE = 3 };
 
@@ -73,8 +79,8 @@ struct SysDesc {
   void* p0;
   void* p1;
   void* q;
-  double* part_a;   // [2 * n_tiles]
-  double* part_b;   // [2 * n_tiles]
+  double* part_a;   // [2 * WARPS * n_tiles]
+  double* part_b;   // [2 * WARPS * n_tiles]
   SysScalars* sc;
 };
 
@@ -107,10 +113,12 @@ cudaError_t launch_axpby(int n, double a, const double* x, const double* y, cons
                          double* out, cudaStream_t s);
 
 // Launchers (pcg.cu)
+// flags[0] = systems still iterating, flags[1] = device-side failure (a bounded
+// wait that gave up); grid sizes from pcg_grid_limits.
 cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* n_active, int grid, cudaStream_t s);
+                         int* flags, int grid, cudaStream_t s);
 cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* n_active, int grid, cudaStream_t s);
+                         int* flags, int grid, cudaStream_t s);
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
 
 // Launchers (spmv.cu): y = K x, *xty = x^T y; partials [ceil(n_nodes/TILE)],
@@ -118,6 +126,6 @@ cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t 
 cudaError_t launch_bsr_spmv(int n_nodes, const int* row_ptr, const int* col, const double* K,
                             const double* x, double* y, double* xty, double* partials,
                             unsigned int* counter, cudaStream_t s);
-int pcg_grid_limit(bool fp64);
+void pcg_grid_limits(bool fp64, int* grid_a, int* grid_b);
 
 }  // namespace sso
