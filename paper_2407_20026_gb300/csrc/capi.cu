@@ -143,7 +143,7 @@ struct sso_batch {
   void* arena = nullptr;
   SysDesc* d_sys = nullptr;
   SysScalars* d_sc = nullptr;
-  int2* d_tiles = nullptr;
+  TileDesc* d_tiles = nullptr;
   int* d_n_tiles = nullptr;
   int* d_n_active = nullptr;
   double* d_dots = nullptr;
@@ -573,6 +573,35 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   return first_bad;
 }
 
+// Tile k of model M (system s of a batch): its block range, the aligned runs
+// of column indices and row_ptr entries, and the node range (halo) of the
+// vector entries its rows read; stage = 1 when all of it fits the FP32
+// staging buffers of kernel A.
+TileDesc make_tile(const sso_model* M, int s, int k) {
+  TileDesc d;
+  d.sys = s;
+  d.node0 = k * TILE;
+  d.nn = std::min(TILE, M->n_nodes - d.node0);
+  d.j0 = M->h_row_ptr[d.node0];
+  const int j1 = M->h_row_ptr[d.node0 + d.nn];
+  d.nblk = j1 - d.j0;
+  d.cb = d.j0 & ~3;
+  d.ncb = ((j1 + 3) & ~3) - d.cb;
+  int lo = M->n_nodes, hi = -1;
+  for (int b = d.j0; b < j1; ++b) {
+    lo = std::min(lo, M->h_col[b]);
+    hi = std::max(hi, M->h_col[b]);
+  }
+  d.vlo = hi >= 0 ? (lo & ~1) : 0;
+  d.nv = hi >= 0 ? ((hi | 1) - d.vlo + 1) : 0;
+  d.rb = d.node0 & ~3;
+  d.nrb = ((d.node0 + d.nn + 1 + 3) & ~3) - d.rb;
+  d.stage = d.nblk > 0 && d.nv > 0 && (long long)d.nblk * 144 <= STAGE_SLAB_K &&
+            d.ncb * 4 <= STAGE_SLAB_C && (long long)d.nv * 24 <= STAGE_SLAB_V &&
+            d.nrb * 4 <= STAGE_SLAB_R;
+  return d;
+}
+
 sso_status ensure_self_batch(sso_model* M) {
   if (M->self_batch) return SSO_OK;
   sso_model* ms[1] = {M};
@@ -862,7 +891,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   B->models.assign(models, models + n);
   B->stream = models[0]->stream;
   B->n_sys = n;
-  std::vector<int2> tiles;
+  std::vector<TileDesc> tiles;
   B->h_sys.resize(n);
   for (int s = 0; s < n; ++s) {
     sso_model* M = models[s];
@@ -887,13 +916,13 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     D.q = M->d_q;
     D.part_a = M->d_part_a;
     D.part_b = M->d_part_b;
-    for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_int2(s, k * TILE));
+    for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_tile(M, s, k));
   }
   B->n_tiles = (int)tiles.size();
   Carver c(nullptr);
   c.take<SysDesc>(n);
   c.take<SysScalars>(n);
-  c.take<int2>(tiles.size());
+  c.take<TileDesc>(tiles.size());
   c.take<int>(1);
   c.take<int>(2);
   c.take<double>(n);
@@ -906,7 +935,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   Carver d(B->arena);
   B->d_sys = d.take<SysDesc>(n);
   B->d_sc = d.take<SysScalars>(n);
-  B->d_tiles = d.take<int2>(tiles.size());
+  B->d_tiles = d.take<TileDesc>(tiles.size());
   B->d_n_tiles = d.take<int>(1);
   B->d_n_active = d.take<int>(2);
   B->d_dots = d.take<double>(n);
@@ -916,7 +945,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->arena, 0, bytes, B->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_tiles, tiles.data(), tiles.size() * sizeof(int2),
+    e = cudaMemcpyAsync(B->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc),
                         cudaMemcpyHostToDevice, B->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(B->d_n_tiles, &B->n_tiles, sizeof(int), cudaMemcpyHostToDevice,

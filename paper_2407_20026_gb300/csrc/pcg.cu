@@ -126,8 +126,58 @@ __device__ __forceinline__ void tile_range(int n_tiles, int& begin, int& end) {
   end = min(n_tiles, begin + per);
 }
 
+// Dynamic state of one system as the kernels of one launch see it: it only
+// changes at the very end of a launch (by the CTA that completes the system),
+// so a CTA reads it once per run of consecutive tiles of that system.
+struct RunState {
+  int state;
+  int parity;
+  int first;
+  double beta, alpha, scale, rr64, ff, rtol2;
+};
+
+__device__ __forceinline__ RunState read_state(const SysScalars* sc) {
+  RunState r;
+  r.state = *(volatile const int*)&sc->state;
+  r.parity = sc->parity;
+  r.first = sc->inner == 0;
+  r.beta = sc->beta;
+  r.alpha = sc->alpha;
+  r.scale = sc->scale;
+  r.rr64 = sc->rr64;
+  r.ff = sc->ff;
+  r.rtol2 = sc->rtol2;
+  return r;
+}
+
+// Final reduction of kernel A for one system (thread 0 updates the scalars).
+template <typename SumFn>
+__device__ __forceinline__ void finish_a(const SysDesc& S, SysScalars* sc, int state,
+                                         int* n_active, SumFn sum2) {
+  double sum = 0.0, sum_b = 0.0;
+  sum2(S.part_a, S.n_tiles * WARPS, state != ST_PCG, sum, sum_b);
+  if (threadIdx.x == 0) {
+    if (state == ST_PCG) {
+      sc->pq = sum;
+      if (!(sum > 0.0) || !isfinite(sum)) {
+        sc->status = SSO_ERR_SINGULAR;
+        sc->state = ST_DONE;
+        atomicSub(n_active, 1);
+      } else {
+        sc->alpha = sc->rz / sum;
+        sc->parity ^= 1;
+      }
+    } else {
+      sc->rr64 = sum;
+      sc->ff = sum_b;
+    }
+    sc->cnt_a = 0u;
+  }
+}
+
+// Kernel A, FP64 CG (and any system kernel A reads from global memory).
 template <typename T>
-__global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const int2* __restrict__ tiles,
+__global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict__ tiles,
                                                       const int* __restrict__ n_tiles_ptr,
                                                       const SysDesc* __restrict__ sys,
                                                       int* __restrict__ flags) {
@@ -138,27 +188,31 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const int2* __restrict__ t
   const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
-  int run = 0;  // tiles of the current system done by this CTA since the last count
+  int run = 0, cur = -1;
+  RunState R;
+  R.state = ST_DONE;
   for (int tile = begin; tile < end; ++tile) {
-    const int2 tl = tiles[tile];
-    const SysDesc& S = sys[tl.x];
+    const int sid = tiles[tile].sys;
+    const int node0 = tiles[tile].node0;
+    const SysDesc& S = sys[sid];
     SysScalars* sc = S.sc;
-    const int state = *(volatile int*)&sc->state;
-    if (state == ST_DONE) continue;
-    const int node = tl.y + ln;
+    if (sid != cur) {
+      cur = sid;
+      R = read_state(sc);
+    }
+    if (R.state == ST_DONE) continue;
+    const int state = R.state;
+    const int node = node0 + ln;
     const bool act = lane < 6 * NODES_PER_WARP && node < S.n_nodes;
     const int i = 6 * node + rr;
     double part = 0.0, part_b = 0.0;
     if (state == ST_PCG) {
       const T* __restrict__ z = (const T*)S.z;
-      const int par = sc->parity;
-      const T* pold = (const T*)(par ? S.p1 : S.p0);
-      T* pnew = (T*)(par ? S.p0 : S.p1);
+      const T* pold = R.first ? z : (const T*)(R.parity ? S.p1 : S.p0);
+      T* pnew = (T*)(R.parity ? S.p0 : S.p1);
       // first iteration of a sweep: p = z, written as z + 0 * z (exact for
       // finite z) so that one code path serves every iteration
-      const bool first = sc->inner == 0;
-      const T beta = first ? T(0) : (T)sc->beta;
-      if (first) pold = z;
+      const T beta = R.first ? T(0) : (T)R.beta;
       if (act) {
         constexpr int CH = sizeof(T) == 4 ? 3 : 2;
         const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
@@ -187,11 +241,10 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const int2* __restrict__ t
       double* dst = S.part_a + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
       dst[0] = part;
       dst[1] = part_b;
-      __threadfence();
     }
     ++run;
     // end of this CTA's run of the system: count it
-    if (tile + 1 < end && tiles[tile + 1].x == tl.x) continue;
+    if (tile + 1 < end && tiles[tile + 1].sys == sid) continue;
     __syncthreads();
     if (t == 0) {
       __threadfence();
@@ -202,33 +255,18 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const int2* __restrict__ t
     __syncthreads();
     if (s_last) {
       __threadfence();
-      const int n_part = S.n_tiles * WARPS;
-      const double sum = ordered_sum(S.part_a, n_part, 2, 0, red);
-      const double sum_b = state == ST_PCG ? 0.0 : ordered_sum(S.part_a, n_part, 2, 1, red);
-      if (t == 0) {
-        if (state == ST_PCG) {
-          sc->pq = sum;
-          if (!(sum > 0.0) || !isfinite(sum)) {
-            sc->status = SSO_ERR_SINGULAR;
-            sc->state = ST_DONE;
-            atomicSub(n_active, 1);
-          } else {
-            sc->alpha = sc->rz / sum;
-            sc->parity ^= 1;
-          }
-        } else {
-          sc->rr64 = sum;
-          sc->ff = sum_b;
-        }
-        sc->cnt_a = 0u;
-      }
+      finish_a(S, sc, state, n_active,
+               [&](const double* part2, int n, bool both, double& a, double& b) {
+                 a = ordered_sum(part2, n, 2, 0, red);
+                 b = both ? ordered_sum(part2, n, 2, 1, red) : 0.0;
+               });
       __syncthreads();
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ tiles,
+__global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict__ tiles,
                                                       const int* __restrict__ n_tiles_ptr,
                                                       const SysDesc* __restrict__ sys,
                                                       int* __restrict__ flags) {
@@ -240,26 +278,37 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ t
   const int node_lane0 = lane - rr;  // lane of row 0 of this lane's node
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
-  int run = 0;
+  int run = 0, cur = -1;
+  RunState R;
+  R.state = ST_DONE;
+  bool work = false;
+  double inv_norm = 0.0;
   for (int tile = begin; tile < end; ++tile) {
-    const int2 tl = tiles[tile];
-    const SysDesc& S = sys[tl.x];
+    const int sid = tiles[tile].sys;
+    const int node0 = tiles[tile].node0;
+    const SysDesc& S = sys[sid];
     SysScalars* sc = S.sc;
-    const int state = *(volatile int*)&sc->state;
-    if (state == ST_DONE) continue;
-    const int node = tl.y + ln;
+    if (sid != cur) {
+      cur = sid;
+      R = read_state(sc);
+      work = R.state == ST_PCG ||
+             (isfinite(R.rr64) && !(R.rr64 <= R.rtol2 * R.ff));
+      inv_norm = R.state == ST_PCG ? 0.0 : 1.0 / ::sqrt(R.rr64);
+    }
+    if (R.state == ST_DONE) continue;
+    const int state = R.state;
+    const int node = node0 + ln;
     const bool act = lane < 6 * NODES_PER_WARP && node < S.n_nodes;
     const int i = 6 * node + rr;
     T* r = (T*)S.r;
     const T* __restrict__ M = MatOf<T>::M(S);
     const bool block = S.precond == SSO_BLOCK_JACOBI;
-    bool work = true;
     T ri = T(0);
     T mv[6];
     if (state == ST_PCG) {
-      const T alpha = (T)sc->alpha;
-      const double ua = sc->alpha * sc->scale;
-      const T* p = (const T*)(sc->parity ? S.p1 : S.p0);
+      const T alpha = (T)R.alpha;
+      const double ua = R.alpha * R.scale;
+      const T* p = (const T*)(R.parity ? S.p1 : S.p0);
       if (act) {
         if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
         else mv[0] = M[i];
@@ -267,15 +316,11 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ t
         ri = fmaT(-alpha, ((const T*)S.q)[i], r[i]);
         r[i] = ri;
       }
-    } else {
-      const double rr64 = sc->rr64;
-      work = isfinite(rr64) && !(rr64 <= sc->rtol2 * sc->ff);
-      if (work && act) {
-        if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
-        else mv[0] = M[i];
-        ri = (T)(S.r64[i] * (1.0 / ::sqrt(rr64)));
-        r[i] = ri;
-      }
+    } else if (work && act) {
+      if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
+      else mv[0] = M[i];
+      ri = (T)(S.r64[i] * inv_norm);
+      r[i] = ri;
     }
     double v1 = 0.0, v2 = 0.0;
     if (work) {
@@ -302,10 +347,9 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ t
       double* dst = S.part_b + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
       dst[0] = v1;
       dst[1] = v2;
-      __threadfence();
     }
     ++run;
-    if (tile + 1 < end && tiles[tile + 1].x == tl.x) continue;
+    if (tile + 1 < end && tiles[tile + 1].sys == sid) continue;
     __syncthreads();
     if (t == 0) {
       __threadfence();
@@ -373,6 +417,300 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const int2* __restrict__ t
   }
 }
 
+// ---------------------------------------------------------------------------
+// Kernel A for the FP32 CG, warp-specialised.  Everything a tile reads is
+// contiguous in memory -- its K rows are one slab of the BSR value array, its
+// column indices and its row_ptr entries one run each, and the z / p entries
+// its columns touch lie in one node range (the tile's halo) -- and their
+// extents are fixed by the mesh (TileDesc, built on the host).  A producer
+// warp streams these five pieces of each tile into a two-stage shared-memory
+// ring with bulk copies (cp.async.bulk, the 1-D form of the TMA engine) and
+// passes the system's scalars along; six consumer warps compute the tile from
+// shared memory with no global loads.  full[s] / empty[s] mbarriers hand each
+// stage over; every wait is bounded.  Tiles that do not fit (scattered
+// numbering) and the FP64 residual passes read global memory instead.
+constexpr int ST_SLAB_K = STAGE_SLAB_K;
+constexpr int ST_SLAB_C = STAGE_SLAB_C;
+constexpr int ST_SLAB_V = STAGE_SLAB_V;
+constexpr int ST_SLAB_R = STAGE_SLAB_R;
+constexpr int ST_OFF_C = ST_SLAB_K;
+constexpr int ST_OFF_Z = ST_OFF_C + ST_SLAB_C;
+constexpr int ST_OFF_P = ST_OFF_Z + ST_SLAB_V;
+constexpr int ST_OFF_R = ST_OFF_P + ST_SLAB_V;
+constexpr int ST_STAGE = ST_OFF_R + ST_SLAB_R;
+constexpr int ST_STAGES = 2;
+constexpr int ST_SMEM = ST_STAGES * ST_STAGE;
+constexpr int ST_THREADS = NT + 32;  // six consumer warps + one producer warp
+constexpr long long kWaitPolls = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitPolls; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+// barrier among the 192 consumer threads only (the producer warp runs ahead)
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+__device__ __forceinline__ double consumer_block_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  consumer_sync();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) s += red[w];
+  }
+  consumer_sync();
+  return s;
+}
+__device__ __forceinline__ void ld6s(const float* p, float v[6]) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+  const float2 a = q[0], b = q[1], c = q[2];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
+// What the producer hands the consumers with each stage.
+struct StageInfo {
+  int state, mode, first, parity;  // mode 1: the tile's data is in the stage
+  float beta;
+  int sys, node0, nn, j0, cb, vlo, rb;
+};
+
+__global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
+    const TileDesc* __restrict__ tiles, const int* __restrict__ n_tiles_ptr,
+    const SysDesc* __restrict__ sys, int* __restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char ring[];
+  __shared__ __align__(8) unsigned long long full[ST_STAGES], empty[ST_STAGES];
+  __shared__ StageInfo info[ST_STAGES];
+  __shared__ double red[WARPS];
+  __shared__ int s_last, s_abort;
+  int* n_active = flags;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  int begin, end;
+  tile_range(*n_tiles_ptr, begin, end);
+  if (t == 0) {
+    for (int s = 0; s < ST_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], WARPS);
+    }
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  if (w == WARPS) {
+    // ---------------- producer warp (lane 0) ----------------
+    if (lane != 0) return;
+    int cur = -1, issued = 0;
+    RunState R;
+    R.state = ST_DONE;
+    for (int tile = begin, k = 0; tile < end; ++tile, ++k) {
+      const int s = k % ST_STAGES, use = k / ST_STAGES;
+      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+        atomicExch(flags + 1, 1);
+        break;
+      }
+      const TileDesc td = tiles[tile];
+      const SysDesc* S = sys + td.sys;
+      if (td.sys != cur) {
+        cur = td.sys;
+        R = read_state(S->sc);
+      }
+      StageInfo inf;
+      inf.state = R.state;
+      inf.mode = 0;
+      inf.first = R.first;
+      inf.parity = R.parity;
+      inf.beta = R.first ? 0.f : (float)R.beta;
+      inf.sys = td.sys;
+      inf.node0 = td.node0;
+      inf.nn = td.nn;
+      inf.j0 = td.j0;
+      inf.cb = td.cb;
+      inf.vlo = td.vlo;
+      inf.rb = td.rb;
+      ++issued;
+      if (R.state == ST_PCG && td.stage) {
+        inf.mode = 1;
+        info[s] = inf;
+        const float* z = (const float*)S->z;
+        const float* pold = R.first ? z : (const float*)(R.parity ? S->p1 : S->p0);
+        const uint32_t kb = (uint32_t)td.nblk * 144u, cb = (uint32_t)td.ncb * 4u;
+        const uint32_t vb = (uint32_t)td.nv * 24u, rb = (uint32_t)td.nrb * 4u;
+        unsigned char* st = ring + s * ST_STAGE;
+        fence_proxy_async();
+        mbar_arrive_tx(&full[s], kb + cb + 2 * vb + rb);
+        bulk_g2s(st, S->K32 + (size_t)td.j0 * 36, kb, &full[s]);
+        bulk_g2s(st + ST_OFF_C, S->col + td.cb, cb, &full[s]);
+        bulk_g2s(st + ST_OFF_Z, z + (size_t)td.vlo * 6, vb, &full[s]);
+        bulk_g2s(st + ST_OFF_P, pold + (size_t)td.vlo * 6, vb, &full[s]);
+        bulk_g2s(st + ST_OFF_R, S->row_ptr + td.rb, rb, &full[s]);
+      } else {
+        info[s] = inf;
+        mbar_arrive(&full[s]);
+      }
+    }
+    // let the copies in flight land before the CTA's shared memory is released
+    for (int k = issued - ST_STAGES; k < issued; ++k)
+      if (k >= 0) mbar_wait(&full[k % ST_STAGES], (k / ST_STAGES) & 1);
+    return;
+  }
+
+  // ---------------- consumer warps ----------------
+  // A warp whose wait gives up sets the error flag and runs the rest of its
+  // tiles dry (no waits, no work) so that every consumer warp still reaches
+  // the same named barriers; the host then fails the solve.
+  const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
+  int run = 0;
+  bool dry = false;
+  for (int tile = begin, k = 0; tile < end; ++tile, ++k) {
+    const int s = k % ST_STAGES, use = k / ST_STAGES;
+    if (!dry && !mbar_wait(&full[s], use & 1)) {
+      dry = true;
+      s_abort = 1;
+      atomicExch(flags + 1, 1);
+    }
+    const StageInfo inf = info[s];
+    const SysDesc& S = sys[inf.sys];
+    SysScalars* sc = S.sc;
+    const int real_state = inf.state;
+    const int state = dry ? ST_DONE : real_state;
+    const int node = inf.node0 + ln;
+    const bool act = lane < 6 * NODES_PER_WARP && ln < inf.nn;
+    const int i = 6 * node + rr;
+    double part = 0.0, part_b = 0.0;
+    if (state == ST_PCG) {
+      float* pnew = (float*)(inf.parity ? S.p0 : S.p1);
+      const float beta = inf.beta;
+      if (act) {
+        float acc = 0.f, zi, pi_old;
+        if (inf.mode == 1) {
+          const unsigned char* st = ring + s * ST_STAGE;
+          const int* Rs = reinterpret_cast<const int*>(st + ST_OFF_R) - inf.rb;
+          const int j0 = Rs[node], j1 = Rs[node + 1];
+          const float* Ks = reinterpret_cast<const float*>(st) + (size_t)(j0 - inf.j0) * 36 + rr * 6;
+          const int* Cs = reinterpret_cast<const int*>(st + ST_OFF_C) - inf.cb;
+          const float* Zs = reinterpret_cast<const float*>(st + ST_OFF_Z) - (size_t)inf.vlo * 6;
+          const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P) - (size_t)inf.vlo * 6;
+          for (int j = j0; j < j1; ++j) {
+            const int c = Cs[j];
+            float kv[6], zv[6], pv[6];
+            ld6s(Ks, kv);
+            ld6s(Zs + (size_t)c * 6, zv);
+            ld6s(Ps + (size_t)c * 6, pv);
+            Ks += 36;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc = fmaf(kv[q], fmaf(beta, pv[q], zv[q]), acc);
+          }
+          zi = Zs[i];
+          pi_old = Ps[i];
+        } else {
+          const float* z = (const float*)S.z;
+          const float* pold = inf.first ? z : (const float*)(inf.parity ? S.p1 : S.p0);
+          const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
+          acc = row_dot<float, 3>(S.K32, S.col, j0, j1, rr, z, pold, beta);
+          zi = z[i];
+          pi_old = pold[i];
+        }
+        const float pi = fmaf(beta, pi_old, zi);
+        pnew[i] = pi;
+        ((float*)S.q)[i] = acc;
+        part = (double)pi * (double)acc;
+      }
+    } else if (state != ST_DONE) {  // ST_INIT or ST_RESID: r64 = b - K64 x in FP64
+      if (act) {
+        const double bi = S.b[i];
+        double acc = bi;
+        part_b = bi * bi;
+        if (state == ST_RESID) {
+          const int j0 = __ldg(S.row_ptr + node), j1 = __ldg(S.row_ptr + node + 1);
+          acc -= row_dot<double, 2>(S.K64, S.col, j0, j1, rr, S.x, S.x, 0.0);
+        }
+        S.r64[i] = acc;
+        part = acc * acc;
+      }
+    }
+    // stage s is consumed: hand it back to the producer
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (real_state == ST_DONE) continue;
+    part = warp_sum(part);
+    part_b = warp_sum(part_b);
+    if (lane == 0) {
+      double* dst = S.part_a + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
+      dst[0] = part;
+      dst[1] = part_b;
+    }
+    ++run;
+    if (tile + 1 < end && tiles[tile + 1].sys == inf.sys) continue;
+    consumer_sync();
+    if (t == 0) {
+      s_last = 0;
+      if (!s_abort) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&sc->cnt_a, (unsigned)run);
+        s_last = (prev + (unsigned)run == (unsigned)S.n_tiles);
+      }
+    }
+    run = 0;
+    consumer_sync();
+    if (s_last) {
+      __threadfence();
+      finish_a(S, sc, real_state, n_active,
+               [&](const double* part2, int n, bool both, double& a, double& b) {
+                 double v = 0.0, vb = 0.0;
+                 for (int q = t; q < n; q += NT) {
+                   v += __ldcg(part2 + 2 * (size_t)q);
+                   if (both) vb += __ldcg(part2 + 2 * (size_t)q + 1);
+                 }
+                 a = consumer_block_sum(v, red);
+                 b = both ? consumer_block_sum(vb, red) : 0.0;
+               });
+      consumer_sync();
+    }
+  }
+}
+
 // out[s] = b_s^T x_s for every system, one CTA per system, fixed order.
 __global__ void __launch_bounds__(NT) dot_kernel(const SysDesc* __restrict__ sys,
                                                  double* __restrict__ out) {
@@ -387,17 +725,29 @@ __global__ void __launch_bounds__(NT) dot_kernel(const SysDesc* __restrict__ sys
 
 }  // namespace
 
-cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* flags, int grid, cudaStream_t s) {
-  if (fp64)
+static cudaError_t staged_attributes() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(pcg_a_staged_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+cudaError_t launch_pcg_a(bool fp64, const TileDesc* tiles, const int* n_tiles,
+                         const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
+  if (fp64) {
     pcg_a_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
-  else
-    pcg_a_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
+  } else {
+    cudaError_t e = staged_attributes();
+    if (e != cudaSuccess) return e;
+    pcg_a_staged_kernel<<<grid, ST_THREADS, ST_SMEM, s>>>(tiles, n_tiles, sys, flags);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* flags, int grid, cudaStream_t s) {
+cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
+                         const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
   if (fp64)
     pcg_b_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
   else
@@ -421,7 +771,9 @@ void pcg_grid_limits(bool fp64, int* grid_a, int* grid_b) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_kernel<double>, NT, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b_kernel<double>, NT, 0);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_kernel<float>, NT, 0);
+    staged_attributes();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_staged_kernel, ST_THREADS,
+                                                  ST_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b_kernel<float>, NT, 0);
   }
   if (sms < 1) sms = 1;

@@ -59,6 +59,25 @@ struct SysScalars {
   int max_sweeps;
 };
 
+// Static description of one tile of a batch (device memory, built once per
+// batch on the host).  The K rows of a tile are the contiguous blocks
+// [j0, j0 + nblk); the columns they read lie in the node range of the halo.
+// The *_b fields give 16-byte aligned runs for bulk copies.
+struct TileDesc {
+  int sys;     // system index in the batch
+  int node0;   // first node of the tile
+  int nn;      // nodes in the tile
+  int j0;      // row_ptr[node0]
+  int nblk;    // row_ptr[node0 + nn] - j0
+  int cb;      // first column index to copy (multiple of 4)
+  int ncb;     // column indices to copy (multiple of 4)
+  int vlo;     // first halo node (even)
+  int nv;      // halo nodes (even)
+  int rb;      // first row_ptr entry to copy (multiple of 4)
+  int nrb;     // row_ptr entries to copy (multiple of 4)
+  int stage;   // 1 when the FP32 slab, columns, halo and row_ptr fit the staging buffers
+};
+
 // Per-system pointers (device memory, one per system of a batch).
 struct SysDesc {
   int n_nodes;
@@ -115,10 +134,15 @@ cudaError_t launch_axpby(int n, double a, const double* x, const double* y, cons
 // Launchers (pcg.cu)
 // flags[0] = systems still iterating, flags[1] = device-side failure (a bounded
 // wait that gave up); grid sizes from pcg_grid_limits.
-cudaError_t launch_pcg_a(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* flags, int grid, cudaStream_t s);
-cudaError_t launch_pcg_b(bool fp64, const int2* tiles, const int* n_tiles, const SysDesc* sys,
-                         int* flags, int grid, cudaStream_t s);
+cudaError_t launch_pcg_a(bool fp64, const TileDesc* tiles, const int* n_tiles,
+                         const SysDesc* sys, int* flags, int grid, cudaStream_t s);
+cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
+                         const SysDesc* sys, int* flags, int grid, cudaStream_t s);
+// Staging-buffer limits of the FP32 kernel A (a tile is staged when it fits).
+constexpr int STAGE_SLAB_K = 40 * 1024;  // K rows (bytes)
+constexpr int STAGE_SLAB_C = 1280;       // column indices (bytes)
+constexpr int STAGE_SLAB_V = 6144;       // one vector halo (bytes)
+constexpr int STAGE_SLAB_R = 256;        // row_ptr run (bytes)
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
 
 // Launchers (spmv.cu): y = K x, *xty = x^T y; partials [ceil(n_nodes/TILE)],

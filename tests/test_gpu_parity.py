@@ -280,3 +280,33 @@ def test_bsr_spmv_entry_point(sso, name):
     assert np.abs(y1 - y_ref).max() <= 1e-13 * np.abs(y_ref).max()
     assert float(d1) == pytest.approx(float(x @ y_ref), rel=1e-12)
     assert np.array_equal(y1, y2.cpu().numpy()) and float(d1) == float(d2)
+
+
+def _permuted(m, seed):
+    """The same structure with randomly renumbered nodes."""
+    n = m["xyz"].shape[0]
+    perm = np.random.default_rng(seed).permutation(n)  # new index of old node k
+    inv = np.argsort(perm)
+    out = dict(m)
+    for k in ("xyz", "fixed", "nodal_load"):
+        out[k] = m[k][inv]
+    out["quad_conn"] = perm[m["quad_conn"]].astype(np.int32)
+    out["beam_conn"] = perm[m["beam_conn"]].astype(np.int32)
+    return out, perm
+
+
+def test_scattered_numbering_fallback_path(sso, orc):
+    """Random node numbering: tile halos span the mesh, so the FP32 kernel
+    reads z and p from global memory instead of shared-memory halos."""
+    m = meshgen.shell(n_el=20, span=10.0, seed=6)
+    ref = orc.gradient(m)
+    mp, perm = _permuted(m, 3)
+    mdl = sso.Model(mp)
+    st = mdl.solve(precision="fp32_ir", rtol=1e-9)
+    assert st["status"] == 0
+    mdl.gradient(1.0)
+    r = mdl.result()
+    u = r["u"].reshape(-1, 6)[perm].ravel()
+    assert rel(u, ref["u"]) <= TOL_FP32_IR
+    assert rel(r["dz"][perm], ref["dz"]) <= TOL_FP32_IR
+    assert rel(r["dt"], ref["dt"]) <= TOL_FP32_IR
