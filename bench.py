@@ -43,11 +43,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batch", type=int, default=64, help="designs per step")
+    p.add_argument("--batch", type=int, default=128, help="designs per step")
     p.add_argument("--n-el", type=int, default=64)
     p.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
     p.add_argument("--precond", default="block_jacobi", choices=["block_jacobi", "jacobi"])
-    p.add_argument("--rtol", type=float, default=1e-8)
+    p.add_argument("--rtol", type=float, default=1e-6)
     p.add_argument("--inner-rtol", type=float, default=1e-3)
     p.add_argument("--iters-per-launch", type=int, default=32)
     p.add_argument("--cpu-sample", type=int, default=3, help="oracle designs in cpu_baseline")

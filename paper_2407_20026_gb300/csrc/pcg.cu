@@ -265,154 +265,211 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict
   }
 }
 
+// Kernel B.  Pure streaming per node (no neighbours): one thread owns one
+// node (all six rows), so z = M^-1 r is a 6x6 product in registers and every
+// vector is read as 24- or 48-byte runs.  Warp w of a CTA takes every
+// WARPS-th tile of the CTA's range; a tile (TILE nodes) is one warp.  The
+// warp reduces the tile's r^T z and r^T r with shuffles, lane 0 stores the
+// tile's partials and adds 1 to the system's completion counter; the warp that
+// completes the system sums all of its tile partials in tile order and updates
+// the scalars.  No CTA barriers; the grouping depends on the system only, so
+// results are bit-identical alone and in any batch.
+__device__ __forceinline__ void ld4x9(const float* p, float m[36]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float4 v = __ldg(q + k);
+    m[4 * k] = v.x; m[4 * k + 1] = v.y; m[4 * k + 2] = v.z; m[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void ld4x9(const double* p, double m[36]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    const double2 v = __ldg(q + k);
+    m[2 * k] = v.x; m[2 * k + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void ld6rw(const float* p, float v[6]) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+  const float2 a = q[0], b = q[1], c = q[2];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+__device__ __forceinline__ void ld6rw(const double* p, double v[6]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = q[0], b = q[1], c = q[2];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+__device__ __forceinline__ void st6(float* p, const float v[6]) {
+  float2* q = reinterpret_cast<float2*>(p);
+  q[0] = make_float2(v[0], v[1]);
+  q[1] = make_float2(v[2], v[3]);
+  q[2] = make_float2(v[4], v[5]);
+}
+__device__ __forceinline__ void st6(double* p, const double v[6]) {
+  double2* q = reinterpret_cast<double2*>(p);
+  q[0] = make_double2(v[0], v[1]);
+  q[1] = make_double2(v[2], v[3]);
+  q[2] = make_double2(v[4], v[5]);
+}
+
+// Scalar update of kernel B for one system, by one thread, once every tile of
+// the system has been counted.  s1 = r^T z, s2 = r^T r.
+__device__ __forceinline__ void finish_b(SysScalars* sc, int state, double s1, double s2,
+                                         int* n_active) {
+  if (state == ST_PCG) {
+    sc->iters += 1;
+    sc->inner += 1;
+    if (!isfinite(s1) || !isfinite(s2)) {
+      sc->status = SSO_ERR_SINGULAR;
+      sc->state = ST_DONE;
+      atomicSub(n_active, 1);
+    } else {
+      sc->beta = s1 / sc->rz;
+      sc->rz = s1;
+      sc->rr = s2;
+      if (s2 <= sc->inner_thr || sc->iters >= sc->max_iter) sc->state = ST_RESID;
+    }
+  } else {
+    const double rr64 = sc->rr64;
+    if (!isfinite(rr64)) {
+      sc->status = SSO_ERR_INVALID;
+      sc->state = ST_DONE;
+      atomicSub(n_active, 1);
+    } else if (rr64 <= sc->rtol2 * sc->ff) {
+      sc->status = SSO_OK;
+      sc->state = ST_DONE;
+      atomicSub(n_active, 1);
+    } else if (sc->iters >= sc->max_iter || sc->sweeps >= sc->max_sweeps ||
+               (sc->sweeps >= 2 && rr64 > 0.0625 * sc->rr64_prev)) {
+      // cap reached, or the FP64 residual fell by less than 4x over the last
+      // sweep (rtol below what this K and FP64 can resolve)
+      sc->status = SSO_ERR_NOT_CONVERGED;
+      sc->state = ST_DONE;
+      atomicSub(n_active, 1);
+    } else if (!(s1 > 0.0)) {
+      sc->status = SSO_ERR_SINGULAR;  // preconditioner not positive definite
+      sc->state = ST_DONE;
+      atomicSub(n_active, 1);
+    } else {
+      sc->rz = s1;
+      sc->rr = s2;
+      sc->rr_start = s2;
+      sc->scale = ::sqrt(rr64);
+      sc->rr64_prev = rr64;
+      sc->inner_thr = s2 * fmax(sc->inner_rtol2, 0.25 * sc->rtol2 * sc->ff / rr64);
+      sc->inner = 0;
+      sc->sweeps += 1;
+      sc->state = ST_PCG;
+    }
+  }
+  sc->cnt_b = 0u;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict__ tiles,
                                                       const int* __restrict__ n_tiles_ptr,
                                                       const SysDesc* __restrict__ sys,
                                                       int* __restrict__ flags) {
-  __shared__ double red[WARPS];
-  __shared__ int s_last;
   int* n_active = flags;
-  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
-  const int node_lane0 = lane - rr;  // lane of row 0 of this lane's node
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
-  int run = 0, cur = -1;
+  int cur = -1;
   RunState R;
   R.state = ST_DONE;
-  bool work = false;
-  double inv_norm = 0.0;
-  for (int tile = begin; tile < end; ++tile) {
-    const int sid = tiles[tile].sys;
-    const int node0 = tiles[tile].node0;
+  bool work = false, block = true;
+  double inv_norm = 0.0, ua = 0.0;
+  T alpha = T(0);
+  for (int tile = begin + w; tile < end; tile += WARPS) {
+    const TileDesc& td = tiles[tile];
+    const int sid = td.sys;
     const SysDesc& S = sys[sid];
     SysScalars* sc = S.sc;
     if (sid != cur) {
       cur = sid;
       R = read_state(sc);
-      work = R.state == ST_PCG ||
-             (isfinite(R.rr64) && !(R.rr64 <= R.rtol2 * R.ff));
+      work = R.state == ST_PCG || (isfinite(R.rr64) && !(R.rr64 <= R.rtol2 * R.ff));
       inv_norm = R.state == ST_PCG ? 0.0 : 1.0 / ::sqrt(R.rr64);
+      alpha = (T)R.alpha;
+      ua = R.alpha * R.scale;
+      block = S.precond == SSO_BLOCK_JACOBI;
     }
     if (R.state == ST_DONE) continue;
     const int state = R.state;
-    const int node = node0 + ln;
-    const bool act = lane < 6 * NODES_PER_WARP && node < S.n_nodes;
-    const int i = 6 * node + rr;
-    T* r = (T*)S.r;
-    const T* __restrict__ M = MatOf<T>::M(S);
-    const bool block = S.precond == SSO_BLOCK_JACOBI;
-    T ri = T(0);
-    T mv[6];
-    if (state == ST_PCG) {
-      const T alpha = (T)R.alpha;
-      const double ua = R.alpha * R.scale;
-      const T* p = (const T*)(R.parity ? S.p1 : S.p0);
-      if (act) {
-        if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
-        else mv[0] = M[i];
-        S.x[i] = fma(ua, (double)p[i], S.x[i]);
-        ri = fmaT(-alpha, ((const T*)S.q)[i], r[i]);
-        r[i] = ri;
-      }
-    } else if (work && act) {
-      if (block) load6(M + (size_t)node * 36 + rr * 6, mv);
-      else mv[0] = M[i];
-      ri = (T)(S.r64[i] * inv_norm);
-      r[i] = ri;
-    }
+    const int node = td.node0 + lane;
     double v1 = 0.0, v2 = 0.0;
-    if (work) {
-      // z = M^-1 r: the node's six residual rows are lanes node_lane0 .. +5
-      T zi = T(0);
-      if (block) {
+    if (lane < td.nn && work) {
+      const size_t i0 = 6 * (size_t)node;
+      T* r = (T*)S.r + i0;
+      const T* M = MatOf<T>::M(S);
+      T rv[6];
+      if (state == ST_PCG) {
+        T pv[6], qv[6];
+        double xv[6];
+        load6((const T*)(R.parity ? S.p1 : S.p0) + i0, pv);
+        load6((const T*)S.q + i0, qv);
+        ld6rw(r, rv);
+        ld6rw(S.x + i0, xv);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const T rk = __shfl_sync(0xffffffffu, ri, (node_lane0 + k) & 31);
-          zi = fmaT(mv[k], rk, zi);
+          xv[k] = fma(ua, (double)pv[k], xv[k]);
+          rv[k] = fmaT(-alpha, qv[k], rv[k]);
+        }
+        st6(S.x + i0, xv);
+      } else {
+        double gv[6];
+        ld6rw(S.r64 + i0, gv);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) rv[k] = (T)(gv[k] * inv_norm);
+      }
+      st6(r, rv);
+      T zv[6];
+      if (block) {
+        T mv[36];
+        ld4x9(M + 36 * (size_t)node, mv);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          T s = T(0);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) s = fmaT(mv[6 * a + c], rv[c], s);
+          zv[a] = s;
         }
       } else {
-        zi = mv[0] * ri;
+        T mv[6];
+        load6(M + i0, mv);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) zv[a] = mv[a] * rv[a];
       }
-      if (act) {
-        ((T*)S.z)[i] = zi;
-        v1 = (double)ri * (double)zi;
-        v2 = (double)ri * (double)ri;
+      st6((T*)S.z + i0, zv);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        v1 += (double)rv[a] * (double)zv[a];
+        v2 += (double)rv[a] * (double)rv[a];
       }
     }
     v1 = warp_sum(v1);
     v2 = warp_sum(v2);
+    int last = 0;
     if (lane == 0) {
-      double* dst = S.part_b + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
+      double* dst = S.part_b + 2 * (size_t)(tile - S.tile0);
       dst[0] = v1;
       dst[1] = v2;
-    }
-    ++run;
-    if (tile + 1 < end && tiles[tile + 1].sys == sid) continue;
-    __syncthreads();
-    if (t == 0) {
       __threadfence();
-      const unsigned prev = atomicAdd(&sc->cnt_b, (unsigned)run);
-      s_last = (prev + (unsigned)run == (unsigned)S.n_tiles);
+      const unsigned prev = atomicAdd(&sc->cnt_b, 1u);
+      last = prev + 1u == (unsigned)S.n_tiles;
     }
-    run = 0;
-    __syncthreads();
-    if (s_last) {
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
       __threadfence();
-      const int n_part = S.n_tiles * WARPS;
-      const double s1 = ordered_sum(S.part_b, n_part, 2, 0, red);
-      const double s2 = ordered_sum(S.part_b, n_part, 2, 1, red);
-      if (t == 0) {
-        if (state == ST_PCG) {
-          sc->iters += 1;
-          sc->inner += 1;
-          if (!isfinite(s1) || !isfinite(s2)) {
-            sc->status = SSO_ERR_SINGULAR;
-            sc->state = ST_DONE;
-            atomicSub(n_active, 1);
-          } else {
-            sc->beta = s1 / sc->rz;
-            sc->rz = s1;
-            sc->rr = s2;
-            if (s2 <= sc->inner_thr || sc->iters >= sc->max_iter) sc->state = ST_RESID;
-          }
-        } else {
-          const double rr64 = sc->rr64;
-          if (!isfinite(rr64)) {
-            sc->status = SSO_ERR_INVALID;
-            sc->state = ST_DONE;
-            atomicSub(n_active, 1);
-          } else if (rr64 <= sc->rtol2 * sc->ff) {
-            sc->status = SSO_OK;
-            sc->state = ST_DONE;
-            atomicSub(n_active, 1);
-          } else if (sc->iters >= sc->max_iter || sc->sweeps >= sc->max_sweeps ||
-                     (sc->sweeps >= 2 && rr64 > 0.0625 * sc->rr64_prev)) {
-            // cap reached, or the FP64 residual fell by less than 4x over the
-            // last sweep (rtol below what this K and FP64 can resolve)
-            sc->status = SSO_ERR_NOT_CONVERGED;
-            sc->state = ST_DONE;
-            atomicSub(n_active, 1);
-          } else if (!(s1 > 0.0)) {
-            sc->status = SSO_ERR_SINGULAR;  // preconditioner not positive definite
-            sc->state = ST_DONE;
-            atomicSub(n_active, 1);
-          } else {
-            sc->rz = s1;
-            sc->rr = s2;
-            sc->rr_start = s2;
-            sc->scale = ::sqrt(rr64);
-            sc->rr64_prev = rr64;
-            sc->inner_thr = s2 * fmax(sc->inner_rtol2, 0.25 * sc->rtol2 * sc->ff / rr64);
-            sc->inner = 0;
-            sc->sweeps += 1;
-            sc->state = ST_PCG;
-          }
-        }
-        sc->cnt_b = 0u;
+      double a1 = 0.0, a2 = 0.0;
+      for (int k = lane; k < S.n_tiles; k += 32) {
+        a1 += __ldcg(S.part_b + 2 * (size_t)k);
+        a2 += __ldcg(S.part_b + 2 * (size_t)k + 1);
       }
-      __syncthreads();
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) finish_b(sc, state, a1, a2, n_active);
     }
   }
 }
