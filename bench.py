@@ -300,6 +300,7 @@ def main():
     achieved = alg_bytes / (ms_a / 1000.0) / 1e9 if ms_a > 0 else None
     a_launches = timed_pairs
     traffic = kernel_traffic("pcg.cu", "pcg_a_%s" % ("f32" if fp32 else "f64"))
+    traffic_bytes = traffic["dram_bytes_per_design_launch"] * B if traffic else None
 
     # end to end: designs from pinned host memory, results back to host
     e2e = None
@@ -378,8 +379,10 @@ def main():
                 "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                 "frac": achieved / peak_gbs if achieved else None,
                 "peak_kind": peak_kind,
-                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic": traffic_bytes,
+                "traffic_source": "profiles/traffic.json (ncu, scaled by designs)" if traffic else None,
                 "alg_bytes_per_launch": alg_bytes / max(a_launches, 1),
+                "alg_bytes_per_cg_launch": B * bytes_pcg,
                 "launches_timed": a_launches, "kernel_ms_total": ms_a,
                 "kernel_b_ms_total": ms_b,
             },

@@ -596,9 +596,9 @@ TileDesc make_tile(const sso_model* M, int s, int k) {
   d.nv = hi >= 0 ? ((hi | 1) - d.vlo + 1) : 0;
   d.rb = d.node0 & ~3;
   d.nrb = ((d.node0 + d.nn + 1 + 3) & ~3) - d.rb;
-  d.stage = d.nblk > 0 && d.nv > 0 && (long long)d.nblk * 144 <= STAGE_SLAB_K &&
-            d.ncb * 4 <= STAGE_SLAB_C && (long long)d.nv * 24 <= STAGE_SLAB_V &&
-            d.nrb * 4 <= STAGE_SLAB_R;
+  d.stage_k = d.nblk > 0 && (long long)d.nblk * 144 <= STAGE_SLAB_K &&
+              d.ncb * 4 <= STAGE_SLAB_C && d.nrb * 4 <= STAGE_SLAB_R;
+  d.stage = d.stage_k && d.nv > 0 && (long long)d.nv * 24 <= STAGE_SLAB_V;
   return d;
 }
 

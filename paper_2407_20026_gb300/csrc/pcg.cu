@@ -485,7 +485,9 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
 // passes the system's scalars along; six consumer warps compute the tile from
 // shared memory with no global loads.  full[s] / empty[s] mbarriers hand each
 // stage over; every wait is bounded.  Tiles that do not fit (scattered
-// numbering) and the FP64 residual passes read global memory instead.
+// numbering) and the FP64 residual passes read global memory instead; a tile
+// whose halo alone does not fit (long grid rows) stages everything but the
+// halo and gathers z and p from global memory.
 constexpr int ST_SLAB_K = STAGE_SLAB_K;
 constexpr int ST_SLAB_C = STAGE_SLAB_C;
 constexpr int ST_SLAB_V = STAGE_SLAB_V;
@@ -627,20 +629,24 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.vlo = td.vlo;
       inf.rb = td.rb;
       ++issued;
-      if (R.state == ST_PCG && td.stage) {
-        inf.mode = 1;
+      if (R.state == ST_PCG && td.stage_k) {
+        // mode 1: K rows, columns, row_ptr and both vector halos; mode 2: the
+        // halo does not fit, the consumers gather z and p from global memory
+        inf.mode = td.stage ? 1 : 2;
         info[s] = inf;
         const float* z = (const float*)S->z;
         const float* pold = R.first ? z : (const float*)(R.parity ? S->p1 : S->p0);
         const uint32_t kb = (uint32_t)td.nblk * 144u, cb = (uint32_t)td.ncb * 4u;
-        const uint32_t vb = (uint32_t)td.nv * 24u, rb = (uint32_t)td.nrb * 4u;
+        const uint32_t vb = td.stage ? (uint32_t)td.nv * 24u : 0u, rb = (uint32_t)td.nrb * 4u;
         unsigned char* st = ring + s * ST_STAGE;
         fence_proxy_async();
         mbar_arrive_tx(&full[s], kb + cb + 2 * vb + rb);
         bulk_g2s(st, S->K32 + (size_t)td.j0 * 36, kb, &full[s]);
         bulk_g2s(st + ST_OFF_C, S->col + td.cb, cb, &full[s]);
-        bulk_g2s(st + ST_OFF_Z, z + (size_t)td.vlo * 6, vb, &full[s]);
-        bulk_g2s(st + ST_OFF_P, pold + (size_t)td.vlo * 6, vb, &full[s]);
+        if (vb) {
+          bulk_g2s(st + ST_OFF_Z, z + (size_t)td.vlo * 6, vb, &full[s]);
+          bulk_g2s(st + ST_OFF_P, pold + (size_t)td.vlo * 6, vb, &full[s]);
+        }
         bulk_g2s(st + ST_OFF_R, S->row_ptr + td.rb, rb, &full[s]);
       } else {
         info[s] = inf;
@@ -701,6 +707,38 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
           }
           zi = Zs[i];
           pi_old = Ps[i];
+        } else if (inf.mode == 2) {
+          // K rows, columns and row_ptr from the stage; z and p gathered from
+          // global memory, three columns in flight at a time
+          const unsigned char* st = ring + s * ST_STAGE;
+          const int* Rs = reinterpret_cast<const int*>(st + ST_OFF_R) - inf.rb;
+          const int j0 = Rs[node], j1 = Rs[node + 1];
+          const float* Kt = reinterpret_cast<const float*>(st) - (size_t)inf.j0 * 36 + rr * 6;
+          const int* Cs = reinterpret_cast<const int*>(st + ST_OFF_C) - inf.cb;
+          const float* z = (const float*)S.z;
+          const float* pold = inf.first ? z : (const float*)(inf.parity ? S.p1 : S.p0);
+          constexpr int CH = 3;
+          for (int jb = j0; jb < j1; jb += CH) {
+            int cc[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) cc[u] = Cs[min(jb + u, j1 - 1)];
+            float kv[CH][6], zv[CH][6], pv[CH][6];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+              ld6s(Kt + (size_t)min(jb + u, j1 - 1) * 36, kv[u]);
+              load6(z + (size_t)cc[u] * 6, zv[u]);
+              load6(pold + (size_t)cc[u] * 6, pv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u)
+              if (jb + u < j1) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                  acc = fmaf(kv[u][q], fmaf(beta, pv[u][q], zv[u][q]), acc);
+              }
+          }
+          zi = z[i];
+          pi_old = pold[i];
         } else {
           const float* z = (const float*)S.z;
           const float* pold = inf.first ? z : (const float*)(inf.parity ? S.p1 : S.p0);

@@ -76,6 +76,7 @@ struct TileDesc {
   int rb;      // first row_ptr entry to copy (multiple of 4)
   int nrb;     // row_ptr entries to copy (multiple of 4)
   int stage;   // 1 when the FP32 slab, columns, halo and row_ptr fit the staging buffers
+  int stage_k; // 1 when the FP32 slab, columns and row_ptr fit (the halo may not)
 };
 
 // Per-system pointers (device memory, one per system of a batch).

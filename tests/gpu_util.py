@@ -54,3 +54,16 @@ def mixed_model(n=5, seed=3):
     m["beam_conn"] = np.asarray(conn, np.int32)
     m["beam_props"] = np.tile([2e11, 8e10, 2e-6, 3e-6, 4e-6, 1e-3], (len(conn), 1))
     return m
+
+
+def hub_model(n_side=8, hub=27):
+    """Grid-shell with one node braced to every other node: the hub's block
+    row is long enough that its tile cannot be staged in shared memory."""
+    m = meshgen.gridshell(n_side=n_side, seed=7)
+    have = {tuple(sorted(e)) for e in m["beam_conn"].tolist()}
+    extra = [(hub, k) for k in range(n_side * n_side)
+             if k != hub and tuple(sorted((hub, k))) not in have]
+    conn = np.concatenate([m["beam_conn"], np.asarray(extra, np.int32)])
+    m["beam_conn"] = conn.astype(np.int32)
+    m["beam_props"] = np.tile(m["beam_props"][:1], (conn.shape[0], 1))
+    return m

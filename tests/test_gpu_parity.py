@@ -10,8 +10,8 @@ import pytest
 import torch
 
 import meshgen
-from gpu_util import (TOL_ELEMENT, TOL_FP32_IR, TOL_FP64, bsr_to_dense, mixed_model, rel,
-                      small_shell, with_supports)
+from gpu_util import (TOL_ELEMENT, TOL_FP32_IR, TOL_FP64, bsr_to_dense, hub_model, mixed_model,
+                      rel, small_shell, with_supports)
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,7 @@ MODELS = {
     "shell9_clamped": lambda: meshgen.shell(n_el=9, span=8.0, supports="clamped",
                                             load="pressure", seed=4),
     "mixed": lambda: mixed_model(5),
+    "hub": lambda: hub_model(),
 }
 
 
