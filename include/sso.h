@@ -236,6 +236,52 @@ sso_status sso_batch_set_profiling(sso_batch* batch, int32_t enable);
 sso_status sso_batch_kernel_times(const sso_batch* batch, double* ms_a, double* ms_b,
                                   int64_t* launches);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of design evaluations.  Each request is one
+ * structure (any size, any topology) whose solve and adjoint gradient of
+ * J = w C (compliance, Sec. 2.3; dJ/dz per node, dJ/dt per quad, Eqs. 5-6)
+ * are wanted.  A server keeps up to max_systems requests resident on the GPU
+ * (their patterns, K, preconditioners and solver state), within
+ * hbm_budget_bytes of per-request device memory and max_tiles tiles of 30
+ * nodes.  Every sso_server_step runs one captured CUDA graph of CG iterations
+ * over the resident systems; meanwhile it admits waiting requests as slots,
+ * tiles and budget allow (their element matrices, assembly and preconditioner
+ * run on a second stream and overlap the CG), and when a system has converged
+ * it computes its gradient, stores the result on the host and releases its
+ * memory.  A request's result is bit-identical to solving it alone with the
+ * same options (sso_model_solve + sso_model_gradient(w, NULL)).  The server
+ * runs on streams of its own; every call returns with the host-visible state
+ * up to date.  Not thread-safe.
+ */
+typedef struct sso_server sso_server;
+
+sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
+                             int32_t max_systems, int32_t max_tiles, sso_server** out);
+void sso_server_destroy(sso_server* server);
+
+/* Queue a request; the mesh (host or device arrays) is copied.  A NULL or
+ * incomplete mesh is rejected here (SSO_ERR_INVALID); a mesh whose contents
+ * are invalid (node indices, non-finite values) is reported by the request's
+ * result status, as is one that can never fit the budget (SSO_ERR_OOM). */
+sso_status sso_server_submit(sso_server* server, const sso_mesh* mesh, double w,
+                             uint64_t* ticket);
+
+/* One round: a graph launch of CG iterations, admissions, harvesting.
+ * n_resident = requests on the GPU, n_waiting = requests queued.  A CUDA
+ * error (SSO_ERR_CUDA) is fatal for the server: destroy it.  With
+ * SSO_DEBUG_SYNC=1 in the environment every model's scatter map is checked
+ * on the host and each phase of the step is synchronised, so that an error
+ * names the phase it came from. */
+sso_status sso_server_step(sso_server* server, int32_t* n_resident, int32_t* n_waiting);
+
+/* Result of a finished request: SSO_ERR_NOT_READY while it is queued or
+ * running; otherwise SSO_OK, the outputs are filled (any pointer may be NULL;
+ * u [6*n_nodes], C [1], dz [n_nodes], dt [n_quads], host or device), stats
+ * holds the request's status and CG statistics, latency_ms the time from
+ * submission to result, and the request is forgotten. */
+sso_status sso_server_poll(sso_server* server, uint64_t ticket, double* u, double* C,
+                           double* dz, double* dt, sso_stats* stats, double* latency_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,14 @@ SIGNATURES = {
     "sso_batch_gradient": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_vp),
                             ctypes.POINTER(Stats)], _i32),
     "sso_batch_set_profiling": ([_vp, _i32], _i32),
+    "sso_server_create": ([ctypes.POINTER(Options), ctypes.c_size_t, _i32, _i32,
+                           ctypes.POINTER(_vp)], _i32),
+    "sso_server_destroy": ([_vp], None),
+    "sso_server_submit": ([_vp, ctypes.POINTER(Mesh), _f64, ctypes.POINTER(ctypes.c_uint64)],
+                          _i32),
+    "sso_server_step": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
+    "sso_server_poll": ([_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats),
+                         ctypes.POINTER(_f64)], _i32),
     "sso_batch_kernel_times": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64),
                                 ctypes.POINTER(ctypes.c_int64)], _i32),
 }

@@ -16,7 +16,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -42,6 +45,17 @@ sso_status cuda_fail(cudaError_t e, const char* what) {
     return fail(SSO_ERR_OOM, buf);
   }
   return fail(SSO_ERR_CUDA, buf);
+}
+
+// SSO_DEBUG_SYNC=1 in the environment: every model's scatter map is checked
+// on the host before upload, and the server synchronises after each of its
+// phases and reports the phase in which a CUDA error appeared.
+bool debug_sync() {
+  static const bool on = [] {
+    const char* v = std::getenv("SSO_DEBUG_SYNC");
+    return v && v[0] == '1';
+  }();
+  return on;
 }
 
 #define CK(expr)                                         \
@@ -118,6 +132,7 @@ struct sso_model {
   double pressure = 0.0, gamma = 0.0;
   std::vector<int> h_row_ptr, h_col;
   void* arena = nullptr;
+  size_t arena_bytes = 0;  // size of the arena (fixed at creation)
   // topology
   int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_brow, *d_diag, *d_cptr, *d_csrc,
       *d_nptr, *d_nsrc;
@@ -320,6 +335,46 @@ void build_topology(const HostMesh& m, HostTopo& T) {
     std::vector<int> fill(T.nptr.begin(), T.nptr.end() - 1);
     for (int s = 0; s < n_slots; ++s) T.nsrc[fill[slot_node[s]]++] = s;
   }
+}
+
+// Every index the set-up and CG kernels follow, checked against the extents
+// of the arrays it indexes (the SSO_DEBUG_SYNC check).
+bool topology_consistent(const HostMesh& m, const HostTopo& T) {
+  const int n = m.n_nodes;
+  const long long nb = (long long)T.col.size(), n_eb = (long long)T.csrc.size();
+  const long long n_slots = (long long)T.nsrc.size();
+  if ((long long)T.row_ptr.size() != n + 1 || T.row_ptr[0] != 0 || T.row_ptr[n] != nb) return false;
+  for (int i = 0; i < n; ++i) {
+    if (T.row_ptr[i + 1] <= T.row_ptr[i]) return false;
+    const int d = T.diag[i];
+    if (d < T.row_ptr[i] || d >= T.row_ptr[i + 1] || T.col[d] != i) return false;
+    for (int b = T.row_ptr[i]; b < T.row_ptr[i + 1]; ++b)
+      if (T.col[b] < 0 || T.col[b] >= n || T.brow[b] != i) return false;
+  }
+  if ((long long)T.cptr.size() != nb + 1 || T.cptr[0] != 0 || T.cptr[nb] != n_eb) return false;
+  for (long long b = 0; b < nb; ++b)
+    if (T.cptr[b + 1] < T.cptr[b]) return false;
+  std::vector<char> seen(n_eb, 0);
+  for (long long k = 0; k < n_eb; ++k) {
+    const int e = T.csrc[k];
+    if (e < 0 || e >= n_eb || seen[e]) return false;
+    seen[e] = 1;
+  }
+  if (n_eb != 4LL * m.n_beams + 16LL * m.n_quads) return false;
+  if ((long long)T.nptr.size() != n + 1 || T.nptr[0] != 0 || T.nptr[n] != n_slots) return false;
+  for (int i = 0; i < n; ++i)
+    if (T.nptr[i + 1] < T.nptr[i]) return false;
+  std::vector<char> seen2(n_slots, 0);
+  for (long long k = 0; k < n_slots; ++k) {
+    const int q = T.nsrc[k];
+    if (q < 0 || q >= n_slots || seen2[q]) return false;
+    seen2[q] = 1;
+  }
+  for (int v : m.beam_conn)
+    if (v < 0 || v >= n) return false;
+  for (int v : m.quad_conn)
+    if (v < 0 || v >= n) return false;
+  return true;
 }
 
 // Lays out (base == nullptr: sizes only) every device array of a model.
@@ -725,6 +780,8 @@ sso_status sso_model_create(const sso_mesh* mesh, void* stream, sso_model** out)
 
   HostTopo T;
   build_topology(hm, T);
+  if (debug_sync() && !topology_consistent(hm, T))
+    return fail(SSO_ERR_INVALID, "scatter map inconsistent (internal error)");
 
   sso_model* M = new sso_model();
   CK(cudaGetDevice(&M->device));
@@ -750,6 +807,7 @@ sso_status sso_model_create(const sso_mesh* mesh, void* stream, sso_model** out)
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "stream/event creation"));
   const size_t bytes = layout_model(M, nullptr);
+  M->arena_bytes = bytes;
   e = cudaMalloc(&M->arena, bytes);
   if (e != cudaSuccess) {
     M->arena = nullptr;
@@ -1111,6 +1169,483 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
     CK(cudaStreamWaitEvent(M->user_stream, M->ev_out, 0));
   }
   return run;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Serving: continuous batching of design evaluations (solve + adjoint z / t
+// gradient of J = w C).  A server owns a batch sized for its capacity
+// (max_systems systems, max_tiles tiles) whose system table and tile list
+// are rewritten between CUDA-graph launches of the CG engine: finished
+// systems leave, newly admitted ones join, without waiting for the others.
+// Admission is by free slot, free tiles and an HBM budget; a request's model
+// (its pattern, K, preconditioner and solver state) stays resident until its
+// result has been produced.
+
+namespace {
+
+struct ServerReq {
+  uint64_t ticket = 0;
+  HostMesh mesh;
+  double w = 1.0;
+  double t_submit = 0.0, t_done = 0.0;  // ms since the server was created
+  int slot = -1;
+  int phase = 0;  // 0 queued, 1 setting up, 2 in CG, 3 result ready
+  sso_model* M = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t ev_setup = nullptr;
+  sso_stats stats{};
+  std::vector<double> u, dz, dt;
+  double C = 0.0;
+};
+
+// Device bytes a model holds.  (Never layout_model on a live model: with a
+// null base it re-carves every device pointer of the model from address 0.)
+size_t model_bytes(const sso_model* M) { return M->arena_bytes; }
+
+// A batch with room for max_sys systems and max_tiles tiles and no models,
+// running on `stream`.
+sso_status batch_with_capacity(cudaStream_t stream, int max_sys, int max_tiles,
+                               sso_batch** out) {
+  sso_batch* B = new sso_batch();
+  B->stream = stream;
+  B->n_sys = max_sys;
+  B->n_tiles = max_tiles;  // sizes the graph's grids; the live count is on the device
+  B->h_sys.assign(max_sys, SysDesc{});
+  Carver c(nullptr);
+  c.take<SysDesc>(max_sys);
+  c.take<SysScalars>(max_sys);
+  c.take<TileDesc>(max_tiles);
+  c.take<int>(1);
+  c.take<int>(2);
+  c.take<double>(max_sys);
+  const size_t bytes = align_up(c.off, 256);
+  cudaError_t e = cudaMalloc(&B->arena, bytes);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "cudaMalloc(server tables)");
+  }
+  Carver d(B->arena);
+  B->d_sys = d.take<SysDesc>(max_sys);
+  B->d_sc = d.take<SysScalars>(max_sys);
+  B->d_tiles = d.take<TileDesc>(max_tiles);
+  B->d_n_tiles = d.take<int>(1);
+  B->d_n_active = d.take<int>(2);
+  B->d_dots = d.take<double>(max_sys);
+  for (int s = 0; s < max_sys; ++s) B->h_sys[s].sc = B->d_sc + s;
+  e = cudaMallocHost(&B->h_sc, sizeof(SysScalars) * max_sys);
+  if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->arena, 0, bytes, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    sso_batch_destroy(B);
+    return cuda_fail(e, "server tables");
+  }
+  *out = B;
+  return SSO_OK;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct sso_server {
+  sso_options opts;
+  size_t budget = 0, used = 0;
+  int max_sys = 0, max_tiles = 0;
+  cudaStream_t cg_stream = nullptr, setup_stream = nullptr;
+  sso_batch* B = nullptr;
+  SysScalars* h_up = nullptr;  // pinned upload staging, one per slot
+  std::deque<ServerReq*> queue;
+  std::unordered_map<uint64_t, ServerReq*> reqs;
+  std::vector<ServerReq*> slot_req;
+  std::vector<int> running, pending;
+  std::vector<std::vector<TileDesc>> slot_tiles;  // tile descriptors of each slot's model
+  int tiles_used = 0;  // tiles of running + pending systems
+  uint64_t next_ticket = 1;
+  std::chrono::steady_clock::time_point t0;
+  bool dirty = false;
+};
+
+namespace {
+
+// Host copy of a mesh given by host or device pointers.
+sso_status mesh_to_host(const sso_mesh* mesh, HostMesh& hm) {
+  if (!mesh) return fail(SSO_ERR_INVALID, "mesh is NULL");
+  if (mesh->n_nodes <= 0 || mesh->n_beams < 0 || mesh->n_quads < 0 ||
+      mesh->n_beams + mesh->n_quads == 0 || !mesh->xyz || !mesh->fixed || !mesh->nodal_load ||
+      (mesh->n_beams > 0 && (!mesh->beam_conn || !mesh->beam_props)) ||
+      (mesh->n_quads > 0 && (!mesh->quad_conn || !mesh->quad_props)))
+    return fail(SSO_ERR_INVALID, "incomplete mesh");
+  hm.n_nodes = mesh->n_nodes;
+  hm.n_beams = mesh->n_beams;
+  hm.n_quads = mesh->n_quads;
+  hm.pressure = mesh->pressure;
+  hm.gamma = mesh->gamma;
+  hm.xyz.resize(3 * (size_t)hm.n_nodes);
+  hm.nodal_load.resize(6 * (size_t)hm.n_nodes);
+  hm.fixed.resize(6 * (size_t)hm.n_nodes);
+  hm.beam_conn.resize(2 * (size_t)hm.n_beams);
+  hm.beam_props.resize(6 * (size_t)hm.n_beams);
+  hm.quad_conn.resize(4 * (size_t)hm.n_quads);
+  hm.quad_props.resize(5 * (size_t)hm.n_quads);
+  CK(to_host(hm.xyz.data(), mesh->xyz, hm.xyz.size() * sizeof(double)));
+  CK(to_host(hm.nodal_load.data(), mesh->nodal_load, hm.nodal_load.size() * sizeof(double)));
+  CK(to_host(hm.fixed.data(), mesh->fixed, hm.fixed.size()));
+  CK(to_host(hm.beam_conn.data(), mesh->beam_conn, hm.beam_conn.size() * sizeof(int)));
+  CK(to_host(hm.beam_props.data(), mesh->beam_props, hm.beam_props.size() * sizeof(double)));
+  CK(to_host(hm.quad_conn.data(), mesh->quad_conn, hm.quad_conn.size() * sizeof(int)));
+  CK(to_host(hm.quad_props.data(), mesh->quad_props, hm.quad_props.size() * sizeof(double)));
+  return SSO_OK;
+}
+
+sso_mesh mesh_view(const HostMesh& hm) {
+  sso_mesh m;
+  m.n_nodes = hm.n_nodes;
+  m.xyz = hm.xyz.data();
+  m.n_beams = hm.n_beams;
+  m.beam_conn = hm.beam_conn.data();
+  m.beam_props = hm.beam_props.data();
+  m.n_quads = hm.n_quads;
+  m.quad_conn = hm.quad_conn.data();
+  m.quad_props = hm.quad_props.data();
+  m.fixed = hm.fixed.data();
+  m.nodal_load = hm.nodal_load.data();
+  m.pressure = hm.pressure;
+  m.gamma = hm.gamma;
+  return m;
+}
+
+sso_status debug_check(cudaStream_t s, const char* phase) {
+  if (!debug_sync()) return SSO_OK;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, phase);
+  return SSO_OK;
+}
+
+// Tile list and system table of the running systems, in slot order.
+sso_status server_upload_tables(sso_server* S, std::vector<std::vector<TileDesc>>& tile_cache) {
+  sso_batch* B = S->B;
+  std::sort(S->running.begin(), S->running.end());
+  // every index the kernels will follow, checked before it reaches the device
+  for (int slot : S->running) {
+    const ServerReq* R = (slot >= 0 && slot < S->max_sys) ? S->slot_req[slot] : nullptr;
+    const sso_model* M = R ? R->M : nullptr;
+    const SysDesc& D = B->h_sys[slot];
+    bool ok = M && (int)tile_cache[slot].size() == M->n_tiles && D.n_nodes == M->n_nodes &&
+              D.n_tiles == M->n_tiles && D.x == M->d_u && D.b == M->d_f && D.K32 == M->d_K32 &&
+              D.col == M->d_col && D.row_ptr == M->d_row_ptr && D.sc == B->d_sc + slot;
+    for (const TileDesc& td : tile_cache[slot])
+      ok = ok && td.sys == slot && td.node0 >= 0 && td.nn > 0 && td.node0 + td.nn <= M->n_nodes &&
+           td.j0 == M->h_row_ptr[td.node0] &&
+           td.j0 + td.nblk == M->h_row_ptr[td.node0 + td.nn];
+    if (!ok) return fail(SSO_ERR_INVALID, "server tables inconsistent (internal error)");
+  }
+  std::vector<TileDesc> tiles;
+  tiles.reserve(S->tiles_used);
+  for (int slot : S->running) {
+    B->h_sys[slot].tile0 = (int)tiles.size();
+    tiles.insert(tiles.end(), tile_cache[slot].begin(), tile_cache[slot].end());
+  }
+  const int n = (int)tiles.size();
+  if (n > 0)
+    CK(cudaMemcpyAsync(B->d_tiles, tiles.data(), n * sizeof(TileDesc), cudaMemcpyHostToDevice,
+                       B->stream));
+  CK(cudaMemcpyAsync(B->d_n_tiles, &n, sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * S->max_sys,
+                     cudaMemcpyHostToDevice, B->stream));
+  CK(cudaStreamSynchronize(B->stream));  // the host vectors above are temporaries
+  S->dirty = false;
+  return SSO_OK;
+}
+
+void fill_sysdesc(SysDesc& D, sso_model* M, int precond) {
+  D.n_nodes = M->n_nodes;
+  D.n_tiles = M->n_tiles;
+  D.precond = precond;
+  D.row_ptr = M->d_row_ptr;
+  D.col = M->d_col;
+  D.K32 = M->d_K32;
+  D.K64 = M->d_K64;
+  D.M32 = M->d_M32;
+  D.M64 = M->d_M64;
+  D.b = M->d_f;
+  D.x = M->d_u;
+  D.r64 = M->d_r64;
+  D.r = M->d_r;
+  D.z = M->d_z;
+  D.p0 = M->d_p0;
+  D.p1 = M->d_p1;
+  D.q = M->d_q;
+  D.part_a = M->d_part_a;
+  D.part_b = M->d_part_b;
+}
+
+void init_scalars(SysScalars& S, const sso_options& o) {
+  std::memset(&S, 0, sizeof(S));
+  const double inner = o.precision == SSO_FP64 ? 0.0 : o.inner_rtol;
+  S.state = ST_INIT;
+  S.status = SSO_ERR_NOT_CONVERGED;
+  S.rtol2 = o.rtol * o.rtol;
+  S.inner_rtol2 = inner * inner;
+  S.max_iter = o.max_iter;
+  S.max_sweeps = o.max_sweeps;
+}
+
+}  // namespace
+
+extern "C" {
+
+sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
+                             int32_t max_systems, int32_t max_tiles, sso_server** out) {
+  if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  sso_status st = check_options(opts);
+  if (st != SSO_OK) return st;
+  if (max_systems <= 0 || max_tiles <= 0 || hbm_budget_bytes == 0)
+    return fail(SSO_ERR_INVALID, "need max_systems > 0, max_tiles > 0, budget > 0");
+  sso_server* S = new sso_server();
+  S->opts = *opts;
+  S->opts.warm_start = 0;
+  S->budget = hbm_budget_bytes;
+  S->max_sys = max_systems;
+  S->max_tiles = max_tiles;
+  S->slot_req.assign(max_systems, nullptr);
+  S->slot_tiles.assign(max_systems, {});
+  S->t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaStreamCreateWithFlags(&S->cg_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_up, sizeof(SysScalars) * max_systems);
+  if (e != cudaSuccess) {
+    sso_server_destroy(S);
+    return cuda_fail(e, "server streams");
+  }
+  st = batch_with_capacity(S->cg_stream, max_systems, max_tiles, &S->B);
+  if (st != SSO_OK) {
+    sso_server_destroy(S);
+    return st;
+  }
+  *out = S;
+  return SSO_OK;
+}
+
+void sso_server_destroy(sso_server* S) {
+  if (!S) return;
+  if (S->cg_stream) cudaStreamSynchronize(S->cg_stream);
+  if (S->setup_stream) cudaStreamSynchronize(S->setup_stream);
+  for (auto& kv : S->reqs) {
+    ServerReq* R = kv.second;
+    if (R->M) sso_model_destroy(R->M);
+    if (R->ev_setup) cudaEventDestroy(R->ev_setup);
+    delete R;
+  }
+  if (S->B) sso_batch_destroy(S->B);
+  if (S->h_up) cudaFreeHost(S->h_up);
+  if (S->cg_stream) cudaStreamDestroy(S->cg_stream);
+  if (S->setup_stream) cudaStreamDestroy(S->setup_stream);
+  delete S;
+}
+
+sso_status sso_server_submit(sso_server* S, const sso_mesh* mesh, double w, uint64_t* ticket) {
+  if (!S || !ticket) return fail(SSO_ERR_INVALID, "NULL argument");
+  ServerReq* R = new ServerReq();
+  sso_status st = mesh_to_host(mesh, R->mesh);
+  if (st != SSO_OK) {
+    delete R;
+    return st;
+  }
+  R->ticket = S->next_ticket++;
+  R->w = w;
+  R->t_submit = ms_since(S->t0);
+  S->reqs[R->ticket] = R;
+  S->queue.push_back(R);
+  *ticket = R->ticket;
+  return SSO_OK;
+}
+
+sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting) {
+  if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
+  sso_batch* B = S->B;
+  const bool fp64 = S->opts.precision == SSO_FP64;
+  const int k = fp64 ? 1 : 0;
+  const int iters = S->opts.iters_per_launch;
+  sso_status st;
+  // 1. one graph launch of CG iterations over the running systems
+  bool launched = false;
+  if (!S->running.empty()) {
+    if (S->dirty && (st = server_upload_tables(S, S->slot_tiles)) != SSO_OK) return st;
+    B->h_flag[0] = (int)S->running.size();
+    B->h_flag[1] = 0;
+    CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
+                       B->stream));
+    if ((st = batch_graph(B, fp64, iters)) != SSO_OK) return st;
+    CK(cudaGraphLaunch(B->exec[k], B->stream));
+    g_launches += 2ull * (unsigned long long)iters;
+    if ((st = debug_check(B->stream, "server: CG graph")) != SSO_OK) return st;
+    CK(cudaMemcpyAsync(B->h_flag + 2, B->d_n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                       B->stream));
+    CK(cudaMemcpyAsync(B->h_sc, B->d_sc, sizeof(SysScalars) * S->max_sys,
+                       cudaMemcpyDeviceToHost, B->stream));
+    CK(cudaEventRecord(B->ev, B->stream));
+    launched = true;
+  }
+  // 2. admission while the GPU iterates: build models, set them up on the
+  //    set-up stream (their kernels overlap the CG graph)
+  while (!S->queue.empty()) {
+    int slot = -1;
+    for (int s2 = 0; s2 < S->max_sys; ++s2)
+      if (!S->slot_req[s2]) {
+        slot = s2;
+        break;
+      }
+    if (slot < 0) break;
+    ServerReq* R = S->queue.front();
+    sso_mesh m = mesh_view(R->mesh);
+    sso_model* M = nullptr;
+    st = sso_model_create(&m, nullptr, &M);
+    if (st == SSO_ERR_CUDA) return st;  // the device, not the request, failed
+    if (st != SSO_OK) {  // invalid request (or one that cannot be allocated)
+      S->queue.pop_front();
+      R->stats.status = st;
+      R->phase = 3;
+      R->t_done = ms_since(S->t0);
+      continue;
+    }
+    const size_t bytes = model_bytes(M);
+    const bool idle = S->running.empty() && S->pending.empty();
+    if (S->tiles_used + M->n_tiles > S->max_tiles || S->used + bytes > S->budget) {
+      sso_model_destroy(M);
+      if (!idle) break;  // wait for finished systems to free room
+      S->queue.pop_front();
+      R->stats.status = SSO_ERR_OOM;  // can never fit
+      R->phase = 3;
+      R->t_done = ms_since(S->t0);
+      continue;
+    }
+    S->queue.pop_front();
+    if ((st = debug_check(S->setup_stream, "server: before set-up")) != SSO_OK) return st;
+    if ((st = setup_model(M, S->opts.precond, S->setup_stream)) != SSO_OK) return st;
+    CK(cudaMemsetAsync(M->d_u, 0, sizeof(double) * 6 * (size_t)M->n_nodes, S->setup_stream));
+    if ((st = debug_check(S->setup_stream, "server: set-up kernels")) != SSO_OK) return st;
+    CK(cudaEventCreateWithFlags(&R->ev_setup, cudaEventDisableTiming));
+    CK(cudaEventRecord(R->ev_setup, S->setup_stream));
+    R->M = M;
+    R->bytes = bytes;
+    R->slot = slot;
+    R->phase = 1;
+    S->slot_req[slot] = R;
+    S->slot_tiles[slot].clear();
+    for (int t = 0; t < M->n_tiles; ++t) S->slot_tiles[slot].push_back(make_tile(M, slot, t));
+    fill_sysdesc(B->h_sys[slot], M, S->opts.precond);
+    S->tiles_used += M->n_tiles;
+    S->used += bytes;
+    S->pending.push_back(slot);
+  }
+  // 3. wait for the launch; harvest the systems that finished
+  if (launched) {
+    CK(cudaEventSynchronize(B->ev));
+    if (B->h_flag[3] != 0)
+      return fail(SSO_ERR_CUDA, "CG kernel gave up waiting for a bulk copy (device fault?)");
+    std::vector<int> done;
+    for (int slot : S->running)
+      if (B->h_sc[slot].state == ST_DONE) done.push_back(slot);
+    for (int slot : done) {
+      ServerReq* R = S->slot_req[slot];
+      sso_model* M = R->M;
+      const size_t ndof = 6 * (size_t)M->n_nodes;
+      cudaStream_t s2 = B->stream;
+      CL(launch_axpby((int)ndof, R->w, M->d_u, nullptr, M->d_fixed, M->d_lam, s2), 1);
+      CL(launch_beam_adjoint(M->n_beams, M->d_xyz, M->d_beam_conn, M->d_beam_props, M->d_u,
+                             M->d_u, R->w, M->d_gslot, s2),
+         M->n_beams > 0);
+      CL(launch_quad_adjoint(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props,
+                             M->pressure, M->gamma, M->d_u, M->d_u, R->w, R->w,
+                             M->d_gslot + 2 * (size_t)M->n_beams, M->d_dt, s2),
+         M->n_quads > 0);
+      CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, nullptr,
+                            M->d_gslot, nullptr, M->d_fixed, nullptr, M->d_dz, s2),
+         1);
+      CL(launch_dot(1, B->d_sys + slot, B->d_dots + slot, s2), 1);
+      R->u.resize(ndof);
+      R->dz.resize(M->n_nodes);
+      R->dt.resize(M->n_quads);
+      CK(cudaMemcpyAsync(R->u.data(), M->d_u, ndof * 8, cudaMemcpyDeviceToHost, s2));
+      CK(cudaMemcpyAsync(R->dz.data(), M->d_dz, M->n_nodes * 8, cudaMemcpyDeviceToHost, s2));
+      if (M->n_quads > 0)
+        CK(cudaMemcpyAsync(R->dt.data(), M->d_dt, M->n_quads * 8, cudaMemcpyDeviceToHost, s2));
+      CK(cudaMemcpyAsync(&R->C, B->d_dots + slot, 8, cudaMemcpyDeviceToHost, s2));
+    }
+    if (!done.empty()) CK(cudaStreamSynchronize(B->stream));
+    if ((st = debug_check(B->stream, "server: gradients")) != SSO_OK) return st;
+    const double now = ms_since(S->t0);
+    for (int slot : done) {
+      ServerReq* R = S->slot_req[slot];
+      const SysScalars& sc = B->h_sc[slot];
+      int err = 0;
+      CK(cudaMemcpy(&err, R->M->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      R->stats.status = err ? SSO_ERR_SINGULAR : sc.status;
+      R->stats.iterations = sc.iters;
+      R->stats.sweeps = sc.sweeps;
+      R->stats.rel_residual = sc.ff > 0.0 ? std::sqrt(sc.rr64 / sc.ff) : 0.0;
+      R->stats.ms = now - R->t_submit;
+      R->t_done = now;
+      R->phase = 3;
+      S->used -= R->bytes;
+      S->tiles_used -= R->M->n_tiles;
+      sso_model_destroy(R->M);
+      R->M = nullptr;
+      S->slot_req[slot] = nullptr;
+      S->running.erase(std::find(S->running.begin(), S->running.end(), slot));
+      S->dirty = true;
+    }
+  }
+  // 4. systems whose set-up has finished join the CG
+  for (size_t i = 0; i < S->pending.size();) {
+    const int slot = S->pending[i];
+    ServerReq* R = S->slot_req[slot];
+    cudaError_t q = cudaEventQuery(R->ev_setup);
+    if (q == cudaErrorNotReady) {
+      ++i;
+      continue;
+    }
+    if (q != cudaSuccess) return cuda_fail(q, "set-up of an admitted request");
+    init_scalars(S->h_up[slot], S->opts);
+    CK(cudaMemcpyAsync(B->d_sc + slot, S->h_up + slot, sizeof(SysScalars),
+                       cudaMemcpyHostToDevice, B->stream));
+    R->phase = 2;
+    S->running.push_back(slot);
+    S->pending.erase(S->pending.begin() + i);
+    S->dirty = true;
+  }
+  if (n_running) *n_running = (int)(S->running.size() + S->pending.size());
+  if (n_waiting) *n_waiting = (int)S->queue.size();
+  return SSO_OK;
+}
+
+sso_status sso_server_poll(sso_server* S, uint64_t ticket, double* u, double* C, double* dz,
+                           double* dt, sso_stats* stats, double* latency_ms) {
+  if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(SSO_ERR_INVALID, "unknown ticket");
+  ServerReq* R = it->second;
+  if (R->phase != 3) return SSO_ERR_NOT_READY;
+  if (u && !R->u.empty()) CK(cudaMemcpy(u, R->u.data(), R->u.size() * 8, cudaMemcpyDefault));
+  if (C) CK(cudaMemcpy(C, &R->C, 8, cudaMemcpyDefault));
+  if (dz && !R->dz.empty())
+    CK(cudaMemcpy(dz, R->dz.data(), R->dz.size() * 8, cudaMemcpyDefault));
+  if (dt && !R->dt.empty())
+    CK(cudaMemcpy(dt, R->dt.data(), R->dt.size() * 8, cudaMemcpyDefault));
+  if (stats) *stats = R->stats;
+  if (latency_ms) *latency_ms = R->t_done - R->t_submit;
+  if (R->ev_setup) cudaEventDestroy(R->ev_setup);
+  S->reqs.erase(it);
+  delete R;
+  return SSO_OK;
 }
 
 }  // extern "C"

@@ -673,7 +673,14 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       s_abort = 1;
       atomicExch(flags + 1, 1);
     }
-    const StageInfo inf = info[s];
+    // a dry warp takes nothing from the stage (it may never have been
+    // written): the system and its state come from global memory, as the
+    // producer read them, so the warp keeps the others' barrier pattern
+    StageInfo inf = info[s];
+    if (dry) {
+      inf.sys = tiles[tile].sys;
+      inf.state = read_state(sys[inf.sys].sc).state;
+    }
     const SysDesc& S = sys[inf.sys];
     SysScalars* sc = S.sc;
     const int real_state = inf.state;

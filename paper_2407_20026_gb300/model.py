@@ -60,27 +60,34 @@ def kernel_launches() -> int:
     return int(_lib.load().sso_kernel_launches())
 
 
+def mesh_struct(mesh):
+    """(sso_mesh, keep-alive list) for a model dict (see meshgen)."""
+    keep = []
+
+    def p(key, dtype):
+        ptr, k = _buf(mesh[key], dtype)
+        keep.append(k)
+        return ptr
+
+    m = _lib.Mesh(int(mesh["xyz"].shape[0]), p("xyz", torch.float64),
+                  int(mesh["beam_conn"].shape[0]), p("beam_conn", torch.int32),
+                  p("beam_props", torch.float64),
+                  int(mesh["quad_conn"].shape[0]), p("quad_conn", torch.int32),
+                  p("quad_props", torch.float64), p("fixed", torch.uint8),
+                  p("nodal_load", torch.float64),
+                  float(mesh.get("pressure", 0.0)), float(mesh.get("gamma", 0.0)))
+    return m, keep
+
+
 class Model:
     """One structure (sso_model): nodes, beams, quads, supports, loads."""
 
     def __init__(self, mesh: dict, stream=None):
         lib = _lib.load()
-        keep = []
-
-        def p(key, dtype):
-            ptr, k = _buf(mesh[key], dtype)
-            keep.append(k)
-            return ptr
-
-        xyz = mesh["xyz"]
-        self.n_nodes = int(xyz.shape[0])
-        self.n_beams = int(mesh["beam_conn"].shape[0])
-        self.n_quads = int(mesh["quad_conn"].shape[0])
-        m = _lib.Mesh(self.n_nodes, p("xyz", torch.float64),
-                      self.n_beams, p("beam_conn", torch.int32), p("beam_props", torch.float64),
-                      self.n_quads, p("quad_conn", torch.int32), p("quad_props", torch.float64),
-                      p("fixed", torch.uint8), p("nodal_load", torch.float64),
-                      float(mesh.get("pressure", 0.0)), float(mesh.get("gamma", 0.0)))
+        m, keep = mesh_struct(mesh)
+        self.n_nodes = m.n_nodes
+        self.n_beams = m.n_beams
+        self.n_quads = m.n_quads
         h = ctypes.c_void_p()
         _lib.check(lib.sso_model_create(ctypes.byref(m), ctypes.c_void_p(_stream_ptr(stream)),
                                         ctypes.byref(h)))
