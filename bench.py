@@ -53,6 +53,19 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=3, help="oracle designs in cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="shell",
+                   choices=["shell", "serving", "gridshell", "large"],
+                   help="shell: batches of 64x64 shell designs (default line); serving: "
+                        "continuous batching of a grid-shell request stream; gridshell: "
+                        "latency of one 10x10 grid-shell evaluation; large: one 512x512 shell")
+    p.add_argument("--requests", type=int, default=512, help="serving: requests per run")
+    p.add_argument("--rates", default="0.5,0.9",
+                   help="serving: Poisson arrival rates as fractions of saturated throughput")
+    p.add_argument("--hbm-budget-gb", type=float, default=64.0)
+    p.add_argument("--max-systems", type=int, default=512)
+    p.add_argument("--alone-sample", type=int, default=16,
+                   help="serving: requests timed one at a time on the FP64 path")
+    p.add_argument("--repeats", type=int, default=1000, help="gridshell: timed evaluations")
     return p.parse_args()
 
 
@@ -203,10 +216,287 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (one GPU each; one JSON line each)
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x, float), q)) if len(x) else None
+
+
+def _gpu_setup():
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import paper_2407_20026_gb300 as sso
+    from paper_2407_20026_gb300 import _build
+    _build.build()
+    return torch, sso, local
+
+
+def _mesh_bytes(m):
+    n = m["xyz"].shape[0]
+    nb = len(m["beam_conn"])
+    nq = len(m["quad_conn"])
+    return n * (3 * 8 + 6 + 6 * 8) + nb * (2 * 4 + 6 * 8) + nq * (4 * 4 + 5 * 8)
+
+
+def run_serving(a):
+    """Serving stream: grid-shell requests of n x n nodes, n ~ U{8..100}
+    (seeded), plan and load as the 10 x 10 grid-shell; each request is solved
+    and its adjoint dC/dz computed by the continuous-batching server.  Runs
+    the stream saturated (every request queued at t = 0: throughput) and as
+    Poisson arrivals at fractions of that throughput (latency from arrival),
+    then times a sample of the same requests one at a time on the FP64
+    single-model path."""
+    torch, sso, local = _gpu_setup()
+    from paper_2407_20026_gb300.serve import Server, run_stream
+    spec = meshgen.serving_stream(a.requests, seed=0)
+    meshes = [meshgen.gridshell(n_side=r["side"], seed=r["seed"]) for r in spec]
+    dofs = [6 * m["xyz"].shape[0] for m in meshes]
+    opts = sso.options(precision=a.precision, precond=a.precond, rtol=a.rtol,
+                       inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch)
+    srv = Server(opts, hbm_budget=int(a.hbm_budget_gb * (1 << 30)), max_systems=a.max_systems)
+    warm = [{"mesh": meshgen.gridshell(n_side=8 + 4 * k, seed=10 ** 6 + k), "t_arrive": 0.0}
+            for k in range(max(a.warmup, 1))]
+    run_stream(srv, warm)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sso.kernel_launches()
+    res, elapsed = run_stream(srv, [{"mesh": m, "t_arrive": 0.0} for m in meshes],
+                              time_limit_s=1800.0)
+    launches = sso.kernel_launches() - l0
+    clk = clocks.stop()
+    failed = [i for i, r in enumerate(res) if r["stats"]["status"] != 0]
+    sat = len(meshes) / elapsed
+    iters = [r["stats"]["iterations"] for r in res]
+    lat_sat = [r["latency_ms"] for r in res]
+
+    poisson = []
+    for frac in [float(x) for x in a.rates.split(",") if x]:
+        rate = frac * sat
+        rng = np.random.default_rng(12345)
+        gaps = rng.exponential(1.0 / rate, len(meshes))
+        t = np.cumsum(gaps) - gaps[0]
+        res2, el2 = run_stream(srv, [{"mesh": m, "t_arrive": float(tt)}
+                                     for m, tt in zip(meshes, t)], time_limit_s=1800.0)
+        lat = [r["latency_arrival_ms"] for r in res2]
+        poisson.append({"rate_frac": frac, "offered_per_s": rate,
+                        "achieved_per_s": len(meshes) / el2,
+                        "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                        "failed": sum(r["stats"]["status"] != 0 for r in res2)})
+    srv.close()
+
+    # the plain path: one request at a time, FP64 CG, same rtol
+    o64 = sso.options(precision="fp64", precond=a.precond, rtol=a.rtol,
+                      iters_per_launch=a.iters_per_launch)
+    idx = list(range(min(a.alone_sample, len(meshes))))
+    w = sso.Model(warm[0]["mesh"])
+    w.solve(o64)
+    w.gradient()
+    w.result()
+    w.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in idx:
+        mdl = sso.Model(meshes[i])
+        mdl.solve(o64)
+        mdl.gradient()
+        mdl.result()
+        mdl.close()
+    alone_s = time.perf_counter() - t0
+    alone = len(idx) / alone_s
+
+    line = {
+        "metric": METRIC, "value": sat, "unit": "evals/s", "n_gpus": 1,
+        "steps": len(meshes), "warmup": len(warm), "ms_per_step": 1000.0 / sat,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if a.precision == "fp32_ir" else "f64", "data": "synthetic",
+        "config": {"workload": "serving stream: %d grid-shell requests, n x n nodes with n ~ "
+                               "U{8..100} (seeded), 10 m plan, -1 kN per free node, solve + "
+                               "adjoint dC/dz, %s %s CG to rtol %g; continuous batching"
+                               % (len(meshes), "FP32+FP64 refinement" if a.precision ==
+                                  "fp32_ir" else "FP64", a.precond, a.rtol),
+                   "mean_dof": float(np.mean(dofs)), "max_dof": int(max(dofs)),
+                   "hbm_budget_gb": a.hbm_budget_gb, "max_systems": a.max_systems,
+                   "iters_per_launch": a.iters_per_launch,
+                   "l2": "working set of the resident requests (GBs) > L2"},
+        "saturated": {"evals_per_s": sat, "seconds": elapsed,
+                      "latency_p50_ms": _pct(lat_sat, 50), "latency_p99_ms": _pct(lat_sat, 99),
+                      "cg_iterations_mean": float(np.mean(iters)),
+                      "cg_iterations_max": int(max(iters)), "failed": len(failed),
+                      "pcg_dof_per_s": float(np.dot(iters, dofs)) / elapsed},
+        "poisson": poisson,
+        "one_at_a_time_fp64": {"evals_per_s": alone, "requests": len(idx),
+                               "mean_dof": float(np.mean([dofs[i] for i in idx])),
+                               "speedup_of_serving": sat / alone},
+        "roofline": None,
+        "cpu_baseline": None,
+        "clocks": clk, "gpu_launches": int(launches),
+        "e2e": {"value": sat, "unit": "evals/s",
+                "h2d_bytes_per_step": int(np.mean([_mesh_bytes(m) for m in meshes])),
+                "d2h_bytes_per_step": int(np.mean([8 * (d + d // 6 + 1) for d in dofs])),
+                "note": "the server takes meshes from host memory and returns results to host "
+                        "memory, so value is already end to end"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gridshell(a):
+    """Latency of one evaluation of the 10 x 10 grid-shell (261 beams, 600
+    DOF) in FP64: set design, solve, adjoint dC/dz, results to host."""
+    torch, sso, local = _gpu_setup()
+    m = meshgen.gridshell(n_side=10, seed=0)
+    mdl = sso.Model(m)
+    opts = sso.options(precision="fp64", precond=a.precond, rtol=1e-8,
+                       iters_per_launch=a.iters_per_launch)
+    z = np.ascontiguousarray(m["xyz"][:, 2])
+    for _ in range(max(a.warmup, 3)):
+        mdl.set_design(z)
+        mdl.solve(opts)
+        mdl.gradient()
+        mdl.result()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sso.kernel_launches()
+    lat = []
+    t_all = time.perf_counter()
+    for _ in range(a.repeats):
+        t0 = time.perf_counter()
+        mdl.set_design(z)
+        st = mdl.solve(opts)
+        mdl.gradient()
+        r = mdl.result()
+        lat.append(1e6 * (time.perf_counter() - t0))
+    total = time.perf_counter() - t_all
+    launches = sso.kernel_launches() - l0
+    clk = clocks.stop()
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 5.0 or k < 3:
+            ref = oracle.gradient(m)
+            k += 1
+        dt = time.perf_counter() - t0
+        err = {"u": float(np.linalg.norm(r["u"] - ref["u"]) / np.linalg.norm(ref["u"])),
+               "C": abs(r["C"] - ref["C"]) / abs(ref["C"]),
+               "dz": float(np.linalg.norm(r["dz"] - ref["dz"]) / np.linalg.norm(ref["dz"]))}
+        cpu = {"value": k / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": "%d evaluations of the same design, %.1f s" % (k, dt),
+               "accuracy_of_gpu": err}
+    line = {
+        "metric": METRIC, "value": a.repeats / total, "unit": "evals/s", "n_gpus": 1,
+        "steps": a.repeats, "warmup": max(a.warmup, 3), "ms_per_step": 1000 * total / a.repeats,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "grid-shell 10x10 nodes, 261 beams, 600 DOF, FP64 %s CG to "
+                               "rtol 1e-8, solve + adjoint dC/dz, results to host" % a.precond,
+                   "l2": "problem fits L2 (latency workload)"},
+        "latency_us": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "min": float(min(lat))},
+        "cg_iterations": st["iterations"],
+        "roofline": None, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": {"value": a.repeats / total, "unit": "evals/s",
+                "h2d_bytes_per_step": 8 * len(z), "d2h_bytes_per_step": 8 * (7 * len(z) + 1),
+                "note": "every evaluation uploads z from host and reads u, C, dz back"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_large(a):
+    """One large shell: 512 x 512 quads (263,169 nodes, 1,579,014 DOF), all
+    edges clamped, 5 kPa pressure; FP32 Jacobi CG with FP64 refinement to a
+    relative residual of 1e-8, then the adjoint dC/dz, dC/dt."""
+    torch, sso, local = _gpu_setup()
+    n_el = a.n_el if a.n_el != 64 else 512
+    m = meshgen.shell(n_el=n_el, supports="clamped", load="pressure")
+    mdl = sso.Model(m)
+    batch = sso.Batch([mdl])
+    opts = sso.options(precision=a.precision, precond=a.precond, rtol=1e-8,
+                       inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch)
+    warm = sso.options(precision=a.precision, precond=a.precond, rtol=1e-8,
+                       inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch,
+                       max_iter=4 * a.iters_per_launch)
+    batch.solve(warm, raise_on_error=False)
+    torch.cuda.synchronize()
+    peak_gbs, peak_kind = measured_peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sso.kernel_launches()
+    batch.set_profiling(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    stream = torch.cuda.current_stream()
+    ev[0].record(stream)
+    stats = batch.solve(opts)
+    ev[1].record(stream)
+    batch.gradient()
+    ev[2].record(stream)
+    ev[2].synchronize()
+    ms_a, ms_b, pairs = batch.kernel_times()
+    su = batch.setup_times()
+    batch.set_profiling(False)
+    launches = sso.kernel_launches() - l0
+    clk = clocks.stop()
+    solve_ms = ev[0].elapsed_time(ev[1])
+    grad_ms = ev[1].elapsed_time(ev[2])
+    s0 = stats[0]
+    n = mdl.n_nodes
+    nb = mdl.n_blocks
+    n_free = 6 * n - int(m["fixed"].sum())
+    fp32 = a.precision == "fp32_ir"
+    wsz = 4 if fp32 else 8
+    bytes_pcg = nb * (36 * wsz + 4) + (n + 1) * 4 + 4 * (6 * n * wsz)
+    bytes_resid = nb * (36 * 8 + 4) + (n + 1) * 4 + 3 * (6 * n * 8)
+    alg = s0["iterations"] * bytes_pcg + s0["sweeps"] * bytes_resid
+    ach = alg / (ms_a / 1e3) / 1e9 if ms_a > 0 else None
+    n_eb = mdl.n_elem_blocks
+    asm_bytes = n_eb * (288 + 4) + (nb + 1) * 4 + nb * 8 + 6 * n + nb * (288 + 144)
+    asm_gbs = asm_bytes / (su["assembly"] / 1e3) / 1e9 if su["assembly"] > 0 else None
+    line = {
+        "metric": METRIC, "value": 1000.0 / (solve_ms + grad_ms), "unit": "evals/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": solve_ms + grad_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
+        "config": {"workload": "large shell %dx%d quads (%d DOF, %d free), clamped edges, 5 kPa, "
+                               "%s %s CG to rtol 1e-8, solve + adjoint dC/dz, dC/dt"
+                               % (n_el, n_el, 6 * n, n_free, "FP32+FP64 refinement" if fp32
+                                  else "FP64", a.precond),
+                   "l2": "K alone (%.0f MB FP32) exceeds L2" % (nb * 144 / 1e6)},
+        "solve_ms": solve_ms, "gradient_ms": grad_ms, "cg_iterations": s0["iterations"],
+        "refinement_sweeps": s0["sweeps"], "rel_residual": s0["rel_residual"],
+        "pcg_dof_per_s": n_free * s0["iterations"] / (solve_ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "pcg_a (BSR SpMV)", "achieved": ach,
+                     "peak": peak_gbs, "unit": "GB/s",
+                     "frac": ach / peak_gbs if ach else None, "peak_kind": peak_kind,
+                     "traffic": None, "alg_bytes_per_cg_launch": bytes_pcg,
+                     "launches_timed": pairs, "kernel_ms_total": ms_a, "kernel_b_ms_total": ms_b},
+        "assembly": {"ms": su["assembly"], "alg_bytes": asm_bytes, "achieved_gbs": asm_gbs,
+                     "frac": asm_gbs / peak_gbs if asm_gbs else None},
+        "elements_ms": su["elements"], "precond_loads_ms": su["precond"],
+        "adjoint_contraction_ms": su["adjoint"],
+        "cpu_baseline": None, "clocks": clk, "gpu_launches": int(launches),
+        "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_workload(a):
+    {"serving": run_serving, "gridshell": run_gridshell, "large": run_large}[a.workload](a)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.workload != "shell":
+        run_workload(a)
         return
     import torch
     import torch.distributed as dist

@@ -235,6 +235,16 @@ sso_status sso_batch_gradient(sso_batch* batch, const double* w, const double* c
 sso_status sso_batch_set_profiling(sso_batch* batch, int32_t enable);
 sso_status sso_batch_kernel_times(const sso_batch* batch, double* ms_a, double* ms_b,
                                   int64_t* launches);
+/* Set-up and adjoint timing while profiling is enabled (same switch and
+ * reset): device milliseconds summed over every model set-up of
+ * sso_batch_solve -- element matrices (Sec. 2.2), assembly of K (Eq. 1),
+ * preconditioner + load vector -- and over every contraction pass of
+ * sso_batch_gradient (the adjoint sum of Eq. 6 and the per-node gather).
+ * setups counts model set-ups timed, gradients the gradient calls.  Any
+ * pointer may be NULL. */
+sso_status sso_batch_setup_times(const sso_batch* batch, double* ms_elements,
+                                 double* ms_assembly, double* ms_precond, double* ms_adjoint,
+                                 int64_t* setups, int64_t* gradients);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of design evaluations.  Each request is one

@@ -177,6 +177,11 @@ struct sso_batch {
   std::vector<cudaEvent_t> pev;
   double prof_ms_a = 0.0, prof_ms_b = 0.0;
   long long prof_launches = 0;
+  // set-up and adjoint timing: 4 events per model around its element,
+  // assembly and preconditioner + load kernels, 2 around the contraction pass
+  std::vector<cudaEvent_t> sev;
+  double prof_ms_el = 0.0, prof_ms_asm = 0.0, prof_ms_pre = 0.0, prof_ms_adj = 0.0;
+  long long prof_setups = 0, prof_grads = 0;
 };
 
 namespace {
@@ -450,23 +455,30 @@ sso_status leave(sso_model* M) {
   return SSO_OK;
 }
 
-// Element matrices, K, preconditioner and loads of one model.
-sso_status setup_model(sso_model* M, int precond, cudaStream_t s) {
+// Element matrices, K, preconditioner and loads of one model.  ev (or NULL):
+// four events recorded before the element kernels, after them, after the
+// assembly and at the end.
+sso_status setup_model(sso_model* M, int precond, cudaStream_t s,
+                       const cudaEvent_t* ev = nullptr) {
+  if (ev) CK(cudaEventRecord(ev[0], s));
   CL(launch_beam_stiffness(M->n_beams, M->d_xyz, M->d_beam_conn, M->d_beam_props, M->d_ke, s),
      M->n_beams > 0);
   CL(launch_quad_stiffness(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props, M->pressure,
                            M->gamma, M->d_ke + (size_t)4 * M->n_beams * 36,
                            M->d_fslot + 2 * (size_t)M->n_beams, s),
      M->n_quads > 0);
+  if (ev) CK(cudaEventRecord(ev[1], s));
   CL(launch_assemble(M->n_blocks, M->d_cptr, M->d_csrc, M->d_ke, M->d_brow, M->d_col,
                      M->d_fixed, M->d_K64, M->d_K32, s),
      1);
+  if (ev) CK(cudaEventRecord(ev[2], s));
   CK(cudaMemsetAsync(M->d_err, 0, sizeof(int), s));
   CL(launch_precond(M->n_nodes, precond, M->d_diag, M->d_K64, M->d_M64, M->d_M32, M->d_err, s),
      1);
   CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, M->d_fslot, nullptr,
                         M->d_nodal_load, M->d_fixed, M->d_f, nullptr, s),
      1);
+  if (ev) CK(cudaEventRecord(ev[3], s));
   M->assembled = true;
   M->assembled_precond = precond;
   return SSO_OK;
@@ -520,6 +532,21 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
   B->exec_iters[k] = iters;
   B->exec_prof[k] = B->profiling;
   return SSO_OK;
+}
+
+// At least n timing events in B->sev.
+sso_status ensure_setup_events(sso_batch* B, size_t n) {
+  while (B->sev.size() < n) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    B->sev.push_back(e);
+  }
+  return SSO_OK;
+}
+
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.f;
 }
 
 // Adds the kernel durations of the last graph launch (after it completed).
@@ -1026,6 +1053,7 @@ void sso_batch_destroy(sso_batch* B) {
   for (int k = 0; k < 2; ++k)
     if (B->exec[k]) cudaGraphExecDestroy(B->exec[k]);
   for (cudaEvent_t e : B->pev) cudaEventDestroy(e);
+  for (cudaEvent_t e : B->sev) cudaEventDestroy(e);
   if (B->arena) cudaFree(B->arena);
   if (B->h_sc) cudaFreeHost(B->h_sc);
   if (B->h_flag) cudaFreeHost(B->h_flag);
@@ -1038,6 +1066,21 @@ sso_status sso_batch_set_profiling(sso_batch* B, int32_t enable) {
   B->profiling = enable ? 1 : 0;
   B->prof_ms_a = B->prof_ms_b = 0.0;
   B->prof_launches = 0;
+  B->prof_ms_el = B->prof_ms_asm = B->prof_ms_pre = B->prof_ms_adj = 0.0;
+  B->prof_setups = B->prof_grads = 0;
+  return SSO_OK;
+}
+
+sso_status sso_batch_setup_times(const sso_batch* B, double* ms_elements, double* ms_assembly,
+                                 double* ms_precond, double* ms_adjoint, int64_t* setups,
+                                 int64_t* gradients) {
+  if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  if (ms_elements) *ms_elements = B->prof_ms_el;
+  if (ms_assembly) *ms_assembly = B->prof_ms_asm;
+  if (ms_precond) *ms_precond = B->prof_ms_pre;
+  if (ms_adjoint) *ms_adjoint = B->prof_ms_adj;
+  if (setups) *setups = B->prof_setups;
+  if (gradients) *gradients = B->prof_grads;
   return SSO_OK;
 }
 
@@ -1063,8 +1106,10 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
     CK(cudaEventRecord(M->ev_in, M->user_stream));
     CK(cudaStreamWaitEvent(B->stream, M->ev_in, 0));
   }
+  const bool prof = B->profiling != 0;
+  if (prof && (st = ensure_setup_events(B, 4 * (size_t)B->n_sys + 2)) != SSO_OK) return st;
   for (int s = 0; s < B->n_sys; ++s) {
-    st = setup_model(B->models[s], opts->precond, B->stream);
+    st = setup_model(B->models[s], opts->precond, B->stream, prof ? &B->sev[4 * s] : nullptr);
     if (st != SSO_OK) return st;
   }
   std::vector<char> active(B->n_sys, 1);
@@ -1082,6 +1127,15 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
     CK(cudaMemcpyAsync(&errs[s], B->models[s]->d_err, sizeof(int), cudaMemcpyDeviceToHost,
                        B->stream));
   CK(cudaStreamSynchronize(B->stream));
+  if (prof) {
+    for (int s = 0; s < B->n_sys; ++s) {
+      const cudaEvent_t* e = &B->sev[4 * s];
+      B->prof_ms_el += elapsed_ms(e[0], e[1]);
+      B->prof_ms_asm += elapsed_ms(e[1], e[2]);
+      B->prof_ms_pre += elapsed_ms(e[2], e[3]);
+    }
+    B->prof_setups += B->n_sys;
+  }
   for (int s = 0; s < B->n_sys; ++s) {
     sso_model* M = B->models[s];
     M->solved = true;
@@ -1136,6 +1190,12 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
     run = batch_run(B, &o, true, active, stats);
     if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
   }
+  const bool prof = B->profiling != 0;
+  const size_t e0 = 4 * (size_t)B->n_sys;
+  if (prof) {
+    if ((st = ensure_setup_events(B, e0 + 2)) != SSO_OK) return st;
+    CK(cudaEventRecord(B->sev[e0], B->stream));
+  }
   for (int s = 0; s < B->n_sys; ++s) {
     sso_model* M = B->models[s];
     const double ws = w ? w[s] : 1.0;
@@ -1162,7 +1222,12 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
       stats[s].ms = 0.0;
     }
   }
+  if (prof) CK(cudaEventRecord(B->sev[e0 + 1], B->stream));
   CK(cudaStreamSynchronize(B->stream));
+  if (prof) {
+    B->prof_ms_adj += elapsed_ms(B->sev[e0], B->sev[e0 + 1]);
+    B->prof_grads += 1;
+  }
   for (int s = 0; s < B->n_sys; ++s) {
     sso_model* M = B->models[s];
     CK(cudaEventRecord(M->ev_out, B->stream));

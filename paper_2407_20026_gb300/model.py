@@ -203,6 +203,16 @@ class Batch:
                                                       ctypes.byref(n)))
         return a.value, b.value, n.value
 
+    def setup_times(self):
+        """Device ms since profiling was enabled: dict with elements, assembly,
+        precond (+ loads), adjoint (contraction pass), setups, gradients."""
+        v = [ctypes.c_double() for _ in range(4)]
+        n = [ctypes.c_int64() for _ in range(2)]
+        _lib.check(_lib.load().sso_batch_setup_times(self._h, *[ctypes.byref(x) for x in v],
+                                                     *[ctypes.byref(x) for x in n]))
+        return {"elements": v[0].value, "assembly": v[1].value, "precond": v[2].value,
+                "adjoint": v[3].value, "setups": n[0].value, "gradients": n[1].value}
+
     def gradient(self, w=None, g=None, raise_on_error=True):
         n = len(self.models)
         wa = (ctypes.c_double * n)(*([1.0] * n if w is None else [float(x) for x in w]))
