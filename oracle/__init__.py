@@ -78,6 +78,7 @@ def _load():
             "orc_gradient": ([mp, f64, vp, vp, vp, vp, vp, vp], i32),
             "orc_adjoint_contract": ([mp, vp, vp, f64, vp, vp], None),
             "orc_cg": ([mp, f64, i32, vp, vp], i32),
+            "orc_volume": ([mp, vp, vp, vp], None),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -229,6 +230,17 @@ def adjoint_contract(model, u, lam, w: float = 1.0):
     _load().orc_adjoint_contract(b.ref(), _ptr(_f64(u, n)), _ptr(_f64(lam, n)), float(w),
                                  _ptr(dz), _ptr(dt))
     return dz, dt[:b.quad_conn.shape[0]]
+
+
+def volume(model):
+    """Material volume W = sum_e A_e t_e of the quads (Sec. 3.3) and its
+    gradients: dict with V, dz [n_nodes], dt [n_quads] (= A_e)."""
+    b = _Bound(model)
+    V = ctypes.c_double(0.0)
+    dz = np.zeros(b.n_nodes)
+    dt = np.zeros(max(b.quad_conn.shape[0], 1))
+    _load().orc_volume(b.ref(), ctypes.byref(V), _ptr(dz), _ptr(dt))
+    return {"V": V.value, "dz": dz, "dt": dt[:b.quad_conn.shape[0]]}
 
 
 def cg(model, rtol: float = 1e-12, max_iter: int = 200000):

@@ -33,6 +33,8 @@
 //  * Global K u = f (Eq. 1) with supports imposed either by deleting the fixed
 //    rows and columns (homogeneous supports, b = 0) or by the Lagrange
 //    multiplier system K_aug u_aug = f_aug with V u = b (Eqs. 2-3).
+//  * Material volume W = sum_e A_e t_e of the quads (Sec. 3.3) with dW/dz and
+//    dW/dt, A_e the facet area above.
 //  * Compliance C = f^T u and the adjoint sensitivity (Eqs. 5-6):
 //    K^T lambda = dJ/du and dJ/dp = dJ/dp|explicit - lambda^T (dK/dp u - df/dp),
 //    for J = w C + g^T u.  dk_e/dp comes from forward-mode dual numbers
@@ -809,6 +811,34 @@ void orc_adjoint_contract(const orc_mesh* m, const double* u, const double* lam,
   const int n = 6 * m->n_nodes;
   std::vector<double> uu(u, u + n), ll(lam, lam + n);
   adjoint_contract(m, uu, ll, w, dz, dt);
+}
+
+// Material volume of the quads, W = sum_e A_e t_e (Sec. 3.3, the volume term
+// of the size-optimisation objective without its minimum-thickness penalty),
+// with A_e the area of the element's flat facet (the same 2 x 2 Gauss
+// integral as the area loads).  dW/dz per node by dual numbers seeded on that
+// node's z in every quad that contains it; dW/dt_e = A_e.
+void orc_volume(const orc_mesh* m, double* V, double* dz, double* dt) {
+  double vol = 0.0;
+  for (int i = 0; i < m->n_nodes; ++i) dz[i] = 0.0;
+  for (int e = 0; e < m->n_quads; ++e) {
+    int nodes[4];
+    for (int a = 0; a < 4; ++a) nodes[a] = m->quad_conn[4 * e + a];
+    const double t = m->quad_props[5 * e + 0];
+    for (int which = 0; which < 4; ++which) {
+      Dual X[4][3];
+      for (int a = 0; a < 4; ++a)
+        for (int k = 0; k < 3; ++k)
+          X[a][k] = Dual(m->xyz[3 * nodes[a] + k], (which == a && k == 2) ? 1.0 : 0.0);
+      const Dual A = quad_area<Dual>(X);
+      dz[nodes[which]] += t * A.d;
+      if (which == 0) {
+        dt[e] = A.v;
+        vol += A.v * t;
+      }
+    }
+  }
+  *V = vol;
 }
 
 // Jacobi-preconditioned FP64 CG on K_ff (element-by-element products with
