@@ -54,10 +54,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="shell",
-                   choices=["shell", "serving", "gridshell", "large"],
+                   choices=["shell", "serving", "gridshell", "large", "training"],
                    help="shell: batches of 64x64 shell designs (default line); serving: "
                         "continuous batching of a grid-shell request stream; gridshell: "
-                        "latency of one 10x10 grid-shell evaluation; large: one 512x512 shell")
+                        "latency of one 10x10 grid-shell evaluation; large: one 512x512 shell; "
+                        "training: MLP through 64 batched 48x48 shell solves per step")
     p.add_argument("--requests", type=int, default=512, help="serving: requests per run")
     p.add_argument("--rates", default="0.5,0.9",
                    help="serving: Poisson arrival rates as fractions of saturated throughput")
@@ -486,8 +487,78 @@ def run_large(a):
     print(json.dumps(line), flush=True)
 
 
+def run_training(a):
+    """Physics-in-the-loop training: a 3-layer MLP (16 -> 128 -> 128 -> n_nodes,
+    FP32) maps 64 seeded latent vectors to nodal z offsets (0.25 tanh, in m) of
+    48 x 48-element shells (t = 0.1 m, corners pinned, self-weight) around the
+    bump of the 64 x 64 shell workload; each step solves the 64
+    shells in one batch, takes the adjoint through the autograd function and
+    backpropagates loss = mean(C + 0.1 V) into the MLP (Adam).  Solves start
+    from the previous step's displacements (warm start)."""
+    torch, sso, local = _gpu_setup()
+    from paper_2407_20026_gb300.autograd import BatchSSOFunction
+    dev = torch.device("cuda", local)
+    B, n_el = 64, 48
+    base = meshgen.shell(n_el=n_el, seed=0, thickness=0.1)
+    n = base["xyz"].shape[0]
+    nq = base["quad_conn"].shape[0]
+    batch = sso.Batch([sso.Model(base) for _ in range(B)])
+    gen = torch.Generator().manual_seed(0)
+    torch.manual_seed(0)
+    mlp = torch.nn.Sequential(torch.nn.Linear(16, 128), torch.nn.ReLU(),
+                              torch.nn.Linear(128, 128), torch.nn.ReLU(),
+                              torch.nn.Linear(128, n)).to(dev)
+    latents = torch.randn(B, 16, generator=gen).to(dev)
+    optim = torch.optim.Adam(mlp.parameters(), lr=1e-3)
+    z0 = torch.tensor(base["xyz"][:, 2], device=dev).expand(B, n)
+    t = torch.full((B, nq), 0.1, dtype=torch.float64, device=dev)
+    opts = sso.options(precision=a.precision, precond=a.precond, rtol=a.rtol,
+                       inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch,
+                       warm_start=1)
+
+    def step():
+        z = z0 + 0.25 * torch.tanh(mlp(latents)).double()
+        u, C, V = BatchSSOFunction.apply(batch, z, t, opts)
+        loss = (C + 0.1 * V).mean()
+        optim.zero_grad()
+        loss.backward()
+        optim.step()
+        return float(loss.detach())
+
+    losses = [step() for _ in range(max(a.warmup, 3))]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sso.kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        losses.append(step())
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    launches = sso.kernel_launches() - l0
+    clk = clocks.stop()
+    line = {
+        "metric": "training steps/sec (64 shell solves + adjoint per step)",
+        "value": a.steps / el, "unit": "steps/s", "n_gpus": 1, "steps": a.steps,
+        "warmup": max(a.warmup, 3), "ms_per_step": 1000 * el / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if a.precision == "fp32_ir" else "f64", "data": "synthetic",
+        "config": {"workload": "training: MLP 16-128-128-%d (FP32), %d latents, %dx%d-element "
+                               "shells (%d DOF), t = 0.1, loss = mean(C + 0.1 V), Adam 1e-3, "
+                               "%s CG to rtol %g, warm start" % (n, B, n_el, n_el, 6 * n,
+                                                                 a.precond, a.rtol),
+                   "l2": "64 x K (%.0f MB) > L2" % (B * batch.models[0].n_blocks * 144 / 1e6)},
+        "design_evals_per_s": B * a.steps / el,
+        "loss_first": losses[0], "loss_last": losses[-1],
+        "roofline": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": int(launches),
+        "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_workload(a):
-    {"serving": run_serving, "gridshell": run_gridshell, "large": run_large}[a.workload](a)
+    {"serving": run_serving, "gridshell": run_gridshell, "large": run_large,
+     "training": run_training}[a.workload](a)
 
 
 def main():

@@ -195,6 +195,16 @@ sso_status sso_model_gradient(sso_model* model, double w, const double* g, sso_s
 sso_status sso_model_get(sso_model* model, double* u, double* C, double* dz, double* dt,
                          double* lam);
 
+/* Material volume of the quads, W = sum_e A_e t_e (Sec. 3.3: the volume term
+ * of the size-optimisation objective, without its minimum-thickness
+ * penalty), at the model's current design, with A_e the area of the
+ * element's flat facet (the 2 x 2 Gauss integral used for area loads).
+ * Outputs (any may be NULL; host or device): V [1], dVdz [n_nodes]
+ * (dW/dz_i, every node), dVdt [n_quads] (dW/dt_e = A_e).  Beams add nothing.
+ * Ordered on the model's stream; returns when the outputs are written.
+ * The sum over elements has a fixed order, so W is reproducible. */
+sso_status sso_model_volume(sso_model* model, double* V, double* dVdz, double* dVdt);
+
 /* Sizes of the model: n_blocks of K and the number of element blocks. */
 sso_status sso_model_info(const sso_model* model, int32_t* n_nodes, int32_t* n_blocks,
                           int32_t* n_elem_blocks);

@@ -144,6 +144,9 @@ struct sso_model {
   float *d_K32, *d_M32;
   void *d_r, *d_z, *d_p0, *d_p1, *d_q;
   double *d_part_a, *d_part_b, *d_dz, *d_dt, *d_C;
+  // material volume (Sec. 3.3): per-quad A t, per-slot t dA/dz (beam slots
+  // stay 0), dW/dz, dW/dt, W
+  double *d_vol, *d_vslot, *d_vdz, *d_vdt, *d_V;
   int* d_err;
   bool assembled = false, solved = false;
   int assembled_precond = -1;
@@ -423,6 +426,11 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_dz = c.take<double>(n);
   M->d_dt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_C = c.take<double>(1);
+  M->d_vol = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
+  M->d_vslot = c.take<double>(M->n_slots);
+  M->d_vdz = c.take<double>(n);
+  M->d_vdt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
+  M->d_V = c.take<double>(1);
   M->d_err = c.take<int>(1);
   return align_up(c.off, 256);
 }
@@ -920,6 +928,30 @@ sso_status sso_model_get(sso_model* M, double* u, double* C, double* dz, double*
     CK(cudaMemcpyAsync(dt, M->d_dt, M->n_quads * 8, cudaMemcpyDefault, M->stream));
   if (lam) CK(cudaMemcpyAsync(lam, M->d_lam, ndof * 8, cudaMemcpyDefault, M->stream));
   CK(cudaStreamSynchronize(M->stream));
+  return leave(M);
+}
+
+sso_status sso_model_volume(sso_model* M, double* V, double* dVdz, double* dVdt) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  cudaStream_t s = M->stream;
+  if (M->n_quads > 0) {
+    CL(launch_quad_volume(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props,
+                          M->d_vslot + 2 * (size_t)M->n_beams, M->d_vdt, M->d_vol, s),
+       1);
+    CL(launch_ordered_sum(M->n_quads, M->d_vol, M->d_V, s), 1);
+  } else {
+    CK(cudaMemsetAsync(M->d_V, 0, sizeof(double), s));
+  }
+  CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, nullptr, M->d_vslot,
+                        nullptr, M->d_fixed, nullptr, M->d_vdz, s),
+     1);
+  if (V) CK(cudaMemcpyAsync(V, M->d_V, 8, cudaMemcpyDefault, s));
+  if (dVdz) CK(cudaMemcpyAsync(dVdz, M->d_vdz, M->n_nodes * 8, cudaMemcpyDefault, s));
+  if (dVdt && M->n_quads > 0)
+    CK(cudaMemcpyAsync(dVdt, M->d_vdt, M->n_quads * 8, cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
   return leave(M);
 }
 

@@ -666,7 +666,74 @@ __global__ void __launch_bounds__(128) beam_adjoint_kernel(
   gslot[2 * e + 1] = -en.d[1];
 }
 
+// Material volume of the quads (Sec. 3.3): per quad the facet area A_e (the
+// 2 x 2 Gauss integral of the facet Jacobian, as for the area loads) with its
+// tangents along the z of its four nodes (dual numbers, one per node).
+// vol[e] = A_e t_e, dt[e] = A_e, vslot[4e + a] = t_e dA_e / dz_a.
+__global__ void __launch_bounds__(128) quad_volume_kernel(
+    int nq, const double* __restrict__ xyz, const int* __restrict__ conn,
+    const double* __restrict__ props, double* __restrict__ vslot, double* __restrict__ dt,
+    double* __restrict__ vol) {
+  typedef DN<4> D;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq) return;
+  D X[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int nd = conn[4 * e + a];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[a][k] = D(xyz[3 * nd + k]);
+    X[a][2].d[a] = 1.0;
+  }
+  QuadGeom<D> g;
+  quad_geom(X, g);
+  D A(0.0);
+#pragma unroll
+  for (int gj = 0; gj < 2; ++gj)
+#pragma unroll
+    for (int gi = 0; gi < 2; ++gi) {
+      QuadPoint<D> P;
+      quad_point(g, gi == 0 ? -GP : GP, gj == 0 ? -GP : GP, P);
+      A = A + (P.xxi * P.yeta - P.yxi * P.xeta);
+    }
+  const double t = props[5 * e + 0];
+  dt[e] = A.v;
+  vol[e] = A.v * t;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) vslot[4 * e + a] = t * A.d[a];
+}
+
+// out = sum of v[0..n) in a fixed order (one CTA: strided partial sums, then a
+// fixed-shape tree), so the result does not depend on timing.
+__global__ void __launch_bounds__(256) ordered_sum_kernel(int n, const double* __restrict__ v,
+                                                          double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += v[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 }  // namespace
+
+cudaError_t launch_quad_volume(int n_quads, const double* xyz, const int* conn,
+                               const double* props, double* vslot, double* dt, double* vol,
+                               cudaStream_t s) {
+  if (n_quads <= 0) return cudaSuccess;
+  quad_volume_kernel<<<(n_quads + 127) / 128, 128, 0, s>>>(n_quads, xyz, conn, props, vslot,
+                                                            dt, vol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ordered_sum(int n, const double* v, double* out, cudaStream_t s) {
+  ordered_sum_kernel<<<1, 256, 0, s>>>(n, v, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_beam_stiffness(int n_beams, const double* xyz, const int* conn,
                                   const double* props, double* ke, cudaStream_t s) {

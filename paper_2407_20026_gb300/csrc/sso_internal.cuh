@@ -108,6 +108,10 @@ struct SysDesc {
 // Launchers (elements.cu)
 cudaError_t launch_beam_stiffness(int n_beams, const double* xyz, const int* conn,
                                   const double* props, double* ke, cudaStream_t s);
+cudaError_t launch_quad_volume(int n_quads, const double* xyz, const int* conn,
+                               const double* props, double* vslot, double* dt, double* vol,
+                               cudaStream_t s);
+cudaError_t launch_ordered_sum(int n, const double* v, double* out, cudaStream_t s);
 cudaError_t launch_quad_stiffness(int n_quads, const double* xyz, const int* conn,
                                   const double* props, double pressure, double gamma,
                                   double* ke, double* fslot, cudaStream_t s);

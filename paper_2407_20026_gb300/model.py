@@ -148,6 +148,21 @@ class Model:
         out["dt"] = out["dt"][:self.n_quads]
         return out
 
+    def volume(self, device=None):
+        """Material volume W = sum A_e t_e at the current design: dict with V,
+        dz [n_nodes], dt [n_quads] (numpy, or torch tensors on `device`)."""
+        n, nq = self.n_nodes, self.n_quads
+        if device is None:
+            V, dz, dt = np.zeros(1), np.zeros(n), np.zeros(max(nq, 1))
+            ptrs = [V.ctypes.data, dz.ctypes.data, dt.ctypes.data]
+        else:
+            V = torch.empty(1, dtype=torch.float64, device=device)
+            dz = torch.empty(n, dtype=torch.float64, device=device)
+            dt = torch.empty(max(nq, 1), dtype=torch.float64, device=device)
+            ptrs = [V.data_ptr(), dz.data_ptr(), dt.data_ptr()]
+        _lib.check(_lib.load().sso_model_volume(self._h, *ptrs))
+        return {"V": V[0] if device is not None else float(V[0]), "dz": dz, "dt": dt[:nq]}
+
     def stiffness(self):
         """(row_ptr, col, K64 [nb,6,6], K32 [nb,6,6]) of the last assembly, numpy."""
         rp = np.zeros(self.n_nodes + 1, np.int32)

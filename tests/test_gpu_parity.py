@@ -243,14 +243,51 @@ def test_autograd_function(sso, orc):
     mdl = sso.Model(m)
     z = torch.tensor(m["xyz"][:, 2], device="cuda", requires_grad=True)
     t = torch.tensor(m["quad_props"][:, 0], device="cuda", requires_grad=True)
-    u, C = SSOFunction.apply(mdl, z, t, sso.options(precision="fp64", rtol=1e-11))
+    u, C, V = SSOFunction.apply(mdl, z, t, sso.options(precision="fp64", rtol=1e-11))
     rng = np.random.default_rng(5)
     gvec = torch.tensor(rng.normal(size=u.shape[0]), device="cuda")
-    J = 0.7 * C + (gvec * u).sum()
+    J = 0.7 * C + (gvec * u).sum() + 0.3 * V
     J.backward()
     ref = orc.gradient(m, w=0.7, g=gvec.cpu().numpy())
-    assert rel(z.grad.cpu().numpy(), ref["dz"]) <= TOL_FP64
-    assert rel(t.grad.cpu().numpy(), ref["dt"]) <= TOL_FP64
+    vol = orc.volume(m)
+    assert abs(float(V.detach()) - vol["V"]) <= TOL_ELEMENT * vol["V"]
+    assert rel(z.grad.cpu().numpy(), ref["dz"] + 0.3 * vol["dz"]) <= TOL_FP64
+    assert rel(t.grad.cpu().numpy(), ref["dt"] + 0.3 * vol["dt"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("name", ["shell5", "shell9_clamped", "mixed", "gridshell13"])
+def test_material_volume(sso, orc, name):
+    """W = sum A_e t_e and its z, t gradients vs the oracle (element-level
+    tolerance: same formulas, different operation order)."""
+    m = MODELS[name]()
+    r = sso.Model(m).volume()
+    ref = orc.volume(m)
+    if m["quad_conn"].shape[0] == 0:
+        assert r["V"] == 0.0 and not np.any(r["dz"])
+        return
+    assert abs(r["V"] - ref["V"]) <= TOL_ELEMENT * ref["V"]
+    assert rel(r["dz"], ref["dz"]) <= 1e-10
+    assert rel(r["dt"], ref["dt"]) <= TOL_ELEMENT
+
+
+def test_batched_autograd_with_volume(sso, orc):
+    """The batched function's gradient of sum_i (C_i + 0.1 V_i) over three
+    designs of one mesh vs the oracle, FP32 CG with refinement."""
+    from paper_2407_20026_gb300.autograd import BatchSSOFunction
+    meshes = [meshgen.shell(n_el=6, span=8.0, seed=s, thickness=0.1) for s in range(3)]
+    batch = sso.Batch([sso.Model(m) for m in meshes])
+    z = torch.tensor(np.stack([m["xyz"][:, 2] for m in meshes]), device="cuda",
+                     requires_grad=True)
+    t = torch.tensor(np.stack([m["quad_props"][:, 0] for m in meshes]), device="cuda",
+                     requires_grad=True)
+    u, C, V = BatchSSOFunction.apply(batch, z, t, sso.options(rtol=1e-10))
+    (C + 0.1 * V).sum().backward()
+    for i, m in enumerate(meshes):
+        ref = orc.gradient(m)
+        vol = orc.volume(m)
+        assert abs(float(C[i]) - ref["C"]) <= TOL_FP32_IR * abs(ref["C"])
+        assert rel(z.grad[i].cpu().numpy(), ref["dz"] + 0.1 * vol["dz"]) <= TOL_FP32_IR
+        assert rel(t.grad[i].cpu().numpy(), ref["dt"] + 0.1 * vol["dt"]) <= TOL_FP32_IR
 
 
 @pytest.mark.parametrize("name", ["gridshell13", "c1"])
