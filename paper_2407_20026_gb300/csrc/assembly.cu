@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(
 
 // Block-Jacobi: Cholesky-invert the 6x6 diagonal block of every node (FP64).
 // Jacobi: invert the diagonal entries.  A non-positive pivot sets *err.
+// Layouts: M64 [n][6][6] (Jacobi: [n][6]); M32 packed [n][M32_PACK]
+// (Jacobi: [n][6]).
 __global__ void __launch_bounds__(128) precond_kernel(int n_nodes, int kind,
                                                       const int* __restrict__ diag_idx,
                                                       const double* __restrict__ K64,
@@ -83,13 +85,16 @@ __global__ void __launch_bounds__(128) precond_kernel(int n_nodes, int kind,
       Li[i][j] = t / L[i][i];
     }
   }
+  // M64 full; M32 packed (upper triangle, M32_PACK floats per node): the
+  // product is symmetric term by term, so nothing is lost
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) {
       double t = 0.0;
       for (int k = (i > j ? i : j); k < 6; ++k) t += Li[k][i] * Li[k][j];
       M64[(size_t)n * 36 + 6 * i + j] = t;
-      M32[(size_t)n * 36 + 6 * i + j] = (float)t;
+      if (i <= j) M32[(size_t)n * M32_PACK + sym6(i, j)] = (float)t;
     }
+  for (int k = 21; k < M32_PACK; ++k) M32[(size_t)n * M32_PACK + k] = 0.f;
 }
 
 // Per node, in slot order: f = nodal load + area-load shares (uz only; quad

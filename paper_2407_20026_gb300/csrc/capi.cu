@@ -140,7 +140,7 @@ struct sso_model {
   // design
   double *d_xyz, *d_beam_props, *d_quad_props, *d_nodal_load;
   // element and global arrays
-  double *d_ke, *d_fslot, *d_gslot, *d_K64, *d_M64, *d_f, *d_u, *d_lam, *d_rhs, *d_r64;
+  double *d_ke, *d_fslot, *d_gslot, *d_K64, *d_M64, *d_f, *d_u, *d_dx, *d_lam, *d_rhs, *d_r64;
   float *d_K32, *d_M32;
   void *d_r, *d_z, *d_p0, *d_p1, *d_q;
   double *d_part_a, *d_part_b, *d_dz, *d_dt, *d_C;
@@ -413,6 +413,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_M32 = c.take<float>(36 * n);
   M->d_f = c.take<double>(ndof);
   M->d_u = c.take<double>(ndof);
+  M->d_dx = c.take<double>(ndof);
   M->d_lam = c.take<double>(ndof);
   M->d_rhs = c.take<double>(ndof);
   M->d_r64 = c.take<double>(ndof);
@@ -596,6 +597,7 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
     if (active[s]) {
       ++n_act;
       if (!warm) CK(cudaMemsetAsync(D.x, 0, sizeof(double) * 6 * (size_t)M->n_nodes, B->stream));
+      CK(cudaMemsetAsync(M->d_dx, 0, sizeof(double) * 6 * (size_t)M->n_nodes, B->stream));
     }
   }
   CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * B->n_sys,
@@ -1025,6 +1027,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     D.M64 = M->d_M64;
     D.b = M->d_f;
     D.x = M->d_u;
+    D.dx = M->d_dx;
     D.r64 = M->d_r64;
     D.r = M->d_r;
     D.z = M->d_z;
@@ -1473,6 +1476,7 @@ void fill_sysdesc(SysDesc& D, sso_model* M, int precond) {
   D.M64 = M->d_M64;
   D.b = M->d_f;
   D.x = M->d_u;
+  D.dx = M->d_dx;
   D.r64 = M->d_r64;
   D.r = M->d_r;
   D.z = M->d_z;

@@ -11,15 +11,17 @@
 //   RESID  A: r64 = b - K64 x (FP64 SpMV), B: finish if ||r64|| <= rtol ||b||,
 //             ||r64||^2, ||b||^2              else r = r64 / ||r64||, z = M^-1 r,
 //                                             start a new inner sweep
-//   PCG    A: p = z + beta p (formed on    B: x += scale alpha p (FP64),
-//             the fly for every column       r -= alpha q, z = M^-1 r,
-//             read), q = K p, p^T q           r^T z, ||r||^2; beta; end the
-//                                             sweep when ||r||^2 <= inner_thr
+//   PCG    A: p = z + beta p (formed on    B: x += scale alpha p (FP64; in
+//             the fly for every column       FP32 mode dx += alpha p), r -= alpha q,
+//             read), q = K p, p^T q           z = M^-1 r, r^T z, ||r||^2; beta;
+//                                             end the sweep when ||r||^2 <= inner_thr
+//   FOLD   A: skipped                      B: x += scale dx, dx = 0 (FP32 mode)
 //   DONE   skipped
 //
-// In FP32_IR mode r, z, p, q and K are FP32 (K32 = round(K64)); x, r64 and
-// every dot product are FP64.  In FP64 mode everything is FP64 and the RESID
-// step only confirms the true residual.
+// In FP32_IR mode r, z, p, q, dx and K are FP32 (K32 = round(K64)); x, r64
+// and every dot product are FP64, and a sweep ends PCG -> FOLD -> RESID.  In
+// FP64 mode everything is FP64, x is updated directly and the RESID step only
+// confirms the true residual.
 //
 // Reductions: every warp reduces its rows with shuffles and stores one
 // partial per (tile, warp); there is no CTA barrier per tile.  When a CTA has
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict
       cur = sid;
       R = read_state(sc);
     }
-    if (R.state == ST_DONE) continue;
+    if (R.state == ST_DONE || R.state == ST_FOLD) continue;
     const int state = R.state;
     const int node = node0 + ln;
     const bool act = lane < 6 * NODES_PER_WARP && node < S.n_nodes;
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict
   }
 }
 
-// Kernel B.  Pure streaming per node (no neighbours): one thread owns one
+// Kernel B of the FP64 CG.  Pure streaming per node (no neighbours): one thread owns one
 // node (all six rows), so z = M^-1 r is a 6x6 product in registers and every
 // vector is read as 24- or 48-byte runs.  Warp w of a CTA takes every
 // WARPS-th tile of the CTA's range; a tile (TILE nodes) is one warp.  The
@@ -316,8 +318,10 @@ __device__ __forceinline__ void st6(double* p, const double v[6]) {
 // Scalar update of kernel B for one system, by one thread, once every tile of
 // the system has been counted.  s1 = r^T z, s2 = r^T r.
 __device__ __forceinline__ void finish_b(SysScalars* sc, int state, double s1, double s2,
-                                         int* n_active) {
-  if (state == ST_PCG) {
+                                         int* n_active, bool fold) {
+  if (state == ST_FOLD) {  // the correction has been added to x by every tile
+    sc->state = ST_RESID;
+  } else if (state == ST_PCG) {
     sc->iters += 1;
     sc->inner += 1;
     if (!isfinite(s1) || !isfinite(s2)) {
@@ -328,7 +332,7 @@ __device__ __forceinline__ void finish_b(SysScalars* sc, int state, double s1, d
       sc->beta = s1 / sc->rz;
       sc->rz = s1;
       sc->rr = s2;
-      if (s2 <= sc->inner_thr || sc->iters >= sc->max_iter) sc->state = ST_RESID;
+      if (s2 <= sc->inner_thr || sc->iters >= sc->max_iter) sc->state = fold ? ST_FOLD : ST_RESID;
     }
   } else {
     const double rr64 = sc->rr64;
@@ -469,37 +473,13 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
       }
       a1 = warp_sum(a1);
       a2 = warp_sum(a2);
-      if (lane == 0) finish_b(sc, state, a1, a2, n_active);
+      if (lane == 0) finish_b(sc, state, a1, a2, n_active, false);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Kernel A for the FP32 CG, warp-specialised.  Everything a tile reads is
-// contiguous in memory -- its K rows are one slab of the BSR value array, its
-// column indices and its row_ptr entries one run each, and the z / p entries
-// its columns touch lie in one node range (the tile's halo) -- and their
-// extents are fixed by the mesh (TileDesc, built on the host).  A producer
-// warp streams these five pieces of each tile into a two-stage shared-memory
-// ring with bulk copies (cp.async.bulk, the 1-D form of the TMA engine) and
-// passes the system's scalars along; six consumer warps compute the tile from
-// shared memory with no global loads.  full[s] / empty[s] mbarriers hand each
-// stage over; every wait is bounded.  Tiles that do not fit (scattered
-// numbering) and the FP64 residual passes read global memory instead; a tile
-// whose halo alone does not fit (long grid rows) stages everything but the
-// halo and gathers z and p from global memory.
-constexpr int ST_SLAB_K = STAGE_SLAB_K;
-constexpr int ST_SLAB_C = STAGE_SLAB_C;
-constexpr int ST_SLAB_V = STAGE_SLAB_V;
-constexpr int ST_SLAB_R = STAGE_SLAB_R;
-constexpr int ST_OFF_C = ST_SLAB_K;
-constexpr int ST_OFF_Z = ST_OFF_C + ST_SLAB_C;
-constexpr int ST_OFF_P = ST_OFF_Z + ST_SLAB_V;
-constexpr int ST_OFF_R = ST_OFF_P + ST_SLAB_V;
-constexpr int ST_STAGE = ST_OFF_R + ST_SLAB_R;
-constexpr int ST_STAGES = 2;
-constexpr int ST_SMEM = ST_STAGES * ST_STAGE;
-constexpr int ST_THREADS = NT + 32;  // six consumer warps + one producer warp
+// mbarrier and bulk-copy (1-D TMA) helpers.  Every wait is bounded.
 constexpr long long kWaitPolls = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -546,6 +526,284 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
     if (mbar_test(bar, parity)) return true;
   return false;
 }
+
+// ---------------------------------------------------------------------------
+// Kernel B for the FP32 CG.  A warp owns a tile (TILE nodes) at a time and
+// works from its own two-stage slice of shared memory.  While it computes one
+// tile, lane 0 has already issued the bulk copies (cp.async.bulk) of the
+// warp's next tile into the other stage: the tile's packed preconditioner
+// blocks (M32_PACK floats per node; Jacobi: 6) and its p, q, r and dx runs.
+// One thread per node then computes
+//   dx += alpha p,  r -= alpha q,  z = M^-1 r,  r^T z,  r^T r
+// from shared memory, and r, z and dx go back out as coalesced runs.  The
+// solution update of a CG sweep accumulates in dx (FP32, in units of the
+// sweep's scaled system); when the sweep ends the system passes through FOLD,
+// where x += scale dx in FP64 (and dx = 0) before the FP64 residual pass.
+// Every stage completes one mbarrier phase per tile (a plain arrival when
+// the tile needs no copy), and every wait is bounded: a warp whose wait gives
+// up raises the error flag and runs its remaining tiles without work.
+// Reductions: one partial per tile; a warp counts its run of consecutive tiles
+// of one system with a single atomic, and the warp that completes the system
+// sums the partials in tile order.
+constexpr int B32_M = M32_PACK * TILE;   // floats of preconditioner per stage
+constexpr int B32_V = 6 * TILE;          // floats per vector run of a tile
+constexpr int B32_STAGE = B32_M + 4 * B32_V;
+constexpr int B32_SMEM = WARPS * 2 * B32_STAGE * (int)sizeof(float);
+
+__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+__device__ __forceinline__ void store_run(float* dst, const float* src, int n2, int lane) {
+  float2* g = reinterpret_cast<float2*>(dst);
+  const float2* d = reinterpret_cast<const float2*>(src);
+  for (int k = lane; k < n2; k += 32) g[k] = d[k];
+}
+
+// What a warp knows about one of its tiles before it touches the data.
+struct BJob {
+  int tile, sid, node0, nn;
+  const SysDesc* S;
+  RunState R;
+  bool work, block;
+  int kind;  // 2: PCG (M and four vectors staged), 1: INIT / RESID (M staged), 0: none
+};
+
+__device__ __forceinline__ BJob make_bjob(const TileDesc* __restrict__ tiles,
+                                          const SysDesc* __restrict__ sys, int tile,
+                                          const BJob* prev) {
+  BJob J;
+  const TileDesc& td = tiles[tile];
+  J.tile = tile;
+  J.sid = td.sys;
+  J.node0 = td.node0;
+  J.nn = td.nn;
+  J.S = sys + J.sid;
+  if (prev && prev->sid == J.sid) {
+    J.R = prev->R;
+    J.work = prev->work;
+    J.block = prev->block;
+  } else {
+    // a system's state cannot change while this warp still holds uncounted
+    // tiles of it, so it may be read ahead
+    J.R = read_state(J.S->sc);
+    J.work = J.R.state == ST_PCG || J.R.state == ST_FOLD ||
+             (isfinite(J.R.rr64) && !(J.R.rr64 <= J.R.rtol2 * J.R.ff));
+    J.block = J.S->precond == SSO_BLOCK_JACOBI;
+  }
+  J.kind = !J.work ? 0 : J.R.state == ST_PCG ? 2
+                       : (J.R.state == ST_INIT || J.R.state == ST_RESID) ? 1 : 0;
+  return J;
+}
+
+// Lane 0: start the copies of job J into stage buffer st (mbarrier bar).
+__device__ __forceinline__ void issue_bjob(const BJob& J, float* st, unsigned long long* bar) {
+  if (J.kind == 0) {
+    mbar_arrive(bar);
+    return;
+  }
+  const SysDesc& S = *J.S;
+  const size_t v0 = 6 * (size_t)J.node0;
+  const uint32_t mb = J.block ? (uint32_t)J.nn * (M32_PACK * 4u) : round16((uint32_t)J.nn * 24u);
+  const uint32_t vb = round16((uint32_t)J.nn * 24u);
+  fence_proxy_async();
+  mbar_arrive_tx(bar, mb + (J.kind == 2 ? 4u * vb : 0u));
+  bulk_g2s(st, J.block ? S.M32 + (size_t)J.node0 * M32_PACK : S.M32 + v0, mb, bar);
+  if (J.kind == 2) {
+    bulk_g2s(st + B32_M, (const float*)(J.R.parity ? S.p1 : S.p0) + v0, vb, bar);
+    bulk_g2s(st + B32_M + B32_V, (const float*)S.q + v0, vb, bar);
+    bulk_g2s(st + B32_M + 2 * B32_V, (const float*)S.r + v0, vb, bar);
+    bulk_g2s(st + B32_M + 3 * B32_V, (const float*)S.dx + v0, vb, bar);
+  }
+}
+
+__global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restrict__ tiles,
+                                                        const int* __restrict__ n_tiles_ptr,
+                                                        const SysDesc* __restrict__ sys,
+                                                        int* __restrict__ flags) {
+  extern __shared__ __align__(128) float b32_smem[];
+  __shared__ __align__(8) unsigned long long full[WARPS][2];
+  int* n_active = flags;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stages = b32_smem + w * 2 * B32_STAGE;
+  if (lane == 0) {
+    mbar_init(&full[w][0], 1);
+    mbar_init(&full[w][1], 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  int begin, end;
+  tile_range(*n_tiles_ptr, begin, end);
+  int k = 0, run = 0, last_k[2] = {-1, -1};
+  bool dry = false;
+  BJob J;
+  if (begin + w < end) {
+    J = make_bjob(tiles, sys, begin + w, nullptr);
+    if (lane == 0) issue_bjob(J, stages, &full[w][0]);
+    last_k[0] = 0;
+  }
+  for (int tile = begin + w; tile < end; tile += WARPS, ++k) {
+    const int s = k & 1;
+    const int nxt = tile + WARPS;
+    BJob JN;
+    if (nxt < end) {
+      JN = make_bjob(tiles, sys, nxt, &J);
+      if (dry) JN.kind = 0;
+      if (lane == 0) issue_bjob(JN, stages + (s ^ 1) * B32_STAGE, &full[w][s ^ 1]);
+      last_k[s ^ 1] = k + 1;
+    }
+    if (!dry) {
+      const bool ok = mbar_wait(&full[w][s], (k >> 1) & 1);
+      if (__any_sync(0xffffffffu, !ok)) {
+        dry = true;
+        if (lane == 0) atomicExch(flags + 1, 1);
+      }
+    }
+    const SysDesc& S = *J.S;
+    SysScalars* sc = S.sc;
+    const int state = J.R.state;
+    if (state != ST_DONE) {
+      const int nn = J.nn;
+      const size_t v0 = 6 * (size_t)J.node0;
+      double v1 = 0.0, v2 = 0.0;
+      if (state == ST_FOLD) {
+        if (!dry) {
+          double* x = S.x + v0;
+          float* dx = (float*)S.dx + v0;
+          for (int i = lane; i < 6 * nn; i += 32) {
+            x[i] = fma(J.R.scale, (double)dx[i], x[i]);
+            dx[i] = 0.f;
+          }
+        }
+      } else if (J.work && !dry) {
+        float* st = stages + s * B32_STAGE;
+        float* Vp = st + B32_M;
+        float* Vq = Vp + B32_V;
+        float* Vr = Vq + B32_V;
+        float* Vd = Vr + B32_V;
+        if (lane < nn) {
+          float rv[6];
+          if (state == ST_PCG) {
+            const float alpha = (float)J.R.alpha;
+            float pv[6], qv[6], dv[6];
+            ld6rw(Vp + 6 * lane, pv);
+            ld6rw(Vq + 6 * lane, qv);
+            ld6rw(Vr + 6 * lane, rv);
+            ld6rw(Vd + 6 * lane, dv);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              dv[c] = fmaf(alpha, pv[c], dv[c]);
+              rv[c] = fmaf(-alpha, qv[c], rv[c]);
+            }
+            st6(Vd + 6 * lane, dv);
+          } else {
+            const double inv_norm = 1.0 / ::sqrt(J.R.rr64);
+            double gv[6];
+            ld6rw(S.r64 + v0 + 6 * lane, gv);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) rv[c] = (float)(gv[c] * inv_norm);
+          }
+          st6(Vr + 6 * lane, rv);
+          float zv[6];
+          if (J.block) {
+            float m[M32_PACK];
+            const float4* mp = reinterpret_cast<const float4*>(st + lane * M32_PACK);
+#pragma unroll
+            for (int c = 0; c < M32_PACK / 4; ++c) {
+              const float4 v = mp[c];
+              m[4 * c] = v.x; m[4 * c + 1] = v.y; m[4 * c + 2] = v.z; m[4 * c + 3] = v.w;
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+              float acc = 0.f;
+#pragma unroll
+              for (int c = 0; c < 6; ++c) acc = fmaf(m[sym6(a, c)], rv[c], acc);
+              zv[a] = acc;
+            }
+          } else {
+            float m[6];
+            ld6rw(st + 6 * lane, m);
+#pragma unroll
+            for (int a = 0; a < 6; ++a) zv[a] = m[a] * rv[a];
+          }
+          st6(Vq + 6 * lane, zv);  // q is consumed: its slot now holds z
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            v1 += (double)rv[a] * (double)zv[a];
+            v2 += (double)rv[a] * (double)rv[a];
+          }
+        }
+        __syncwarp();
+        store_run((float*)S.r + v0, Vr, 3 * nn, lane);
+        store_run((float*)S.z + v0, Vq, 3 * nn, lane);
+        if (state == ST_PCG) store_run((float*)S.dx + v0, Vd, 3 * nn, lane);
+      }
+      // the stage is free for the copies of the tile after next
+      __syncwarp();
+      v1 = warp_sum(v1);
+      v2 = warp_sum(v2);
+      if (lane == 0) {
+        double* dst = S.part_b + 2 * (size_t)(tile - S.tile0);
+        dst[0] = v1;
+        dst[1] = v2;
+      }
+      ++run;
+      if (!(nxt < end && JN.sid == J.sid)) {
+        int last = 0;
+        if (lane == 0) {
+          __threadfence();
+          const unsigned prev = atomicAdd(&sc->cnt_b, (unsigned)run);
+          last = prev + (unsigned)run == (unsigned)S.n_tiles;
+        }
+        run = 0;
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+          __threadfence();
+          double a1 = 0.0, a2 = 0.0;
+          if (state != ST_FOLD) {
+            for (int q = lane; q < S.n_tiles; q += 32) {
+              a1 += __ldcg(S.part_b + 2 * (size_t)q);
+              a2 += __ldcg(S.part_b + 2 * (size_t)q + 1);
+            }
+            a1 = warp_sum(a1);
+            a2 = warp_sum(a2);
+          }
+          if (lane == 0) finish_b(sc, state, a1, a2, n_active, true);
+        }
+      }
+    }
+    if (nxt < end) J = JN;
+  }
+  // copies still in flight land before the shared memory is released
+  if (dry && lane == 0)
+    for (int st = 0; st < 2; ++st)
+      if (last_k[st] >= 0) mbar_wait(&full[w][st], (last_k[st] >> 1) & 1);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel A for the FP32 CG, warp-specialised.  Everything a tile reads is
+// contiguous in memory -- its K rows are one slab of the BSR value array, its
+// column indices and its row_ptr entries one run each, and the z / p entries
+// its columns touch lie in one node range (the tile's halo) -- and their
+// extents are fixed by the mesh (TileDesc, built on the host).  A producer
+// warp streams these five pieces of each tile into a two-stage shared-memory
+// ring with bulk copies (cp.async.bulk, the 1-D form of the TMA engine) and
+// passes the system's scalars along; six consumer warps compute the tile from
+// shared memory with no global loads.  full[s] / empty[s] mbarriers hand each
+// stage over; every wait is bounded.  Tiles that do not fit (scattered
+// numbering) and the FP64 residual passes read global memory instead; a tile
+// whose halo alone does not fit (long grid rows) stages everything but the
+// halo and gathers z and p from global memory.
+constexpr int ST_SLAB_K = STAGE_SLAB_K;
+constexpr int ST_SLAB_C = STAGE_SLAB_C;
+constexpr int ST_SLAB_V = STAGE_SLAB_V;
+constexpr int ST_SLAB_R = STAGE_SLAB_R;
+constexpr int ST_OFF_C = ST_SLAB_K;
+constexpr int ST_OFF_Z = ST_OFF_C + ST_SLAB_C;
+constexpr int ST_OFF_P = ST_OFF_Z + ST_SLAB_V;
+constexpr int ST_OFF_R = ST_OFF_P + ST_SLAB_V;
+constexpr int ST_STAGE = ST_OFF_R + ST_SLAB_R;
+constexpr int ST_STAGES = 2;
+constexpr int ST_SMEM = ST_STAGES * ST_STAGE;
+constexpr int ST_THREADS = NT + 32;  // six consumer warps + one producer warp
 // barrier among the 192 consumer threads only (the producer warp runs ahead)
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
@@ -684,7 +942,8 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     const SysDesc& S = sys[inf.sys];
     SysScalars* sc = S.sc;
     const int real_state = inf.state;
-    const int state = dry ? ST_DONE : real_state;
+    const bool skip = real_state == ST_DONE || real_state == ST_FOLD;
+    const int state = dry || skip ? ST_DONE : real_state;
     const int node = inf.node0 + ln;
     const bool act = lane < 6 * NODES_PER_WARP && ln < inf.nn;
     const int i = 6 * node + rr;
@@ -775,7 +1034,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     // stage s is consumed: hand it back to the producer
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
-    if (real_state == ST_DONE) continue;
+    if (skip) continue;
     part = warp_sum(part);
     part_b = warp_sum(part_b);
     if (lane == 0) {
@@ -836,6 +1095,15 @@ static cudaError_t staged_attributes() {
   return e;
 }
 
+static cudaError_t b32_attributes() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(pcg_b32_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, B32_SMEM);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 cudaError_t launch_pcg_a(bool fp64, const TileDesc* tiles, const int* n_tiles,
                          const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
   if (fp64) {
@@ -852,8 +1120,11 @@ cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
                          const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
   if (fp64)
     pcg_b_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
-  else
-    pcg_b_kernel<float><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
+  else {
+    cudaError_t e = b32_attributes();
+    if (e != cudaSuccess) return e;
+    pcg_b32_kernel<<<grid, NT, B32_SMEM, s>>>(tiles, n_tiles, sys, flags);
+  }
   return cudaGetLastError();
 }
 
@@ -876,7 +1147,8 @@ void pcg_grid_limits(bool fp64, int* grid_a, int* grid_b) {
     staged_attributes();
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, pcg_a_staged_kernel, ST_THREADS,
                                                   ST_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b_kernel<float>, NT, 0);
+    b32_attributes();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, pcg_b32_kernel, NT, B32_SMEM);
   }
   if (sms < 1) sms = 1;
   *grid_a = sms * (per_sm_a < 1 ? 1 : per_sm_a);

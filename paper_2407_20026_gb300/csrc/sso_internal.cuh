@@ -31,7 +31,9 @@ constexpr int NT = 32 * WARPS;                // 192 threads
 // 6 * SPMV_TILE threads.
 constexpr int SPMV_TILE = 32;
 
-enum SysState : int { ST_INIT = 0, ST_PCG = 1, ST_RESID = 2, ST_DONE = 3 };
+// FOLD (FP32 mode only): the sweep's FP32 correction is added to the FP64
+// solution before the FP64 residual pass.
+enum SysState : int { ST_INIT = 0, ST_PCG = 1, ST_RESID = 2, ST_DONE = 3, ST_FOLD = 4 };
 
 // Per-system solver scalars (device memory, one per system).
 struct SysScalars {
@@ -89,10 +91,11 @@ struct SysDesc {
   const int* col;
   const float* K32;
   const double* K64;
-  const float* M32;
+  const float* M32;  // block-Jacobi: packed upper triangle, M32_PACK per node; Jacobi: 6 per node
   const double* M64;
   const double* b;  // right-hand side (FP64)
   double* x;        // solution (FP64)
+  void* dx;         // FP32 mode: correction of the current sweep (x += scale dx at its end)
   double* r64;      // FP64 residual
   void* r;          // inner vectors, float or double
   void* z;
@@ -103,6 +106,14 @@ struct SysDesc {
   double* part_b;   // [2 * WARPS * n_tiles]
   SysScalars* sc;
 };
+
+// ---------------------------------------------------------------------------
+// Packed symmetric 6x6 (upper triangle by rows, 21 values, 3 zeros of
+// padding so that every node starts on a 16-byte boundary).
+constexpr int M32_PACK = 24;
+__host__ __device__ constexpr int sym6(int a, int c) {
+  return a <= c ? a * 6 - a * (a - 1) / 2 + (c - a) : c * 6 - c * (c - 1) / 2 + (a - c);
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (elements.cu)
