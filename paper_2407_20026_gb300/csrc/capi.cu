@@ -144,6 +144,8 @@ struct sso_model {
   float *d_K32, *d_M32;
   void *d_r, *d_z, *d_p0, *d_p1, *d_q;
   double *d_part_a, *d_part_b, *d_dz, *d_dt, *d_C;
+  unsigned* d_chunk_cnt;
+  double* d_chunk_part;
   // material volume (Sec. 3.3): per-quad A t, per-slot t dA/dz (beam slots
   // stay 0), dW/dz, dW/dt, W
   double *d_vol, *d_vslot, *d_vdz, *d_vdt, *d_V;
@@ -385,6 +387,8 @@ bool topology_consistent(const HostMesh& m, const HostTopo& T) {
   return true;
 }
 
+int n_chunks_of(const sso_model* M) { return (M->n_tiles + CHUNK - 1) / CHUNK; }
+
 // Lays out (base == nullptr: sizes only) every device array of a model.
 size_t layout_model(sso_model* M, void* base) {
   Carver c(base);
@@ -424,6 +428,8 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_q = c.take<double>(ndof);
   M->d_part_a = c.take<double>(2 * (size_t)WARPS * M->n_tiles);
   M->d_part_b = c.take<double>(2 * (size_t)WARPS * M->n_tiles);
+  M->d_chunk_cnt = c.take<unsigned>(2 * (size_t)n_chunks_of(M));
+  M->d_chunk_part = c.take<double>(4 * (size_t)n_chunks_of(M));
   M->d_dz = c.take<double>(n);
   M->d_dt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_C = c.take<double>(1);
@@ -598,6 +604,8 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
       ++n_act;
       if (!warm) CK(cudaMemsetAsync(D.x, 0, sizeof(double) * 6 * (size_t)M->n_nodes, B->stream));
       CK(cudaMemsetAsync(M->d_dx, 0, sizeof(double) * 6 * (size_t)M->n_nodes, B->stream));
+      CK(cudaMemsetAsync(M->d_chunk_cnt, 0, sizeof(unsigned) * 2 * (size_t)n_chunks_of(M),
+                         B->stream));
     }
   }
   CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * B->n_sys,
@@ -1036,6 +1044,9 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     D.q = M->d_q;
     D.part_a = M->d_part_a;
     D.part_b = M->d_part_b;
+    D.n_chunks = n_chunks_of(M);
+    D.chunk_cnt = M->d_chunk_cnt;
+    D.chunk_part = M->d_chunk_part;
     for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_tile(M, s, k));
   }
   B->n_tiles = (int)tiles.size();
@@ -1485,6 +1496,9 @@ void fill_sysdesc(SysDesc& D, sso_model* M, int precond) {
   D.q = M->d_q;
   D.part_a = M->d_part_a;
   D.part_b = M->d_part_b;
+  D.n_chunks = n_chunks_of(M);
+  D.chunk_cnt = M->d_chunk_cnt;
+  D.chunk_part = M->d_chunk_part;
 }
 
 void init_scalars(SysScalars& S, const sso_options& o) {

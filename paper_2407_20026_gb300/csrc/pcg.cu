@@ -53,10 +53,6 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
 template <typename T> struct MatOf;
-template <> struct MatOf<float> {
-  static __device__ __forceinline__ const float* K(const SysDesc& S) { return S.K32; }
-  static __device__ __forceinline__ const float* M(const SysDesc& S) { return S.M32; }
-};
 template <> struct MatOf<double> {
   static __device__ __forceinline__ const double* K(const SysDesc& S) { return S.K64; }
   static __device__ __forceinline__ const double* M(const SysDesc& S) { return S.M64; }
@@ -80,14 +76,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   }
   __syncthreads();
   return s;
-}
-
-// Ordered sum of n values part[k * stride + off]; valid in thread 0.
-__device__ __forceinline__ double ordered_sum(const double* part, int n, int stride, int off,
-                                              double* red) {
-  double v = 0.0;
-  for (int k = threadIdx.x; k < n; k += NT) v += __ldcg(part + (size_t)k * stride + off);
-  return block_sum(v, red);
 }
 
 // sum_j K[j][rr][:] . (z + beta pold)[col[j]] over j in [j0, j1), in j order.
@@ -152,34 +140,116 @@ __device__ __forceinline__ RunState read_state(const SysScalars* sc) {
   return r;
 }
 
-// Final reduction of kernel A for one system (thread 0 updates the scalars).
-template <typename SumFn>
-__device__ __forceinline__ void finish_a(const SysDesc& S, SysScalars* sc, int state,
-                                         int* n_active, SumFn sum2) {
-  double sum = 0.0, sum_b = 0.0;
-  sum2(S.part_a, S.n_tiles * WARPS, state != ST_PCG, sum, sum_b);
-  if (threadIdx.x == 0) {
-    if (state == ST_PCG) {
-      sc->pq = sum;
-      if (!(sum > 0.0) || !isfinite(sum)) {
-        sc->status = SSO_ERR_SINGULAR;
-        sc->state = ST_DONE;
-        atomicSub(n_active, 1);
-      } else {
-        sc->alpha = sc->rz / sum;
-        sc->parity ^= 1;
-      }
+// Scalar update of kernel A for one system (one thread): sum = p^T q in a CG
+// iteration, else ||r64||^2; sum_b = ||b||^2.
+__device__ __forceinline__ void finish_a_scalars(SysScalars* sc, int state, double sum,
+                                                 double sum_b, int* n_active) {
+  if (state == ST_PCG) {
+    sc->pq = sum;
+    if (!(sum > 0.0) || !isfinite(sum)) {
+      sc->status = SSO_ERR_SINGULAR;
+      sc->state = ST_DONE;
+      atomicSub(n_active, 1);
     } else {
-      sc->rr64 = sum;
-      sc->ff = sum_b;
+      sc->alpha = sc->rz / sum;
+      sc->parity ^= 1;
     }
-    sc->cnt_a = 0u;
+  } else {
+    sc->rr64 = sum;
+    sc->ff = sum_b;
+  }
+  sc->cnt_a = 0u;
+}
+
+// Sums of the pairs p[2e], p[2e + 1] for e in [e0, min(e0 + CHUNK_PER_THREAD, e1)),
+// in e order; every load is issued before the first add.
+__device__ __forceinline__ void sum_pairs(const double* p, int e0, int e1, double& a,
+                                          double& b) {
+  double x[CHUNK_PER_THREAD], y[CHUNK_PER_THREAD];
+#pragma unroll
+  for (int u = 0; u < CHUNK_PER_THREAD; ++u) {
+    const int e = e0 + u;
+    x[u] = e < e1 ? __ldcg(p + 2 * (size_t)e) : 0.0;
+    y[u] = e < e1 ? __ldcg(p + 2 * (size_t)e + 1) : 0.0;
+  }
+  a = 0.0;
+  b = 0.0;
+#pragma unroll
+  for (int u = 0; u < CHUNK_PER_THREAD; ++u) {
+    a += x[u];
+    b += y[u];
+  }
+}
+
+// Kernel A, end of a CTA's run of the system-local tiles [r0, r1) (their
+// partials written): the run is counted into its chunks; a chunk completed
+// here is summed (CHUNK_PER_THREAD contiguous partials per thread), and the
+// chunk that completes the system leads to the sum of the chunk sums and the
+// scalar update.  Every grouping depends on the system alone.  sync() is a
+// barrier over the NT threads running this, bsum() their fixed-order sum
+// (valid in thread 0); flag is shared scratch; count = false (an aborted CTA)
+// counts nothing.
+template <typename Sync, typename BSum>
+__device__ __forceinline__ void a_count_run(const SysDesc& S, SysScalars* sc, int state, int r0,
+                                            int r1, int t, int* n_active, int* flag, bool count,
+                                            Sync sync, BSum bsum) {
+  for (int c = r0 / CHUNK; c * CHUNK < r1; ++c) {
+    const int lo = max(r0, c * CHUNK), hi = min(r1, (c + 1) * CHUNK);
+    const int m = min(CHUNK, S.n_tiles - c * CHUNK);
+    if (t == 0) {
+      int done = 0;
+      if (count) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&S.chunk_cnt[c], (unsigned)(hi - lo));
+        done = prev + (unsigned)(hi - lo) == (unsigned)m;
+      }
+      *flag = done;
+    }
+    sync();
+    const bool done = *flag != 0;
+    sync();
+    if (!done) continue;
+    __threadfence();
+    double v, vb;
+    sum_pairs(S.part_a + 2 * (size_t)c * CHUNK * WARPS, CHUNK_PER_THREAD * t, m * WARPS, v, vb);
+    const double ca = bsum(v);
+    const double cb = bsum(vb);
+    if (S.n_chunks == 1) {  // the chunk is the system
+      if (t == 0) {
+        S.chunk_cnt[c] = 0u;
+        finish_a_scalars(sc, state, ca, cb, n_active);
+      }
+      sync();
+      continue;
+    }
+    if (t == 0) {
+      S.chunk_part[2 * c] = ca;
+      S.chunk_part[2 * c + 1] = cb;
+      S.chunk_cnt[c] = 0u;
+      __threadfence();
+      const unsigned prev = atomicAdd(&sc->cnt_a, 1u);
+      *flag = prev + 1u == (unsigned)S.n_chunks;
+    }
+    sync();
+    const bool last = *flag != 0;
+    sync();
+    if (!last) continue;
+    __threadfence();
+    double sa = 0.0, sb = 0.0;
+    for (int q = t; q < S.n_chunks; q += NT) {
+      sa += __ldcg(S.chunk_part + 2 * (size_t)q);
+      sb += __ldcg(S.chunk_part + 2 * (size_t)q + 1);
+    }
+    const double A = bsum(sa);
+    const double Bs = bsum(sb);
+    if (t == 0) finish_a_scalars(sc, state, A, Bs, n_active);
+    sync();
   }
 }
 
 // Kernel A, FP64 CG (and any system kernel A reads from global memory).
 template <typename T>
-__global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict__ tiles,
+__global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const TileDesc* __restrict__ tiles,
                                                       const int* __restrict__ n_tiles_ptr,
                                                       const SysDesc* __restrict__ sys,
                                                       int* __restrict__ flags) {
@@ -247,23 +317,11 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict
     ++run;
     // end of this CTA's run of the system: count it
     if (tile + 1 < end && tiles[tile + 1].sys == sid) continue;
+    const int r1 = tile - S.tile0 + 1;
     __syncthreads();
-    if (t == 0) {
-      __threadfence();
-      const unsigned prev = atomicAdd(&sc->cnt_a, (unsigned)run);
-      s_last = (prev + (unsigned)run == (unsigned)S.n_tiles);
-    }
+    a_count_run(S, sc, state, r1 - run, r1, t, n_active, &s_last, true,
+                [] { __syncthreads(); }, [&](double v) { return block_sum(v, red); });
     run = 0;
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      finish_a(S, sc, state, n_active,
-               [&](const double* part2, int n, bool both, double& a, double& b) {
-                 a = ordered_sum(part2, n, 2, 0, red);
-                 b = both ? ordered_sum(part2, n, 2, 1, red) : 0.0;
-               });
-      __syncthreads();
-    }
   }
 }
 
@@ -276,14 +334,6 @@ __global__ void __launch_bounds__(NT, 4) pcg_a_kernel(const TileDesc* __restrict
 // completes the system sums all of its tile partials in tile order and updates
 // the scalars.  No CTA barriers; the grouping depends on the system only, so
 // results are bit-identical alone and in any batch.
-__device__ __forceinline__ void ld4x9(const float* p, float m[36]) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const float4 v = __ldg(q + k);
-    m[4 * k] = v.x; m[4 * k + 1] = v.y; m[4 * k + 2] = v.z; m[4 * k + 3] = v.w;
-  }
-}
 __device__ __forceinline__ void ld4x9(const double* p, double m[36]) {
   const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
@@ -370,6 +420,55 @@ __device__ __forceinline__ void finish_b(SysScalars* sc, int state, double s1, d
   sc->cnt_b = 0u;
 }
 
+// Kernel B, warp level: adds n of this warp's tiles to chunk c of system S.
+// The warp that completes a chunk sums the chunk's tile partials
+// (CHUNK_PER_THREAD contiguous ones per lane); the one that completes the last chunk sums the chunk sums in order
+// and updates the scalars.  Every grouping depends on the system alone.
+__device__ __forceinline__ void b_count(const SysDesc& S, SysScalars* sc, int state, int c, int n,
+                                        int lane, int* n_active, bool fold) {
+  const int m = min(CHUNK, S.n_tiles - c * CHUNK);
+  unsigned* cnt = S.chunk_cnt + S.n_chunks;
+  double* cpart = S.chunk_part + 2 * (size_t)S.n_chunks;
+  int done = 0;
+  if (lane == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&cnt[c], (unsigned)n);
+    done = prev + (unsigned)n == (unsigned)m;
+  }
+  if (!__shfl_sync(0xffffffffu, done, 0)) return;
+  __threadfence();
+  double v1, v2;
+  sum_pairs(S.part_b + 2 * (size_t)c * CHUNK, CHUNK_PER_THREAD * lane, m, v1, v2);
+  v1 = warp_sum(v1);
+  v2 = warp_sum(v2);
+  if (S.n_chunks == 1) {  // the chunk is the system
+    if (lane == 0) {
+      cnt[c] = 0u;
+      finish_b(sc, state, v1, v2, n_active, fold);
+    }
+    return;
+  }
+  int last = 0;
+  if (lane == 0) {
+    cpart[2 * c] = v1;
+    cpart[2 * c + 1] = v2;
+    cnt[c] = 0u;
+    __threadfence();
+    const unsigned prev = atomicAdd(&sc->cnt_b, 1u);
+    last = prev + 1u == (unsigned)S.n_chunks;
+  }
+  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  __threadfence();
+  double a1 = 0.0, a2 = 0.0;
+  for (int q = lane; q < S.n_chunks; q += 32) {
+    a1 += __ldcg(cpart + 2 * (size_t)q);
+    a2 += __ldcg(cpart + 2 * (size_t)q + 1);
+  }
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane == 0) finish_b(sc, state, a1, a2, n_active, fold);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict__ tiles,
                                                       const int* __restrict__ n_tiles_ptr,
@@ -385,6 +484,7 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
   bool work = false, block = true;
   double inv_norm = 0.0, ua = 0.0;
   T alpha = T(0);
+  int pend_c = -1, pend_n = 0;
   for (int tile = begin + w; tile < end; tile += WARPS) {
     const TileDesc& td = tiles[tile];
     const int sid = td.sys;
@@ -454,26 +554,23 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
     }
     v1 = warp_sum(v1);
     v2 = warp_sum(v2);
-    int last = 0;
+    const int lt = tile - S.tile0;
     if (lane == 0) {
-      double* dst = S.part_b + 2 * (size_t)(tile - S.tile0);
+      double* dst = S.part_b + 2 * (size_t)lt;
       dst[0] = v1;
       dst[1] = v2;
-      __threadfence();
-      const unsigned prev = atomicAdd(&sc->cnt_b, 1u);
-      last = prev + 1u == (unsigned)S.n_tiles;
     }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      double a1 = 0.0, a2 = 0.0;
-      for (int k = lane; k < S.n_tiles; k += 32) {
-        a1 += __ldcg(S.part_b + 2 * (size_t)k);
-        a2 += __ldcg(S.part_b + 2 * (size_t)k + 1);
-      }
-      a1 = warp_sum(a1);
-      a2 = warp_sum(a2);
-      if (lane == 0) finish_b(sc, state, a1, a2, n_active, false);
+    // count the warp's tiles per chunk, flushing when the chunk or the run ends
+    if (lt / CHUNK != pend_c) {
+      if (pend_n) b_count(S, sc, state, pend_c, pend_n, lane, n_active, false);
+      pend_c = lt / CHUNK;
+      pend_n = 0;
+    }
+    ++pend_n;
+    if (!(tile + WARPS < end && tiles[tile + WARPS].sys == sid)) {
+      b_count(S, sc, state, pend_c, pend_n, lane, n_active, false);
+      pend_c = -1;
+      pend_n = 0;
     }
   }
 }
@@ -632,7 +729,7 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
   __syncwarp();
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
-  int k = 0, run = 0, last_k[2] = {-1, -1};
+  int k = 0, pend_c = -1, pend_n = 0, last_k[2] = {-1, -1};
   bool dry = false;
   BJob J;
   if (begin + w < end) {
@@ -740,34 +837,23 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
       __syncwarp();
       v1 = warp_sum(v1);
       v2 = warp_sum(v2);
+      const int lt = tile - S.tile0;
       if (lane == 0) {
-        double* dst = S.part_b + 2 * (size_t)(tile - S.tile0);
+        double* dst = S.part_b + 2 * (size_t)lt;
         dst[0] = v1;
         dst[1] = v2;
       }
-      ++run;
+      // count the warp's tiles per chunk, flushing when the chunk or the run ends
+      if (lt / CHUNK != pend_c) {
+        if (pend_n) b_count(S, sc, state, pend_c, pend_n, lane, n_active, true);
+        pend_c = lt / CHUNK;
+        pend_n = 0;
+      }
+      ++pend_n;
       if (!(nxt < end && JN.sid == J.sid)) {
-        int last = 0;
-        if (lane == 0) {
-          __threadfence();
-          const unsigned prev = atomicAdd(&sc->cnt_b, (unsigned)run);
-          last = prev + (unsigned)run == (unsigned)S.n_tiles;
-        }
-        run = 0;
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-          __threadfence();
-          double a1 = 0.0, a2 = 0.0;
-          if (state != ST_FOLD) {
-            for (int q = lane; q < S.n_tiles; q += 32) {
-              a1 += __ldcg(S.part_b + 2 * (size_t)q);
-              a2 += __ldcg(S.part_b + 2 * (size_t)q + 1);
-            }
-            a1 = warp_sum(a1);
-            a2 = warp_sum(a2);
-          }
-          if (lane == 0) finish_b(sc, state, a1, a2, n_active, true);
-        }
+        b_count(S, sc, state, pend_c, pend_n, lane, n_active, true);
+        pend_c = -1;
+        pend_n = 0;
       }
     }
     if (nxt < end) J = JN;
@@ -1044,31 +1130,13 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     }
     ++run;
     if (tile + 1 < end && tiles[tile + 1].sys == inf.sys) continue;
+    const int r1 = tile - S.tile0 + 1;
     consumer_sync();
-    if (t == 0) {
-      s_last = 0;
-      if (!s_abort) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&sc->cnt_a, (unsigned)run);
-        s_last = (prev + (unsigned)run == (unsigned)S.n_tiles);
-      }
-    }
+    const bool count = !s_abort;
+    consumer_sync();
+    a_count_run(S, sc, real_state, r1 - run, r1, t, n_active, &s_last, count,
+                [] { consumer_sync(); }, [&](double v) { return consumer_block_sum(v, red); });
     run = 0;
-    consumer_sync();
-    if (s_last) {
-      __threadfence();
-      finish_a(S, sc, real_state, n_active,
-               [&](const double* part2, int n, bool both, double& a, double& b) {
-                 double v = 0.0, vb = 0.0;
-                 for (int q = t; q < n; q += NT) {
-                   v += __ldcg(part2 + 2 * (size_t)q);
-                   if (both) vb += __ldcg(part2 + 2 * (size_t)q + 1);
-                 }
-                 a = consumer_block_sum(v, red);
-                 b = both ? consumer_block_sum(vb, red) : 0.0;
-               });
-      consumer_sync();
-    }
   }
 }
 

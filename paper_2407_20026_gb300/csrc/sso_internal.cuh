@@ -43,7 +43,7 @@ struct SysScalars {
   int inner;        // CG iterations in the current sweep
   int sweeps;       // FP64 residual recomputations after the first
   int status;       // sso_status
-  unsigned int cnt_a, cnt_b;  // tile-completion counters (last-CTA reduction)
+  unsigned int cnt_a, cnt_b;  // chunk-completion counters (last-chunk reduction)
   double rz;        // r^T z of the current iteration
   double beta;      // rz_new / rz_old
   double pq;        // p^T K p
@@ -104,10 +104,24 @@ struct SysDesc {
   void* q;
   double* part_a;   // [2 * WARPS * n_tiles]
   double* part_b;   // [2 * WARPS * n_tiles]
+  // two-level reductions: the system's tiles fall in fixed chunks of CHUNK;
+  // the kernel that completes a chunk sums its partials, the one that
+  // completes the last chunk sums the chunk sums
+  int n_chunks;
+  unsigned* chunk_cnt;  // [2 * n_chunks]: tiles counted per chunk, kernel A then kernel B
+  double* chunk_part;   // [4 * n_chunks]: two sums per chunk, kernel A then kernel B
   SysScalars* sc;
 };
 
 // ---------------------------------------------------------------------------
+// Tiles per reduction chunk.  A chunk's kernel-A partials (CHUNK * WARPS)
+// are CHUNK_PER_THREAD contiguous ones per thread of a CTA, its kernel-B
+// partials (CHUNK) as many per lane of a warp: one round of loads each.
+constexpr int CHUNK = 256;
+constexpr int CHUNK_PER_THREAD = 8;
+static_assert(CHUNK * WARPS == NT * CHUNK_PER_THREAD, "kernel-A chunk: 8 partials per thread");
+static_assert(CHUNK == 32 * CHUNK_PER_THREAD, "kernel-B chunk: 8 partials per lane");
+
 // Packed symmetric 6x6 (upper triangle by rows, 21 values, 3 zeros of
 // padding so that every node starts on a 16-byte boundary).
 constexpr int M32_PACK = 24;
