@@ -687,18 +687,44 @@ TileDesc make_tile(const sso_model* M, int s, int k) {
   d.nblk = j1 - d.j0;
   d.cb = d.j0 & ~3;
   d.ncb = ((j1 + 3) & ~3) - d.cb;
-  int lo = M->n_nodes, hi = -1;
-  for (int b = d.j0; b < j1; ++b) {
-    lo = std::min(lo, M->h_col[b]);
-    hi = std::max(hi, M->h_col[b]);
+  // halo: the sorted column nodes, cut into runs at gaps longer than 8 nodes
+  // (a gap shorter than that costs less to copy than a run of its own), each
+  // run widened to even bounds (16-byte bulk copies of 24-byte nodes); a
+  // single run covering everything is used whenever it fits
+  std::vector<int> cols(M->h_col.begin() + d.j0, M->h_col.begin() + j1);
+  std::sort(cols.begin(), cols.end());
+  cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+  for (int k = 0; k < HALO_RUNS; ++k) d.vlo[k] = d.nv[k] = 0;
+  int halo_nodes = 0, runs = 0;
+  if (!cols.empty()) {
+    const int lo = cols.front() & ~1, hi = cols.back() | 1;
+    if ((long long)(hi - lo + 1) * 24 <= STAGE_SLAB_V) {
+      d.vlo[0] = lo;
+      d.nv[0] = hi - lo + 1;
+      runs = 1;
+    } else {
+      std::vector<std::pair<int, int>> seg;  // [first, last] nodes, even / odd bounds
+      for (int c : cols) {
+        const int a = c & ~1, b = c | 1;
+        if (!seg.empty() && a <= seg.back().second + 9)
+          seg.back().second = std::max(seg.back().second, b);
+        else
+          seg.push_back({a, b});
+      }
+      runs = (int)seg.size();
+      for (int k = 0; k < runs && k < HALO_RUNS; ++k) {
+        d.vlo[k] = seg[k].first;
+        d.nv[k] = seg[k].second - seg[k].first + 1;
+      }
+    }
+    for (int k = 0; k < HALO_RUNS; ++k) halo_nodes += d.nv[k];
   }
-  d.vlo = hi >= 0 ? (lo & ~1) : 0;
-  d.nv = hi >= 0 ? ((hi | 1) - d.vlo + 1) : 0;
   d.rb = d.node0 & ~3;
   d.nrb = ((d.node0 + d.nn + 1 + 3) & ~3) - d.rb;
   d.stage_k = d.nblk > 0 && (long long)d.nblk * 144 <= STAGE_SLAB_K &&
               d.ncb * 4 <= STAGE_SLAB_C && d.nrb * 4 <= STAGE_SLAB_R;
-  d.stage = d.stage_k && d.nv > 0 && (long long)d.nv * 24 <= STAGE_SLAB_V;
+  d.stage = d.stage_k && runs >= 1 && runs <= HALO_RUNS &&
+            (long long)halo_nodes * 24 <= STAGE_SLAB_V;
   return d;
 }
 

@@ -32,6 +32,7 @@
 // grouping into tiles and warps depends only on the system itself, so its
 // iterates are bit-identical whether it runs alone or inside any batch.
 // There are no spin-waits.
+#include <climits>
 #include <math.h>
 
 #include "sso_internal.cuh"
@@ -916,7 +917,10 @@ __device__ __forceinline__ void ld6s(const float* p, float v[6]) {
 struct StageInfo {
   int state, mode, first, parity;  // mode 1: the tile's data is in the stage
   float beta;
-  int sys, node0, nn, j0, cb, vlo, rb;
+  int sys, node0, nn, j0, cb, rb;
+  // halo runs in the stage: column c sits at slot c + shift[k] (nodes) for the
+  // last run k whose first node is <= c (first nodes of unused runs: INT_MAX)
+  int v1, v2, sh0, sh1, sh2;
 };
 
 __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
@@ -970,8 +974,12 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.nn = td.nn;
       inf.j0 = td.j0;
       inf.cb = td.cb;
-      inf.vlo = td.vlo;
       inf.rb = td.rb;
+      inf.v1 = td.nv[1] ? td.vlo[1] : INT_MAX;
+      inf.v2 = td.nv[2] ? td.vlo[2] : INT_MAX;
+      inf.sh0 = -td.vlo[0];
+      inf.sh1 = td.nv[0] - td.vlo[1];
+      inf.sh2 = td.nv[0] + td.nv[1] - td.vlo[2];
       ++issued;
       if (R.state == ST_PCG && td.stage_k) {
         // mode 1: K rows, columns, row_ptr and both vector halos; mode 2: the
@@ -981,15 +989,24 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         const float* z = (const float*)S->z;
         const float* pold = R.first ? z : (const float*)(R.parity ? S->p1 : S->p0);
         const uint32_t kb = (uint32_t)td.nblk * 144u, cb = (uint32_t)td.ncb * 4u;
-        const uint32_t vb = td.stage ? (uint32_t)td.nv * 24u : 0u, rb = (uint32_t)td.nrb * 4u;
+        const uint32_t rb = (uint32_t)td.nrb * 4u;
+        uint32_t vb = 0u;
+        if (td.stage)
+          for (int k = 0; k < HALO_RUNS; ++k) vb += (uint32_t)td.nv[k] * 24u;
         unsigned char* st = ring + s * ST_STAGE;
         fence_proxy_async();
         mbar_arrive_tx(&full[s], kb + cb + 2 * vb + rb);
         bulk_g2s(st, S->K32 + (size_t)td.j0 * 36, kb, &full[s]);
         bulk_g2s(st + ST_OFF_C, S->col + td.cb, cb, &full[s]);
-        if (vb) {
-          bulk_g2s(st + ST_OFF_Z, z + (size_t)td.vlo * 6, vb, &full[s]);
-          bulk_g2s(st + ST_OFF_P, pold + (size_t)td.vlo * 6, vb, &full[s]);
+        if (td.stage) {
+          uint32_t off = 0u;  // bytes into each vector slab
+          for (int k = 0; k < HALO_RUNS; ++k) {
+            if (!td.nv[k]) continue;
+            const uint32_t b = (uint32_t)td.nv[k] * 24u;
+            bulk_g2s(st + ST_OFF_Z + off, z + (size_t)td.vlo[k] * 6, b, &full[s]);
+            bulk_g2s(st + ST_OFF_P + off, pold + (size_t)td.vlo[k] * 6, b, &full[s]);
+            off += b;
+          }
         }
         bulk_g2s(st + ST_OFF_R, S->row_ptr + td.rb, rb, &full[s]);
       } else {
@@ -1045,20 +1062,23 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
           const int j0 = Rs[node], j1 = Rs[node + 1];
           const float* Ks = reinterpret_cast<const float*>(st) + (size_t)(j0 - inf.j0) * 36 + rr * 6;
           const int* Cs = reinterpret_cast<const int*>(st + ST_OFF_C) - inf.cb;
-          const float* Zs = reinterpret_cast<const float*>(st + ST_OFF_Z) - (size_t)inf.vlo * 6;
-          const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P) - (size_t)inf.vlo * 6;
+          const float* Zs = reinterpret_cast<const float*>(st + ST_OFF_Z);
+          const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P);
+          const int v1 = inf.v1, v2 = inf.v2, sh0 = inf.sh0, sh1 = inf.sh1, sh2 = inf.sh2;
+          auto slot = [&](int c) { return 6 * (c + (c >= v2 ? sh2 : (c >= v1 ? sh1 : sh0))); };
           for (int j = j0; j < j1; ++j) {
-            const int c = Cs[j];
+            const int o = slot(Cs[j]);
             float kv[6], zv[6], pv[6];
             ld6s(Ks, kv);
-            ld6s(Zs + (size_t)c * 6, zv);
-            ld6s(Ps + (size_t)c * 6, pv);
+            ld6s(Zs + o, zv);
+            ld6s(Ps + o, pv);
             Ks += 36;
 #pragma unroll
             for (int q = 0; q < 6; ++q) acc = fmaf(kv[q], fmaf(beta, pv[q], zv[q]), acc);
           }
-          zi = Zs[i];
-          pi_old = Ps[i];
+          const int oi = slot(node) + rr;
+          zi = Zs[oi];
+          pi_old = Ps[oi];
         } else if (inf.mode == 2) {
           // K rows, columns and row_ptr from the stage; z and p gathered from
           // global memory, three columns in flight at a time

@@ -65,6 +65,11 @@ struct SysScalars {
 // batch on the host).  The K rows of a tile are the contiguous blocks
 // [j0, j0 + nblk); the columns they read lie in the node range of the halo.
 // The *_b fields give 16-byte aligned runs for bulk copies.
+// A tile's halo (the z / p entries its rows read) is staged as at most this
+// many runs of consecutive nodes: the rows above, at and below a tile of a
+// row-major grid.
+constexpr int HALO_RUNS = 3;
+
 struct TileDesc {
   int sys;     // system index in the batch
   int node0;   // first node of the tile
@@ -73,8 +78,8 @@ struct TileDesc {
   int nblk;    // row_ptr[node0 + nn] - j0
   int cb;      // first column index to copy (multiple of 4)
   int ncb;     // column indices to copy (multiple of 4)
-  int vlo;     // first halo node (even)
-  int nv;      // halo nodes (even)
+  int vlo[HALO_RUNS];  // first node of each halo run (even), ascending
+  int nv[HALO_RUNS];   // nodes of each halo run (even; 0: unused)
   int rb;      // first row_ptr entry to copy (multiple of 4)
   int nrb;     // row_ptr entries to copy (multiple of 4)
   int stage;   // 1 when the FP32 slab, columns, halo and row_ptr fit the staging buffers

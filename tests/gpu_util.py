@@ -67,3 +67,16 @@ def hub_model(n_side=8, hub=27):
     m["beam_conn"] = conn.astype(np.int32)
     m["beam_props"] = np.tile(m["beam_props"][:1], (conn.shape[0], 1))
     return m
+
+
+def permuted(m, perm):
+    """The same structure with its nodes renumbered: old node k becomes
+    perm[k].  Returns (mesh, perm); u_new[6 perm[k] + d] = u_old[6 k + d]."""
+    perm = np.asarray(perm)
+    inv = np.argsort(perm)
+    out = dict(m)
+    for k in ("xyz", "fixed", "nodal_load"):
+        out[k] = m[k][inv]
+    out["quad_conn"] = perm[m["quad_conn"]].astype(np.int32)
+    out["beam_conn"] = perm[m["beam_conn"]].astype(np.int32)
+    return out, perm

@@ -11,7 +11,7 @@ import torch
 
 import meshgen
 from gpu_util import (TOL_ELEMENT, TOL_FP32_IR, TOL_FP64, bsr_to_dense, hub_model, mixed_model,
-                      rel, small_shell, with_supports)
+                      permuted, rel, small_shell, with_supports)
 
 pytestmark = pytest.mark.gpu
 
@@ -320,25 +320,12 @@ def test_bsr_spmv_entry_point(sso, name):
     assert np.array_equal(y1, y2.cpu().numpy()) and float(d1) == float(d2)
 
 
-def _permuted(m, seed):
-    """The same structure with randomly renumbered nodes."""
-    n = m["xyz"].shape[0]
-    perm = np.random.default_rng(seed).permutation(n)  # new index of old node k
-    inv = np.argsort(perm)
-    out = dict(m)
-    for k in ("xyz", "fixed", "nodal_load"):
-        out[k] = m[k][inv]
-    out["quad_conn"] = perm[m["quad_conn"]].astype(np.int32)
-    out["beam_conn"] = perm[m["beam_conn"]].astype(np.int32)
-    return out, perm
-
-
 def test_scattered_numbering_fallback_path(sso, orc):
     """Random node numbering: tile halos span the mesh, so the FP32 kernel
     reads z and p from global memory instead of shared-memory halos."""
     m = meshgen.shell(n_el=20, span=10.0, seed=6)
     ref = orc.gradient(m)
-    mp, perm = _permuted(m, 3)
+    mp, perm = permuted(m, np.random.default_rng(3).permutation(m["xyz"].shape[0]))
     mdl = sso.Model(mp)
     st = mdl.solve(precision="fp32_ir", rtol=1e-9)
     assert st["status"] == 0
