@@ -430,7 +430,6 @@ def run_large(a):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = sso.kernel_launches()
-    batch.set_profiling(True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     stream = torch.cuda.current_stream()
     ev[0].record(stream)
@@ -439,11 +438,17 @@ def run_large(a):
     batch.gradient()
     ev[2].record(stream)
     ev[2].synchronize()
+    launches = sso.kernel_launches() - l0
+    clk = clocks.stop()
+    # kernel and phase durations: the same solve again, untimed, with events
+    # around every kernel (they serialise the kernels)
+    batch.set_profiling(True)
+    batch.solve(opts)
+    batch.gradient()
+    torch.cuda.synchronize()
     ms_a, ms_b, pairs = batch.kernel_times()
     su = batch.setup_times()
     batch.set_profiling(False)
-    launches = sso.kernel_launches() - l0
-    clk = clocks.stop()
     solve_ms = ev[0].elapsed_time(ev[1])
     grad_ms = ev[1].elapsed_time(ev[2])
     s0 = stats[0]
@@ -619,7 +624,6 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     launches0 = sso.kernel_launches()
-    batch.set_profiling(True)
     step_ms = []
     iters_total = 0
     sweeps_total = 0
@@ -638,11 +642,20 @@ def main():
         iters_total += sum(s["iterations"] for s in stats)
         sweeps_total += sum(s["sweeps"] for s in stats)
     torch.cuda.synchronize()
-    ms_a, ms_b, timed_pairs = batch.kernel_times()
-    batch.set_profiling(False)
     launches = sso.kernel_launches() - launches0
     clk = clocks.stop()
     barrier()
+    # kernel durations: one more step, untimed, with CUDA events around every
+    # CG kernel on the library's stream (the events serialise the kernels, so
+    # they are kept out of the timed steps)
+    batch.set_profiling(True)
+    flush.fill_(-1.0)
+    pstats = step_device()
+    torch.cuda.synchronize()
+    ms_a, ms_b, timed_pairs = batch.kernel_times()
+    batch.set_profiling(False)
+    p_iters = sum(s["iterations"] for s in pstats)
+    p_sweeps = sum(s["sweeps"] for s in pstats)
     total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -657,7 +670,7 @@ def main():
     wsz = 4 if fp32 else 8
     bytes_pcg = nblk * (36 * wsz + 4) + (n_nodes + 1) * 4 + 4 * (6 * n_nodes * wsz)
     bytes_resid = nblk * (36 * 8 + 4) + (n_nodes + 1) * 4 + 3 * (6 * n_nodes * 8)
-    alg_bytes = iters_total * bytes_pcg + sweeps_total * bytes_resid
+    alg_bytes = p_iters * bytes_pcg + p_sweeps * bytes_resid
     achieved = alg_bytes / (ms_a / 1000.0) / 1e9 if ms_a > 0 else None
     a_launches = timed_pairs
     traffic = kernel_traffic("pcg.cu", "pcg_a_%s" % ("f32" if fp32 else "f64"))

@@ -65,6 +65,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Programmatic dependent launch: a CG kernel lets the next kernel of the
+// stream begin launching as soon as all of its own CTAs run (its grids are one
+// wave, so waiting CTAs never hold back its own), and waits for the previous
+// kernel's completion and memory before its first read of solver state.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Sum over the NT threads of the CTA in a fixed order; valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);
@@ -256,11 +265,13 @@ __global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const TileDesc* __restrict
                                                       int* __restrict__ flags) {
   __shared__ double red[WARPS];
   __shared__ int s_last;
+  pdl_trigger();
   int* n_active = flags;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
+  pdl_wait();
   int run = 0, cur = -1;
   RunState R;
   R.state = ST_DONE;
@@ -475,10 +486,12 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
                                                       const int* __restrict__ n_tiles_ptr,
                                                       const SysDesc* __restrict__ sys,
                                                       int* __restrict__ flags) {
+  pdl_trigger();
   int* n_active = flags;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
+  pdl_wait();
   int cur = -1;
   RunState R;
   R.state = ST_DONE;
@@ -719,6 +732,7 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
                                                         int* __restrict__ flags) {
   extern __shared__ __align__(128) float b32_smem[];
   __shared__ __align__(8) unsigned long long full[WARPS][2];
+  pdl_trigger();
   int* n_active = flags;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stages = b32_smem + w * 2 * B32_STAGE;
@@ -730,6 +744,7 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
   __syncwarp();
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
+  pdl_wait();
   int k = 0, pend_c = -1, pend_n = 0, last_k[2] = {-1, -1};
   bool dry = false;
   BJob J;
@@ -931,6 +946,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
   __shared__ StageInfo info[ST_STAGES];
   __shared__ double red[WARPS];
   __shared__ int s_last, s_abort;
+  pdl_trigger();
   int* n_active = flags;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   int begin, end;
@@ -944,6 +960,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     s_abort = 0;
   }
   __syncthreads();
+  pdl_wait();
 
   if (w == WARPS) {
     // ---------------- producer warp (lane 0) ----------------
@@ -1192,28 +1209,42 @@ static cudaError_t b32_attributes() {
   return e;
 }
 
+// A CG kernel launched with programmatic stream serialisation (see pdl_wait).
+static cudaError_t launch_cg_kernel(void (*kernel)(const TileDesc*, const int*, const SysDesc*,
+                                                   int*),
+                                    int grid, int threads, int smem, cudaStream_t s,
+                                    const TileDesc* tiles, const int* n_tiles,
+                                    const SysDesc* sys, int* flags) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, tiles, n_tiles, sys, flags);
+}
+
 cudaError_t launch_pcg_a(bool fp64, const TileDesc* tiles, const int* n_tiles,
                          const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
-  if (fp64) {
-    pcg_a_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
-  } else {
-    cudaError_t e = staged_attributes();
-    if (e != cudaSuccess) return e;
-    pcg_a_staged_kernel<<<grid, ST_THREADS, ST_SMEM, s>>>(tiles, n_tiles, sys, flags);
-  }
-  return cudaGetLastError();
+  if (fp64)
+    return launch_cg_kernel(pcg_a_kernel<double>, grid, NT, 0, s, tiles, n_tiles, sys, flags);
+  cudaError_t e = staged_attributes();
+  if (e != cudaSuccess) return e;
+  return launch_cg_kernel(pcg_a_staged_kernel, grid, ST_THREADS, ST_SMEM, s, tiles, n_tiles,
+                          sys, flags);
 }
 
 cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
                          const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
   if (fp64)
-    pcg_b_kernel<double><<<grid, NT, 0, s>>>(tiles, n_tiles, sys, flags);
-  else {
-    cudaError_t e = b32_attributes();
-    if (e != cudaSuccess) return e;
-    pcg_b32_kernel<<<grid, NT, B32_SMEM, s>>>(tiles, n_tiles, sys, flags);
-  }
-  return cudaGetLastError();
+    return launch_cg_kernel(pcg_b_kernel<double>, grid, NT, 0, s, tiles, n_tiles, sys, flags);
+  cudaError_t e = b32_attributes();
+  if (e != cudaSuccess) return e;
+  return launch_cg_kernel(pcg_b32_kernel, grid, NT, B32_SMEM, s, tiles, n_tiles, sys, flags);
 }
 
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s) {
