@@ -65,6 +65,41 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Double-float sums of FP32 products: an unevaluated sum hi + lo of two
+// floats, formed only with error-free transformations (the exact product
+// a b = p + fma(a, b, -p); Knuth's two-sum; a fast two-sum to renormalise),
+// so a dot product of FP32 vectors is accumulated to about 48 significant
+// bits on the FP32 pipes.  The FP32 CG kernels sum a warp's terms this way
+// and convert once to FP64, where every later sum (tiles, chunks) happens:
+// on this GPU an FP64 instruction costs a warp about 64 FP32 ones.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, e);
+  return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+// Fixed-shape tree over the warp; the sum is in lane 0.
+__device__ __forceinline__ DF df_warp_sum(DF x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF y;
+    y.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
+    y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
+    x = df_add(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ double df_double(DF x) { return (double)x.hi + (double)x.lo; }
+
 // Programmatic dependent launch: a CG kernel lets the next kernel of the
 // stream begin launching as soon as all of its own CTAs run (its grids are one
 // wave, so waiting CTAs never hold back its own), and waits for the previous
@@ -776,7 +811,7 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
     if (state != ST_DONE) {
       const int nn = J.nn;
       const size_t v0 = 6 * (size_t)J.node0;
-      double v1 = 0.0, v2 = 0.0;
+      DF d1 = {0.f, 0.f}, d2 = {0.f, 0.f};  // r^T z, r^T r terms of the thread's node
       if (state == ST_FOLD) {
         if (!dry) {
           double* x = S.x + v0;
@@ -838,10 +873,12 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
             for (int a = 0; a < 6; ++a) zv[a] = m[a] * rv[a];
           }
           st6(Vq + 6 * lane, zv);  // q is consumed: its slot now holds z
+          d1 = df_prod(rv[0], zv[0]);
+          d2 = df_prod(rv[0], rv[0]);
 #pragma unroll
-          for (int a = 0; a < 6; ++a) {
-            v1 += (double)rv[a] * (double)zv[a];
-            v2 += (double)rv[a] * (double)rv[a];
+          for (int a = 1; a < 6; ++a) {
+            d1 = df_add(d1, df_prod(rv[a], zv[a]));
+            d2 = df_add(d2, df_prod(rv[a], rv[a]));
           }
         }
         __syncwarp();
@@ -851,8 +888,8 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
       }
       // the stage is free for the copies of the tile after next
       __syncwarp();
-      v1 = warp_sum(v1);
-      v2 = warp_sum(v2);
+      const double v1 = df_double(df_warp_sum(d1));
+      const double v2 = df_double(df_warp_sum(d2));
       const int lt = tile - S.tile0;
       if (lane == 0) {
         double* dst = S.part_b + 2 * (size_t)lt;
@@ -1068,6 +1105,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     const bool act = lane < 6 * NODES_PER_WARP && ln < inf.nn;
     const int i = 6 * node + rr;
     double part = 0.0, part_b = 0.0;
+    DF dpart = {0.f, 0.f};  // CG state: the warp's p^T q terms
     if (state == ST_PCG) {
       float* pnew = (float*)(inf.parity ? S.p0 : S.p1);
       const float beta = inf.beta;
@@ -1139,7 +1177,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         const float pi = fmaf(beta, pi_old, zi);
         pnew[i] = pi;
         ((float*)S.q)[i] = acc;
-        part = (double)pi * (double)acc;
+        dpart = df_prod(pi, acc);
       }
     } else if (state != ST_DONE) {  // ST_INIT or ST_RESID: r64 = b - K64 x in FP64
       if (act) {
@@ -1158,8 +1196,12 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
     if (skip) continue;
-    part = warp_sum(part);
-    part_b = warp_sum(part_b);
+    if (real_state == ST_PCG) {
+      part = df_double(df_warp_sum(dpart));
+    } else {
+      part = warp_sum(part);
+      part_b = warp_sum(part_b);
+    }
     if (lane == 0) {
       double* dst = S.part_a + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
       dst[0] = part;
