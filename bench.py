@@ -266,8 +266,11 @@ def run_serving(a):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = sso.kernel_launches()
+    info0 = srv.info()
     res, elapsed = run_stream(srv, [{"mesh": m, "t_arrive": 0.0} for m in meshes],
                               time_limit_s=1800.0)
+    info1 = srv.info()
+    phases = {k: info1[k] - info0[k] for k in info1}
     launches = sso.kernel_launches() - l0
     clk = clocks.stop()
     failed = [i for i, r in enumerate(res) if r["stats"]["status"] != 0]
@@ -328,7 +331,8 @@ def run_serving(a):
                       "latency_p50_ms": _pct(lat_sat, 50), "latency_p99_ms": _pct(lat_sat, 99),
                       "cg_iterations_mean": float(np.mean(iters)),
                       "cg_iterations_max": int(max(iters)), "failed": len(failed),
-                      "pcg_dof_per_s": float(np.dot(iters, dofs)) / elapsed},
+                      "pcg_dof_per_s": float(np.dot(iters, dofs)) / elapsed,
+                      "server_host_phases": phases},
         "poisson": poisson,
         "one_at_a_time_fp64": {"evals_per_s": alone, "requests": len(idx),
                                "mean_dof": float(np.mean([dofs[i] for i in idx])),

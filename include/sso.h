@@ -279,7 +279,8 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
                              int32_t max_systems, int32_t max_tiles, sso_server** out);
 void sso_server_destroy(sso_server* server);
 
-/* Queue a request; the mesh (host or device arrays) is copied.  A NULL or
+/* Queue a request; the mesh (host or device arrays) is copied, and worker
+ * threads of the server start building its scatter map at once.  A NULL or
  * incomplete mesh is rejected here (SSO_ERR_INVALID); a mesh whose contents
  * are invalid (node indices, non-finite values) is reported by the request's
  * result status, as is one that can never fit the budget (SSO_ERR_OOM). */
@@ -293,6 +294,21 @@ sso_status sso_server_submit(sso_server* server, const sso_mesh* mesh, double w,
  * on the host and each phase of the step is synchronised, so that an error
  * names the phase it came from. */
 sso_status sso_server_step(sso_server* server, int32_t* n_resident, int32_t* n_waiting);
+
+/* Tickets whose results became ready since the last call (in completion
+ * order), at most `capacity` of them; *n receives the count.  Results stay
+ * available to sso_server_poll until polled. */
+sso_status sso_server_completed(sso_server* server, uint64_t* tickets, int32_t capacity,
+                                int32_t* n);
+
+/* Host time spent in each phase of sso_server_step since creation (ms[8]):
+ * ms[0] admission (model build, set-up kernels enqueued), ms[1] system-table
+ * uploads, ms[2] waiting for the CG graph, ms[3] harvest (adjoint
+ * contraction, results to host, freeing the model); parts of ms[0]: ms[4]
+ * waiting for the worker threads' preparation, ms[5] arena allocation and
+ * upload, ms[6] set-up kernel launches; ms[7] reserved (0).  counts[2]:
+ * steps, CG graph launches.  Either pointer may be NULL. */
+sso_status sso_server_info(const sso_server* server, double* ms, int64_t* counts);
 
 /* Result of a finished request: SSO_ERR_NOT_READY while it is queued or
  * running; otherwise SSO_OK, the outputs are filled (any pointer may be NULL;

@@ -100,6 +100,9 @@ SIGNATURES = {
     "sso_server_submit": ([_vp, ctypes.POINTER(Mesh), _f64, ctypes.POINTER(ctypes.c_uint64)],
                           _i32),
     "sso_server_step": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
+    "sso_server_completed": ([_vp, ctypes.POINTER(ctypes.c_uint64), _i32, ctypes.POINTER(_i32)],
+                             _i32),
+    "sso_server_info": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(ctypes.c_int64)], _i32),
     "sso_server_poll": ([_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats),
                          ctypes.POINTER(_f64)], _i32),
     "sso_batch_kernel_times": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64),

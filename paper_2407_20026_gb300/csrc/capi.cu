@@ -17,11 +17,17 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <deque>
 #include <unordered_map>
 #include <string>
 #include <vector>
+#include <map>
+#include <memory>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 
 #include "sso_internal.cuh"
 
@@ -96,14 +102,16 @@ cudaError_t to_host(void* dst, const void* src, size_t bytes) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Carves typed arrays out of one allocation (256-byte aligned).
+// Carves 256-byte-aligned arrays out of one allocation; with a null base the
+// pointers it returns are the arrays' byte offsets.
 struct Carver {
-  char* base;
+  uintptr_t base;
   size_t off = 0;
-  explicit Carver(void* b) : base((char*)b) {}
+  explicit Carver(void* b) : base(reinterpret_cast<uintptr_t>(b)) {}
   template <class T>
   T* take(size_t n) {
     off = align_up(off, 256);
-    T* p = base ? (T*)(base + off) : nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
     off += n * sizeof(T);
     return p;
   }
@@ -133,6 +141,7 @@ struct sso_model {
   std::vector<int> h_row_ptr, h_col;
   void* arena = nullptr;
   size_t arena_bytes = 0;  // size of the arena (fixed at creation)
+  bool own_arena = true;   // false: the arena belongs to a server's pool
   // topology
   int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_brow, *d_diag, *d_cptr, *d_csrc,
       *d_nptr, *d_nsrc;
@@ -280,27 +289,54 @@ sso_status validate(const HostMesh& m) {
 // Element-block eb -> (row node, col node).
 void build_topology(const HostMesh& m, HostTopo& T) {
   const int n = m.n_nodes;
-  std::vector<std::vector<int>> adj(n);
-  for (int i = 0; i < n; ++i) adj[i].push_back(i);
+  // node adjacency (with the node itself) in flat arrays: count, prefix,
+  // fill, then sort and deduplicate each short row in place
+  std::vector<int> cnt(n + 1, 0);
+  for (int i = 0; i < n; ++i) cnt[i + 1] = 1;
   for (int e = 0; e < m.n_beams; ++e)
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) adj[m.beam_conn[2 * e + a]].push_back(m.beam_conn[2 * e + b]);
+    for (int a = 0; a < 2; ++a) cnt[m.beam_conn[2 * e + a] + 1] += 2;
   for (int e = 0; e < m.n_quads; ++e)
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) adj[m.quad_conn[4 * e + a]].push_back(m.quad_conn[4 * e + b]);
+    for (int a = 0; a < 4; ++a) cnt[m.quad_conn[4 * e + a] + 1] += 4;
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> flat(cnt[n]);
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int i = 0; i < n; ++i) flat[fill[i]++] = i;
+  for (int e = 0; e < m.n_beams; ++e)
+    for (int a = 0; a < 2; ++a) {
+      const int r = m.beam_conn[2 * e + a];
+      for (int b = 0; b < 2; ++b) flat[fill[r]++] = m.beam_conn[2 * e + b];
+    }
+  for (int e = 0; e < m.n_quads; ++e)
+    for (int a = 0; a < 4; ++a) {
+      const int r = m.quad_conn[4 * e + a];
+      for (int b = 0; b < 4; ++b) flat[fill[r]++] = m.quad_conn[4 * e + b];
+    }
   T.row_ptr.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    std::sort(adj[i].begin(), adj[i].end());
-    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
-    T.row_ptr[i + 1] = T.row_ptr[i] + (int)adj[i].size();
+    int* b = flat.data() + cnt[i];
+    const int len = cnt[i + 1] - cnt[i];
+    for (int k = 1; k < len; ++k) {  // insertion sort: rows are short
+      const int v = b[k];
+      int j = k - 1;
+      while (j >= 0 && b[j] > v) {
+        b[j + 1] = b[j];
+        --j;
+      }
+      b[j + 1] = v;
+    }
+    int u = 0;
+    for (int k = 0; k < len; ++k)
+      if (u == 0 || b[k] != b[u - 1]) b[u++] = b[k];
+    T.row_ptr[i + 1] = T.row_ptr[i] + u;
   }
   const int nb = T.row_ptr[n];
   T.col.resize(nb);
   T.brow.resize(nb);
   T.diag.resize(n);
   for (int i = 0; i < n; ++i) {
-    std::copy(adj[i].begin(), adj[i].end(), T.col.begin() + T.row_ptr[i]);
+    const int* b = flat.data() + cnt[i];
     for (int k = T.row_ptr[i]; k < T.row_ptr[i + 1]; ++k) {
+      T.col[k] = b[k - T.row_ptr[i]];
       T.brow[k] = i;
       if (T.col[k] == i) T.diag[i] = k;
     }
@@ -728,6 +764,164 @@ TileDesc make_tile(const sso_model* M, int s, int k) {
   return d;
 }
 
+// Host half of a model: the mesh, validated, and its scatter map, node
+// incidence and tile descriptors, plus the packed image of every array the
+// device arena starts with.  Built without CUDA calls, so any thread may run
+// it.
+struct ModelPrep {
+  HostMesh hm;
+  HostTopo T;
+  sso_model* M = nullptr;  // counts, host copies and arena offsets (base 0)
+  std::vector<TileDesc> tiles;  // sys = -1
+  std::vector<unsigned char> image;  // arena bytes [0, prefix)
+  size_t bytes = 0, prefix = 0;
+  std::string error;
+  ~ModelPrep() { delete M; }
+};
+
+// Copies a mesh (host or device arrays) into P.hm after the argument checks.
+sso_status mesh_to_prep(const sso_mesh* mesh, ModelPrep& P) {
+  if (!mesh) return fail(SSO_ERR_INVALID, "mesh is NULL");
+  if (mesh->n_nodes <= 0 || mesh->n_beams < 0 || mesh->n_quads < 0)
+    return fail(SSO_ERR_INVALID, "need n_nodes > 0, n_beams >= 0, n_quads >= 0");
+  if (mesh->n_beams + mesh->n_quads == 0) return fail(SSO_ERR_INVALID, "no elements");
+  if (!mesh->xyz || !mesh->fixed || !mesh->nodal_load)
+    return fail(SSO_ERR_INVALID, "xyz, fixed and nodal_load are required");
+  if (mesh->n_beams > 0 && (!mesh->beam_conn || !mesh->beam_props))
+    return fail(SSO_ERR_INVALID, "beam arrays missing");
+  if (mesh->n_quads > 0 && (!mesh->quad_conn || !mesh->quad_props))
+    return fail(SSO_ERR_INVALID, "quad arrays missing");
+  const long long eb = 4LL * mesh->n_beams + 16LL * mesh->n_quads;
+  if (eb >= (1LL << 31) || 6LL * mesh->n_nodes >= (1LL << 31))
+    return fail(SSO_ERR_INVALID, "mesh too large for 32-bit block indices");
+  HostMesh& hm = P.hm;
+  hm.n_nodes = mesh->n_nodes;
+  hm.n_beams = mesh->n_beams;
+  hm.n_quads = mesh->n_quads;
+  hm.pressure = mesh->pressure;
+  hm.gamma = mesh->gamma;
+  hm.xyz.resize(3 * (size_t)hm.n_nodes);
+  hm.nodal_load.resize(6 * (size_t)hm.n_nodes);
+  hm.fixed.resize(6 * (size_t)hm.n_nodes);
+  hm.beam_conn.resize(2 * (size_t)hm.n_beams);
+  hm.beam_props.resize(6 * (size_t)hm.n_beams);
+  hm.quad_conn.resize(4 * (size_t)hm.n_quads);
+  hm.quad_props.resize(5 * (size_t)hm.n_quads);
+  CK(to_host(hm.xyz.data(), mesh->xyz, hm.xyz.size() * sizeof(double)));
+  CK(to_host(hm.nodal_load.data(), mesh->nodal_load, hm.nodal_load.size() * sizeof(double)));
+  CK(to_host(hm.fixed.data(), mesh->fixed, hm.fixed.size()));
+  CK(to_host(hm.beam_conn.data(), mesh->beam_conn, hm.beam_conn.size() * sizeof(int)));
+  CK(to_host(hm.beam_props.data(), mesh->beam_props, hm.beam_props.size() * sizeof(double)));
+  CK(to_host(hm.quad_conn.data(), mesh->quad_conn, hm.quad_conn.size() * sizeof(int)));
+  CK(to_host(hm.quad_props.data(), mesh->quad_props, hm.quad_props.size() * sizeof(double)));
+  for (auto& f : hm.fixed) f = f ? 1 : 0;
+  return SSO_OK;
+}
+
+// Validation, scatter map, tile descriptors and the arena image.  On failure
+// the message is in P.error (this may run off the calling thread).
+sso_status prepare_model(ModelPrep& P) {
+  const HostMesh& hm = P.hm;
+  sso_status st = validate(hm);
+  if (st != SSO_OK) {
+    P.error = g_last_error;
+    return st;
+  }
+  build_topology(hm, P.T);
+  if (debug_sync() && !topology_consistent(hm, P.T)) {
+    P.error = "scatter map inconsistent (internal error)";
+    return SSO_ERR_INVALID;
+  }
+  const HostTopo& T = P.T;
+  sso_model* M = new sso_model();
+  P.M = M;
+  M->n_nodes = hm.n_nodes;
+  M->n_beams = hm.n_beams;
+  M->n_quads = hm.n_quads;
+  M->n_blocks = (int)T.col.size();
+  M->n_eb = (int)T.csrc.size();
+  M->n_slots = (int)T.nsrc.size();
+  M->n_tiles = (hm.n_nodes + TILE - 1) / TILE;
+  M->pressure = hm.pressure;
+  M->gamma = hm.gamma;
+  M->h_row_ptr = T.row_ptr;
+  M->h_col = T.col;
+  sso_default_options(&M->last_opts);
+  P.tiles.reserve(M->n_tiles);
+  for (int t = 0; t < M->n_tiles; ++t) P.tiles.push_back(make_tile(M, -1, t));
+  // arena offsets (base 0) and the image of the arrays that start it
+  P.bytes = layout_model(M, nullptr);
+  P.prefix = (size_t)reinterpret_cast<uintptr_t>(M->d_ke);
+  P.image.assign(P.prefix, 0);
+  auto put = [&](const void* dev_off, const void* src, size_t b) {
+    if (b) std::memcpy(P.image.data() + reinterpret_cast<uintptr_t>(dev_off), src, b);
+  };
+  put(M->d_beam_conn, hm.beam_conn.data(), hm.beam_conn.size() * 4);
+  put(M->d_quad_conn, hm.quad_conn.data(), hm.quad_conn.size() * 4);
+  put(M->d_row_ptr, T.row_ptr.data(), T.row_ptr.size() * 4);
+  put(M->d_col, T.col.data(), T.col.size() * 4);
+  put(M->d_brow, T.brow.data(), T.brow.size() * 4);
+  put(M->d_diag, T.diag.data(), T.diag.size() * 4);
+  put(M->d_cptr, T.cptr.data(), T.cptr.size() * 4);
+  put(M->d_csrc, T.csrc.data(), T.csrc.size() * 4);
+  put(M->d_nptr, T.nptr.data(), T.nptr.size() * 4);
+  put(M->d_nsrc, T.nsrc.data(), T.nsrc.size() * 4);
+  put(M->d_fixed, hm.fixed.data(), hm.fixed.size());
+  put(M->d_xyz, hm.xyz.data(), hm.xyz.size() * 8);
+  put(M->d_beam_props, hm.beam_props.data(), hm.beam_props.size() * 8);
+  put(M->d_quad_props, hm.quad_props.data(), hm.quad_props.size() * 8);
+  put(M->d_nodal_load, hm.nodal_load.data(), hm.nodal_load.size() * 8);
+  return SSO_OK;
+}
+
+// Device half: arena (arena != NULL: given, e.g. from a server pool, and
+// not freed with the model), one upload of the image (from `image`, a pinned
+// copy of P.image, when given), the rest zeroed.  own_stream:
+// the model gets its own stream and events (ordered after user_stream) and the
+// call returns with the upload done; otherwise everything is ordered on s
+// and the model has no stream of its own (server models).  Takes P.M.
+sso_status create_model_device(ModelPrep& P, cudaStream_t user_stream, bool own_stream,
+                               cudaStream_t s, sso_model** out, void* arena = nullptr,
+                               const void* image = nullptr) {
+  sso_model* M = P.M;
+  P.M = nullptr;
+  auto cleanup = [&](sso_status st) {
+    sso_model_destroy(M);
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&M->device);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGetDevice"));
+  M->user_stream = user_stream;
+  if (own_stream) {
+    e = cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "stream/event creation"));
+    s = M->stream;
+  }
+  M->arena_bytes = P.bytes;
+  if (arena) {
+    M->arena = arena;
+    M->own_arena = false;
+  } else {
+    e = cudaMalloc(&M->arena, P.bytes);
+    if (e != cudaSuccess) {
+      M->arena = nullptr;
+      return cleanup(cuda_fail(e, "cudaMalloc(model arena)"));
+    }
+  }
+  layout_model(M, M->arena);
+  e = cudaMemcpyAsync(M->arena, image ? image : P.image.data(), P.prefix,
+                      cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(static_cast<unsigned char*>(M->arena) + P.prefix, 0, P.bytes - P.prefix,
+                        s);
+  if (e == cudaSuccess && own_stream) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "uploading the model"));
+  *out = M;
+  return SSO_OK;
+}
+
 sso_status ensure_self_batch(sso_model* M) {
   if (M->self_batch) return SSO_OK;
   sso_model* ms[1] = {M};
@@ -811,111 +1005,18 @@ sso_status sso_bsr_spmv(int32_t n_nodes, const int32_t* d_row_ptr, const int32_t
 sso_status sso_model_create(const sso_mesh* mesh, void* stream, sso_model** out) {
   if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!mesh) return fail(SSO_ERR_INVALID, "mesh is NULL");
-  if (mesh->n_nodes <= 0 || mesh->n_beams < 0 || mesh->n_quads < 0)
-    return fail(SSO_ERR_INVALID, "need n_nodes > 0, n_beams >= 0, n_quads >= 0");
-  if (mesh->n_beams + mesh->n_quads == 0) return fail(SSO_ERR_INVALID, "no elements");
-  if (!mesh->xyz || !mesh->fixed || !mesh->nodal_load)
-    return fail(SSO_ERR_INVALID, "xyz, fixed and nodal_load are required");
-  if (mesh->n_beams > 0 && (!mesh->beam_conn || !mesh->beam_props))
-    return fail(SSO_ERR_INVALID, "beam arrays missing");
-  if (mesh->n_quads > 0 && (!mesh->quad_conn || !mesh->quad_props))
-    return fail(SSO_ERR_INVALID, "quad arrays missing");
-  const long long eb = 4LL * mesh->n_beams + 16LL * mesh->n_quads;
-  if (eb >= (1LL << 31) || 6LL * mesh->n_nodes >= (1LL << 31))
-    return fail(SSO_ERR_INVALID, "mesh too large for 32-bit block indices");
-
-  HostMesh hm;
-  hm.n_nodes = mesh->n_nodes;
-  hm.n_beams = mesh->n_beams;
-  hm.n_quads = mesh->n_quads;
-  hm.pressure = mesh->pressure;
-  hm.gamma = mesh->gamma;
-  hm.xyz.resize(3 * (size_t)hm.n_nodes);
-  hm.nodal_load.resize(6 * (size_t)hm.n_nodes);
-  hm.fixed.resize(6 * (size_t)hm.n_nodes);
-  hm.beam_conn.resize(2 * (size_t)hm.n_beams);
-  hm.beam_props.resize(6 * (size_t)hm.n_beams);
-  hm.quad_conn.resize(4 * (size_t)hm.n_quads);
-  hm.quad_props.resize(5 * (size_t)hm.n_quads);
-  CK(to_host(hm.xyz.data(), mesh->xyz, hm.xyz.size() * sizeof(double)));
-  CK(to_host(hm.nodal_load.data(), mesh->nodal_load, hm.nodal_load.size() * sizeof(double)));
-  CK(to_host(hm.fixed.data(), mesh->fixed, hm.fixed.size()));
-  CK(to_host(hm.beam_conn.data(), mesh->beam_conn, hm.beam_conn.size() * sizeof(int)));
-  CK(to_host(hm.beam_props.data(), mesh->beam_props, hm.beam_props.size() * sizeof(double)));
-  CK(to_host(hm.quad_conn.data(), mesh->quad_conn, hm.quad_conn.size() * sizeof(int)));
-  CK(to_host(hm.quad_props.data(), mesh->quad_props, hm.quad_props.size() * sizeof(double)));
-  for (auto& f : hm.fixed) f = f ? 1 : 0;
-  sso_status st = validate(hm);
+  ModelPrep P;
+  sso_status st = mesh_to_prep(mesh, P);
   if (st != SSO_OK) return st;
-
-  HostTopo T;
-  build_topology(hm, T);
-  if (debug_sync() && !topology_consistent(hm, T))
-    return fail(SSO_ERR_INVALID, "scatter map inconsistent (internal error)");
-
-  sso_model* M = new sso_model();
-  CK(cudaGetDevice(&M->device));
-  M->user_stream = (cudaStream_t)stream;
-  M->n_nodes = hm.n_nodes;
-  M->n_beams = hm.n_beams;
-  M->n_quads = hm.n_quads;
-  M->n_blocks = (int)T.col.size();
-  M->n_eb = (int)T.csrc.size();
-  M->n_slots = (int)T.nsrc.size();
-  M->n_tiles = (hm.n_nodes + TILE - 1) / TILE;
-  M->pressure = hm.pressure;
-  M->gamma = hm.gamma;
-  M->h_row_ptr = T.row_ptr;
-  M->h_col = T.col;
-  sso_default_options(&M->last_opts);
-  auto cleanup = [&](sso_status s) {
-    sso_model_destroy(M);
-    return s;
-  };
-  cudaError_t e = cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_in, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&M->ev_out, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "stream/event creation"));
-  const size_t bytes = layout_model(M, nullptr);
-  M->arena_bytes = bytes;
-  e = cudaMalloc(&M->arena, bytes);
-  if (e != cudaSuccess) {
-    M->arena = nullptr;
-    return cleanup(cuda_fail(e, "cudaMalloc(model arena)"));
-  }
-  layout_model(M, M->arena);
-  cudaStream_t s = M->stream;
-  auto up = [&](void* dst, const void* src, size_t b) {
-    return b ? cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s) : cudaSuccess;
-  };
-  e = cudaMemsetAsync(M->arena, 0, bytes, s);
-  if (e == cudaSuccess) e = up(M->d_beam_conn, hm.beam_conn.data(), hm.beam_conn.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_quad_conn, hm.quad_conn.data(), hm.quad_conn.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_row_ptr, T.row_ptr.data(), T.row_ptr.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_col, T.col.data(), T.col.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_brow, T.brow.data(), T.brow.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_diag, T.diag.data(), T.diag.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_cptr, T.cptr.data(), T.cptr.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_csrc, T.csrc.data(), T.csrc.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_nptr, T.nptr.data(), T.nptr.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_nsrc, T.nsrc.data(), T.nsrc.size() * 4);
-  if (e == cudaSuccess) e = up(M->d_fixed, hm.fixed.data(), hm.fixed.size());
-  if (e == cudaSuccess) e = up(M->d_xyz, hm.xyz.data(), hm.xyz.size() * 8);
-  if (e == cudaSuccess) e = up(M->d_beam_props, hm.beam_props.data(), hm.beam_props.size() * 8);
-  if (e == cudaSuccess) e = up(M->d_quad_props, hm.quad_props.data(), hm.quad_props.size() * 8);
-  if (e == cudaSuccess) e = up(M->d_nodal_load, hm.nodal_load.data(), hm.nodal_load.size() * 8);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "uploading the model"));
-  *out = M;
-  return SSO_OK;
+  if ((st = prepare_model(P)) != SSO_OK) return fail(st, P.error);
+  return create_model_device(P, (cudaStream_t)stream, true, nullptr, out);
 }
 
 void sso_model_destroy(sso_model* M) {
   if (!M) return;
   if (M->self_batch) sso_batch_destroy(M->self_batch);
   if (M->stream) cudaStreamSynchronize(M->stream);
-  if (M->arena) cudaFree(M->arena);
+  if (M->arena && M->own_arena) cudaFree(M->arena);
   if (M->ev_in) cudaEventDestroy(M->ev_in);
   if (M->ev_out) cudaEventDestroy(M->ev_out);
   if (M->stream) cudaStreamDestroy(M->stream);
@@ -1322,9 +1423,116 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
 
 namespace {
 
+// A server's device memory: one allocation of its HBM budget, carved into
+// model arenas first-fit, with freed ranges merged with their neighbours.
+struct DevPool {
+  unsigned char* base = nullptr;
+  size_t size = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  void* alloc(size_t n) {
+    n = align_up(n, 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      const size_t off = it->first, rem = it->second - n;
+      free_.erase(it);
+      if (rem) free_[off + n] = rem;
+      return base + off;
+    }
+    return nullptr;
+  }
+  void release(void* p, size_t n) {
+    size_t off = (size_t)(static_cast<unsigned char*>(p) - base);
+    n = align_up(n, 256);
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+};
+
+// Pinned staging for model uploads: images are copied into a ring of pinned
+// host memory and uploaded from there asynchronously; a region is reused
+// once the event recorded after its upload has completed.
+struct PinnedRing {
+  unsigned char* base = nullptr;
+  size_t size = 0, head = 0;
+  struct Use {
+    size_t begin, end;
+    cudaEvent_t ev;
+  };
+  std::deque<Use> busy;
+  std::vector<cudaEvent_t> spare;
+  // A region of n bytes (16-byte aligned start), or nullptr if n exceeds the
+  // ring.  Regions are handed out in order, so the ones in use span
+  // [oldest begin, head) circularly; the oldest are waited for until n fits.
+  unsigned char* take(size_t n, cudaError_t& err) {
+    err = cudaSuccess;
+    if (n > size) return nullptr;
+    size_t a = 0;
+    for (;;) {
+      if (busy.empty()) {
+        a = 0;
+        break;
+      }
+      const size_t tail = busy.front().begin, h = align_up(head, 16);
+      if (h > tail) {  // in use: [tail, h)
+        if (h + n <= size) {
+          a = h;
+          break;
+        }
+        if (n <= tail) {
+          a = 0;
+          break;
+        }
+      } else if (h + n <= tail) {  // in use: [tail, size) and [0, h)
+        a = h;
+        break;
+      }
+      err = cudaEventSynchronize(busy.front().ev);
+      if (err != cudaSuccess) return nullptr;
+      spare.push_back(busy.front().ev);
+      busy.pop_front();
+    }
+    head = a + n;
+    return base + a;
+  }
+  // Marks [p, p + n) busy until stream s passes this point.
+  cudaError_t mark(unsigned char* p, size_t n, cudaStream_t s) {
+    cudaEvent_t ev;
+    if (!spare.empty()) {
+      ev = spare.back();
+      spare.pop_back();
+    } else {
+      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    busy.push_back({(size_t)(p - base), (size_t)(p - base) + n, ev});
+    return cudaEventRecord(ev, s);
+  }
+  void release_all() {
+    for (auto& u : busy) cudaEventDestroy(u.ev);
+    for (auto ev : spare) cudaEventDestroy(ev);
+    busy.clear();
+    spare.clear();
+    if (base) cudaFreeHost(base);
+    base = nullptr;
+  }
+};
+
 struct ServerReq {
   uint64_t ticket = 0;
-  HostMesh mesh;
+  std::unique_ptr<ModelPrep> prep;  // host half of the model, built by a worker thread
+  bool prep_done = false;           // guarded by the server's mutex
+  sso_status prep_status = SSO_OK;
   double w = 1.0;
   double t_submit = 0.0, t_done = 0.0;  // ms since the server was created
   int slot = -1;
@@ -1336,10 +1544,6 @@ struct ServerReq {
   std::vector<double> u, dz, dt;
   double C = 0.0;
 };
-
-// Device bytes a model holds.  (Never layout_model on a live model: with a
-// null base it re-carves every device pointer of the model from address 0.)
-size_t model_bytes(const sso_model* M) { return M->arena_bytes; }
 
 // A batch with room for max_sys systems and max_tiles tiles and no models,
 // running on `stream`.
@@ -1396,6 +1600,8 @@ struct sso_server {
   int max_sys = 0, max_tiles = 0;
   cudaStream_t cg_stream = nullptr, setup_stream = nullptr;
   sso_batch* B = nullptr;
+  DevPool pool;                // model arenas
+  PinnedRing ring;             // upload staging
   SysScalars* h_up = nullptr;  // pinned upload staging, one per slot
   std::deque<ServerReq*> queue;
   std::unordered_map<uint64_t, ServerReq*> reqs;
@@ -1406,57 +1612,50 @@ struct sso_server {
   uint64_t next_ticket = 1;
   std::chrono::steady_clock::time_point t0;
   bool dirty = false;
+  // host time per phase of sso_server_step (ms): admission (model build and
+  // set-up enqueue), table upload, wait for the CG graph, harvest
+  double ms_admit = 0.0, ms_upload = 0.0, ms_wait = 0.0, ms_harvest = 0.0;
+  // parts of the admission time: waiting for a worker's preparation, arena
+  // allocation and upload, set-up kernel launches
+  double ms_admit_prep = 0.0, ms_admit_device = 0.0, ms_admit_setup = 0.0;
+  long long steps = 0, graph_launches = 0;
+  std::vector<uint64_t> completed;  // tickets finished since the last sso_server_completed
+  // worker threads preparing submitted requests (scatter map, tiles, arena image)
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ServerReq*> prep_queue;
+  bool stop = false;
 };
 
 namespace {
+constexpr int kIdleAdmit = 16;  // requests admitted per step while no CG graph runs
+constexpr size_t kRingBytes = 64u << 20;  // pinned upload staging of a server
 
-// Host copy of a mesh given by host or device pointers.
-sso_status mesh_to_host(const sso_mesh* mesh, HostMesh& hm) {
-  if (!mesh) return fail(SSO_ERR_INVALID, "mesh is NULL");
-  if (mesh->n_nodes <= 0 || mesh->n_beams < 0 || mesh->n_quads < 0 ||
-      mesh->n_beams + mesh->n_quads == 0 || !mesh->xyz || !mesh->fixed || !mesh->nodal_load ||
-      (mesh->n_beams > 0 && (!mesh->beam_conn || !mesh->beam_props)) ||
-      (mesh->n_quads > 0 && (!mesh->quad_conn || !mesh->quad_props)))
-    return fail(SSO_ERR_INVALID, "incomplete mesh");
-  hm.n_nodes = mesh->n_nodes;
-  hm.n_beams = mesh->n_beams;
-  hm.n_quads = mesh->n_quads;
-  hm.pressure = mesh->pressure;
-  hm.gamma = mesh->gamma;
-  hm.xyz.resize(3 * (size_t)hm.n_nodes);
-  hm.nodal_load.resize(6 * (size_t)hm.n_nodes);
-  hm.fixed.resize(6 * (size_t)hm.n_nodes);
-  hm.beam_conn.resize(2 * (size_t)hm.n_beams);
-  hm.beam_props.resize(6 * (size_t)hm.n_beams);
-  hm.quad_conn.resize(4 * (size_t)hm.n_quads);
-  hm.quad_props.resize(5 * (size_t)hm.n_quads);
-  CK(to_host(hm.xyz.data(), mesh->xyz, hm.xyz.size() * sizeof(double)));
-  CK(to_host(hm.nodal_load.data(), mesh->nodal_load, hm.nodal_load.size() * sizeof(double)));
-  CK(to_host(hm.fixed.data(), mesh->fixed, hm.fixed.size()));
-  CK(to_host(hm.beam_conn.data(), mesh->beam_conn, hm.beam_conn.size() * sizeof(int)));
-  CK(to_host(hm.beam_props.data(), mesh->beam_props, hm.beam_props.size() * sizeof(double)));
-  CK(to_host(hm.quad_conn.data(), mesh->quad_conn, hm.quad_conn.size() * sizeof(int)));
-  CK(to_host(hm.quad_props.data(), mesh->quad_props, hm.quad_props.size() * sizeof(double)));
-  return SSO_OK;
+void prep_worker(sso_server* S) {
+  for (;;) {
+    ServerReq* R;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [S] { return S->stop || !S->prep_queue.empty(); });
+      if (S->stop) return;
+      R = S->prep_queue.front();
+      S->prep_queue.pop_front();
+    }
+    const sso_status st = prepare_model(*R->prep);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      R->prep_status = st;
+      R->prep_done = true;
+    }
+    S->cv_done.notify_all();
+  }
 }
+}  // namespace
 
-sso_mesh mesh_view(const HostMesh& hm) {
-  sso_mesh m;
-  m.n_nodes = hm.n_nodes;
-  m.xyz = hm.xyz.data();
-  m.n_beams = hm.n_beams;
-  m.beam_conn = hm.beam_conn.data();
-  m.beam_props = hm.beam_props.data();
-  m.n_quads = hm.n_quads;
-  m.quad_conn = hm.quad_conn.data();
-  m.quad_props = hm.quad_props.data();
-  m.fixed = hm.fixed.data();
-  m.nodal_load = hm.nodal_load.data();
-  m.pressure = hm.pressure;
-  m.gamma = hm.gamma;
-  return m;
-}
+namespace {
 
+// With SSO_DEBUG_SYNC set: synchronise s and name the phase of any CUDA error.
 sso_status debug_check(cudaStream_t s, const char* phase) {
   if (!debug_sync()) return SSO_OK;
   cudaError_t e = cudaStreamSynchronize(s);
@@ -1559,12 +1758,30 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
   S->slot_req.assign(max_systems, nullptr);
   S->slot_tiles.assign(max_systems, {});
   S->t0 = std::chrono::steady_clock::now();
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int n_workers = (int)std::min(8u, std::max(1u, hw));
+  for (int k = 0; k < n_workers; ++k) S->workers.emplace_back(prep_worker, S);
   cudaError_t e = cudaStreamCreateWithFlags(&S->cg_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&S->h_up, sizeof(SysScalars) * max_systems);
   if (e != cudaSuccess) {
     sso_server_destroy(S);
     return cuda_fail(e, "server streams");
+  }
+  e = cudaMalloc(&S->pool.base, hbm_budget_bytes);
+  if (e != cudaSuccess) {
+    S->pool.base = nullptr;
+    sso_server_destroy(S);
+    return cuda_fail(e, "cudaMalloc(server HBM budget)");
+  }
+  S->pool.size = hbm_budget_bytes;
+  S->pool.free_[0] = hbm_budget_bytes;
+  S->ring.size = kRingBytes;
+  e = cudaMallocHost(&S->ring.base, kRingBytes);
+  if (e != cudaSuccess) {
+    S->ring.base = nullptr;
+    sso_server_destroy(S);
+    return cuda_fail(e, "cudaMallocHost(upload staging)");
   }
   st = batch_with_capacity(S->cg_stream, max_systems, max_tiles, &S->B);
   if (st != SSO_OK) {
@@ -1577,6 +1794,12 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
 
 void sso_server_destroy(sso_server* S) {
   if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (std::thread& t : S->workers) t.join();
   if (S->cg_stream) cudaStreamSynchronize(S->cg_stream);
   if (S->setup_stream) cudaStreamSynchronize(S->setup_stream);
   for (auto& kv : S->reqs) {
@@ -1586,6 +1809,8 @@ void sso_server_destroy(sso_server* S) {
     delete R;
   }
   if (S->B) sso_batch_destroy(S->B);
+  if (S->pool.base) cudaFree(S->pool.base);
+  S->ring.release_all();
   if (S->h_up) cudaFreeHost(S->h_up);
   if (S->cg_stream) cudaStreamDestroy(S->cg_stream);
   if (S->setup_stream) cudaStreamDestroy(S->setup_stream);
@@ -1595,7 +1820,8 @@ void sso_server_destroy(sso_server* S) {
 sso_status sso_server_submit(sso_server* S, const sso_mesh* mesh, double w, uint64_t* ticket) {
   if (!S || !ticket) return fail(SSO_ERR_INVALID, "NULL argument");
   ServerReq* R = new ServerReq();
-  sso_status st = mesh_to_host(mesh, R->mesh);
+  R->prep.reset(new ModelPrep());
+  sso_status st = mesh_to_prep(mesh, *R->prep);
   if (st != SSO_OK) {
     delete R;
     return st;
@@ -1605,6 +1831,11 @@ sso_status sso_server_submit(sso_server* S, const sso_mesh* mesh, double w, uint
   R->t_submit = ms_since(S->t0);
   S->reqs[R->ticket] = R;
   S->queue.push_back(R);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->prep_queue.push_back(R);
+  }
+  S->cv_work.notify_one();
   *ticket = R->ticket;
   return SSO_OK;
 }
@@ -1618,8 +1849,17 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
   sso_status st;
   // 1. one graph launch of CG iterations over the running systems
   bool launched = false;
+  ++S->steps;
+  auto tick = std::chrono::steady_clock::now();
+  auto lap = [&tick](double& acc) {
+    const auto now = std::chrono::steady_clock::now();
+    acc += std::chrono::duration<double, std::milli>(now - tick).count();
+    tick = now;
+  };
   if (!S->running.empty()) {
     if (S->dirty && (st = server_upload_tables(S, S->slot_tiles)) != SSO_OK) return st;
+    lap(S->ms_upload);
+    ++S->graph_launches;
     B->h_flag[0] = (int)S->running.size();
     B->h_flag[1] = 0;
     CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
@@ -1635,9 +1875,14 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
     CK(cudaEventRecord(B->ev, B->stream));
     launched = true;
   }
+  tick = std::chrono::steady_clock::now();
   // 2. admission while the GPU iterates: build models, set them up on the
-  //    set-up stream (their kernels overlap the CG graph)
+  //    set-up stream (their kernels overlap the CG graph).  With a graph in
+  //    flight the host admits until it completes; with the GPU idle it admits
+  //    a few requests and returns, so that CG starts on them at once.
+  int admitted = 0;
   while (!S->queue.empty()) {
+    if (launched ? cudaEventQuery(B->ev) != cudaErrorNotReady : admitted >= kIdleAdmit) break;
     int slot = -1;
     for (int s2 = 0; s2 < S->max_sys; ++s2)
       if (!S->slot_req[s2]) {
@@ -1646,26 +1891,67 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
       }
     if (slot < 0) break;
     ServerReq* R = S->queue.front();
-    sso_mesh m = mesh_view(R->mesh);
-    sso_model* M = nullptr;
-    st = sso_model_create(&m, nullptr, &M);
-    if (st == SSO_ERR_CUDA) return st;  // the device, not the request, failed
-    if (st != SSO_OK) {  // invalid request (or one that cannot be allocated)
+    auto ta = std::chrono::steady_clock::now();
+    auto lap2 = [&ta](double& acc) {
+      const auto now = std::chrono::steady_clock::now();
+      acc += std::chrono::duration<double, std::milli>(now - ta).count();
+      ta = now;
+    };
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_done.wait(lk, [R] { return R->prep_done; });
+    }
+    lap2(S->ms_admit_prep);
+    if (R->prep_status != SSO_OK) {  // invalid request: its result is the error
       S->queue.pop_front();
-      R->stats.status = st;
+      R->stats.status = R->prep_status;
       R->phase = 3;
+      S->completed.push_back(R->ticket);
       R->t_done = ms_since(S->t0);
+      R->prep.reset();
       continue;
     }
-    const size_t bytes = model_bytes(M);
+    const size_t bytes = R->prep->bytes;
+    const int n_tiles = (int)R->prep->tiles.size();
     const bool idle = S->running.empty() && S->pending.empty();
-    if (S->tiles_used + M->n_tiles > S->max_tiles || S->used + bytes > S->budget) {
-      sso_model_destroy(M);
+    if (S->tiles_used + n_tiles > S->max_tiles || S->used + bytes > S->budget) {
       if (!idle) break;  // wait for finished systems to free room
       S->queue.pop_front();
       R->stats.status = SSO_ERR_OOM;  // can never fit
       R->phase = 3;
+      S->completed.push_back(R->ticket);
       R->t_done = ms_since(S->t0);
+      R->prep.reset();
+      continue;
+    }
+    void* arena = S->pool.alloc(bytes);
+    if (!arena) {  // fragmented: wait for finished systems, unless none is left
+      if (!idle) break;
+      S->queue.pop_front();
+      R->stats.status = SSO_ERR_OOM;
+      R->phase = 3;
+      S->completed.push_back(R->ticket);
+      R->t_done = ms_since(S->t0);
+      R->prep.reset();
+      continue;
+    }
+    cudaError_t re;
+    unsigned char* staged = S->ring.take(R->prep->prefix, re);
+    if (re != cudaSuccess) return cuda_fail(re, "upload staging");
+    if (staged) std::memcpy(staged, R->prep->image.data(), R->prep->prefix);
+    sso_model* M = nullptr;
+    st = create_model_device(*R->prep, nullptr, false, S->setup_stream, &M, arena, staged);
+    if (staged) CK(S->ring.mark(staged, R->prep->prefix, S->setup_stream));
+    lap2(S->ms_admit_device);
+    if (st != SSO_OK) S->pool.release(arena, bytes);
+    if (st == SSO_ERR_CUDA) return st;  // the device, not the request, failed
+    if (st != SSO_OK) {  // could not be set up
+      S->queue.pop_front();
+      R->stats.status = st;
+      R->phase = 3;
+      S->completed.push_back(R->ticket);
+      R->t_done = ms_since(S->t0);
+      R->prep.reset();
       continue;
     }
     S->queue.pop_front();
@@ -1675,21 +1961,26 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
     if ((st = debug_check(S->setup_stream, "server: set-up kernels")) != SSO_OK) return st;
     CK(cudaEventCreateWithFlags(&R->ev_setup, cudaEventDisableTiming));
     CK(cudaEventRecord(R->ev_setup, S->setup_stream));
+    lap2(S->ms_admit_setup);
     R->M = M;
     R->bytes = bytes;
     R->slot = slot;
     R->phase = 1;
     S->slot_req[slot] = R;
-    S->slot_tiles[slot].clear();
-    for (int t = 0; t < M->n_tiles; ++t) S->slot_tiles[slot].push_back(make_tile(M, slot, t));
+    S->slot_tiles[slot].swap(R->prep->tiles);
+    for (TileDesc& td : S->slot_tiles[slot]) td.sys = slot;
+    R->prep.reset();
     fill_sysdesc(B->h_sys[slot], M, S->opts.precond);
     S->tiles_used += M->n_tiles;
     S->used += bytes;
     S->pending.push_back(slot);
+    ++admitted;
   }
+  lap(S->ms_admit);
   // 3. wait for the launch; harvest the systems that finished
   if (launched) {
     CK(cudaEventSynchronize(B->ev));
+    lap(S->ms_wait);
     if (B->h_flag[3] != 0)
       return fail(SSO_ERR_CUDA, "CG kernel gave up waiting for a bulk copy (device fault?)");
     std::vector<int> done;
@@ -1736,14 +2027,18 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
       R->stats.ms = now - R->t_submit;
       R->t_done = now;
       R->phase = 3;
+      S->completed.push_back(R->ticket);
       S->used -= R->bytes;
       S->tiles_used -= R->M->n_tiles;
+      void* arena = R->M->arena;
       sso_model_destroy(R->M);
+      S->pool.release(arena, R->bytes);
       R->M = nullptr;
       S->slot_req[slot] = nullptr;
       S->running.erase(std::find(S->running.begin(), S->running.end(), slot));
       S->dirty = true;
     }
+    lap(S->ms_harvest);
   }
   // 4. systems whose set-up has finished join the CG
   for (size_t i = 0; i < S->pending.size();) {
@@ -1765,6 +2060,35 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
   }
   if (n_running) *n_running = (int)(S->running.size() + S->pending.size());
   if (n_waiting) *n_waiting = (int)S->queue.size();
+  return SSO_OK;
+}
+
+sso_status sso_server_completed(sso_server* S, uint64_t* tickets, int32_t capacity,
+                                int32_t* n) {
+  if (!S || !n || (capacity > 0 && !tickets)) return fail(SSO_ERR_INVALID, "NULL argument");
+  const int k = std::min<int>(std::max(capacity, 0), (int)S->completed.size());
+  std::copy(S->completed.begin(), S->completed.begin() + k, tickets);
+  S->completed.erase(S->completed.begin(), S->completed.begin() + k);
+  *n = k;
+  return SSO_OK;
+}
+
+sso_status sso_server_info(const sso_server* S, double* ms, int64_t* counts) {
+  if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
+  if (ms) {
+    ms[0] = S->ms_admit;
+    ms[1] = S->ms_upload;
+    ms[2] = S->ms_wait;
+    ms[3] = S->ms_harvest;
+    ms[4] = S->ms_admit_prep;
+    ms[5] = S->ms_admit_device;
+    ms[6] = S->ms_admit_setup;
+    ms[7] = 0.0;
+  }
+  if (counts) {
+    counts[0] = S->steps;
+    counts[1] = S->graph_launches;
+  }
   return SSO_OK;
 }
 

@@ -52,6 +52,26 @@ class Server:
         _lib.check(_lib.load().sso_server_step(self._h, ctypes.byref(r), ctypes.byref(q)))
         return r.value, q.value
 
+    def completed(self, capacity=4096):
+        """Tickets finished since the last call (their results await poll)."""
+        buf = (ctypes.c_uint64 * capacity)()
+        n = ctypes.c_int32()
+        out = []
+        while True:
+            _lib.check(_lib.load().sso_server_completed(self._h, buf, capacity, ctypes.byref(n)))
+            out.extend(buf[:n.value])
+            if n.value < capacity:
+                return out
+
+    def info(self):
+        """Host ms per phase of the steps so far and step / graph-launch counts."""
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_int64 * 2)()
+        _lib.check(_lib.load().sso_server_info(self._h, ms, n))
+        return {"admit_ms": ms[0], "upload_ms": ms[1], "wait_ms": ms[2], "harvest_ms": ms[3],
+                "admit_prep_ms": ms[4], "admit_device_ms": ms[5], "admit_setup_ms": ms[6],
+                "steps": n[0], "graph_launches": n[1]}
+
     def poll(self, ticket):
         """None while the request is not finished, else a dict of results."""
         n, nq = self._shapes[ticket]
@@ -94,7 +114,9 @@ def run_stream(server, requests, time_limit_s=600.0):
             outstanding.add(tk)
             nxt += 1
         resident, waiting = server.step()
-        for tk in list(outstanding):
+        for tk in server.completed():
+            if tk not in outstanding:
+                continue
             r = server.poll(tk)
             if r is not None:
                 i = tickets[tk]
