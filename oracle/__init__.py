@@ -79,6 +79,7 @@ def _load():
             "orc_adjoint_contract": ([mp, vp, vp, f64, vp, vp], None),
             "orc_cg": ([mp, f64, i32, vp, vp], i32),
             "orc_volume": ([mp, vp, vp, vp], None),
+            "orc_adjoint_contract_E": ([mp, vp, vp, vp], None),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -230,6 +231,35 @@ def adjoint_contract(model, u, lam, w: float = 1.0):
     _load().orc_adjoint_contract(b.ref(), _ptr(_f64(u, n)), _ptr(_f64(lam, n)), float(w),
                                  _ptr(dz), _ptr(dt))
     return dz, dt[:b.quad_conn.shape[0]]
+
+
+def adjoint_contract_E(model, u, lam):
+    """-lambda_e^T (dk_e/dE) u_e per quad (the E part of Eq. 6)."""
+    b = _Bound(model)
+    n = 6 * b.n_nodes
+    dE = np.zeros(max(b.quad_conn.shape[0], 1))
+    _load().orc_adjoint_contract_E(b.ref(), _ptr(_f64(u, n)), _ptr(_f64(lam, n)), _ptr(dE))
+    return dE[:b.quad_conn.shape[0]]
+
+
+def simp_model(model, rho, penal):
+    """The model with SIMP moduli E_j = rho_j^penal E*_j (Eq. simp_eq), E* the
+    model's own moduli."""
+    out = dict(model)
+    props = np.array(model["quad_props"], dtype=np.float64, copy=True)
+    props[:, 1] = np.asarray(rho, np.float64) ** penal * props[:, 1]
+    out["quad_props"] = props
+    return out
+
+
+def simp_gradient(model, rho, penal, w: float = 1.0, g=None):
+    """gradient() of the SIMP model plus drho: dJ/drho_j = dJ/dE_j P rho_j^(P-1) E*_j."""
+    rho = np.asarray(rho, np.float64)
+    ms = simp_model(model, rho, penal)
+    r = gradient(ms, w, g)
+    dE = adjoint_contract_E(ms, r["u"], r["lam"])
+    r["drho"] = dE * penal * rho ** (penal - 1.0) * np.asarray(model["quad_props"])[:, 1]
+    return r
 
 
 def volume(model):

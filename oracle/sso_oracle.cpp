@@ -813,6 +813,27 @@ void orc_adjoint_contract(const orc_mesh* m, const double* u, const double* lam,
   adjoint_contract(m, uu, ll, w, dz, dt);
 }
 
+// dJ/dE_j per quad for J = w C + g^T u at a given (u, lambda): the stiffness
+// term -lambda_e^T (dk_e/dE) u_e of Eq. 6 (loads do not depend on E), dk_e/dE by
+// dual numbers seeded on the element's Young's modulus.  With SIMP (Eq.
+// simp_eq, E_j = p_j^P E*_j) the caller forms dJ/dp_j = dJ/dE_j P p_j^(P-1) E*_j.
+void orc_adjoint_contract_E(const orc_mesh* m, const double* u, const double* lam, double* dE) {
+  for (int e = 0; e < m->n_quads; ++e) {
+    int nodes[4];
+    for (int a = 0; a < 4; ++a) nodes[a] = m->quad_conn[4 * e + a];
+    Dual X[4][3], p[5], K[24][24];
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) X[a][k] = Dual(m->xyz[3 * nodes[a] + k]);
+    for (int k = 0; k < 5; ++k) p[k] = Dual(m->quad_props[5 * e + k], k == 1 ? 1.0 : 0.0);
+    quad_ke<Dual>(X, p, K);
+    double s = 0.0;
+    for (int i = 0; i < 24; ++i)
+      for (int j = 0; j < 24; ++j)
+        s += lam[6 * nodes[i / 6] + i % 6] * K[i][j].d * u[6 * nodes[j / 6] + j % 6];
+    dE[e] = -s;
+  }
+}
+
 // Material volume of the quads, W = sum_e A_e t_e (Sec. 3.3, the volume term
 // of the size-optimisation objective without its minimum-thickness penalty),
 // with A_e the area of the element's flat facet (the same 2 x 2 Gauss
