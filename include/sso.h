@@ -179,6 +179,17 @@ void sso_model_destroy(sso_model* model);
  * thicknesses (either may be NULL to keep the current values). */
 sso_status sso_model_set_design(sso_model* model, const double* z, const double* t);
 
+/* SIMP topology variables (Sec. 3.5, Eq. simp_eq): E_j = rho_j^penal E*_j for
+ * every quad, E* the moduli the model was created with.  rho [n_quads] (host
+ * or device) in (0, 1], penal >= 1; rho NULL restores E*.  Afterwards every
+ * gradient call also yields dJ/drho (sso_model_get_topology_gradient):
+ * -(penal / rho_j) lambda_e^T k_e u_e, the stiffness term of Eq. 6 for this
+ * variable (loads do not depend on rho).  Errors: SSO_ERR_INVALID for a
+ * density outside (0, 1], a penalty below 1, or rho on a model without quads. */
+sso_status sso_model_set_topology(sso_model* model, const double* rho, double penal);
+/* dJ/drho [n_quads] of the last gradient call (host or device output). */
+sso_status sso_model_get_topology_gradient(sso_model* model, double* drho);
+
 /* Element matrices -> K (FP64, and its FP32 rounding) -> supports ->
  * preconditioner -> loads -> CG / iterative refinement.  Results stay on the
  * device; read them with sso_model_get.  `stats` may be NULL. */

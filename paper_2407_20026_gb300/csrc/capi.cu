@@ -158,6 +158,10 @@ struct sso_model {
   // material volume (Sec. 3.3): per-quad A t, per-slot t dA/dz (beam slots
   // stay 0), dW/dz, dW/dt, W
   double *d_vol, *d_vslot, *d_vdz, *d_vdt, *d_V;
+  // SIMP topology (Eq. simp_eq): reference moduli E*, densities, dJ/drho
+  double *d_E0, *d_rho, *d_drho;
+  bool has_topology = false;
+  double penal = 1.0;
   int* d_err;
   bool assembled = false, solved = false;
   int assembled_precond = -1;
@@ -444,6 +448,8 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_beam_props = c.take<double>(6 * (size_t)M->n_beams);
   M->d_quad_props = c.take<double>(5 * (size_t)M->n_quads);
   M->d_nodal_load = c.take<double>(ndof);
+  M->d_E0 = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
+  M->d_rho = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_ke = c.take<double>((size_t)M->n_eb * 36);
   M->d_fslot = c.take<double>(M->n_slots);
   M->d_gslot = c.take<double>(M->n_slots);
@@ -474,6 +480,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_vdz = c.take<double>(n);
   M->d_vdt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_V = c.take<double>(1);
+  M->d_drho = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_err = c.take<int>(1);
   return align_up(c.off, 256);
 }
@@ -871,6 +878,12 @@ sso_status prepare_model(ModelPrep& P) {
   put(M->d_beam_props, hm.beam_props.data(), hm.beam_props.size() * 8);
   put(M->d_quad_props, hm.quad_props.data(), hm.quad_props.size() * 8);
   put(M->d_nodal_load, hm.nodal_load.data(), hm.nodal_load.size() * 8);
+  {
+    std::vector<double> e0(hm.n_quads), one(hm.n_quads, 1.0);
+    for (int e = 0; e < hm.n_quads; ++e) e0[e] = hm.quad_props[5 * (size_t)e + 1];
+    put(M->d_E0, e0.data(), e0.size() * 8);
+    put(M->d_rho, one.data(), one.size() * 8);
+  }
   return SSO_OK;
 }
 
@@ -1064,6 +1077,45 @@ sso_status sso_model_get(sso_model* M, double* u, double* C, double* dz, double*
   if (dt && M->n_quads > 0)
     CK(cudaMemcpyAsync(dt, M->d_dt, M->n_quads * 8, cudaMemcpyDefault, M->stream));
   if (lam) CK(cudaMemcpyAsync(lam, M->d_lam, ndof * 8, cudaMemcpyDefault, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  return leave(M);
+}
+
+sso_status sso_model_set_topology(sso_model* M, const double* rho, double penal) {
+  if (!M) return fail(SSO_ERR_INVALID, "model is NULL");
+  if (rho && !(penal >= 1.0 && std::isfinite(penal)))
+    return fail(SSO_ERR_INVALID, "need a finite penalty factor >= 1");
+  if (M->n_quads == 0) return rho ? fail(SSO_ERR_INVALID, "the model has no quads") : SSO_OK;
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  if (rho) {
+    std::vector<double> h(M->n_quads);
+    CK(to_host(h.data(), rho, h.size() * sizeof(double)));
+    for (double v : h)
+      if (!(v > 0.0 && v <= 1.0)) return fail(SSO_ERR_INVALID, "densities must lie in (0, 1]");
+    CK(cudaMemcpyAsync(M->d_rho, h.data(), h.size() * 8, cudaMemcpyHostToDevice, M->stream));
+    CK(cudaStreamSynchronize(M->stream));  // h is a temporary
+    M->penal = penal;
+    M->has_topology = true;
+  } else {
+    const std::vector<double> one(M->n_quads, 1.0);
+    CK(cudaMemcpyAsync(M->d_rho, one.data(), one.size() * 8, cudaMemcpyHostToDevice, M->stream));
+    CK(cudaStreamSynchronize(M->stream));
+    M->penal = 1.0;
+    M->has_topology = false;
+  }
+  CL(launch_simp(M->n_quads, M->d_rho, M->d_E0, M->penal, M->d_quad_props, M->stream), 1);
+  M->assembled = false;
+  M->solved = false;
+  return leave(M);
+}
+
+sso_status sso_model_get_topology_gradient(sso_model* M, double* drho) {
+  if (!M || !drho) return fail(SSO_ERR_INVALID, "NULL argument");
+  if (!M->has_topology) return fail(SSO_ERR_INVALID, "no topology densities set");
+  sso_status st = enter(M);
+  if (st != SSO_OK) return st;
+  CK(cudaMemcpyAsync(drho, M->d_drho, M->n_quads * 8, cudaMemcpyDefault, M->stream));
   CK(cudaStreamSynchronize(M->stream));
   return leave(M);
 }
@@ -1382,7 +1434,8 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
        M->n_beams > 0);
     CL(launch_quad_adjoint(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props, M->pressure,
                            M->gamma, M->d_u, lam, lam_scale, ws,
-                           M->d_gslot + 2 * (size_t)M->n_beams, M->d_dt, B->stream),
+                           M->d_gslot + 2 * (size_t)M->n_beams, M->d_dt, B->stream,
+                           M->d_rho, M->penal, M->has_topology ? M->d_drho : nullptr),
        M->n_quads > 0);
     CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, nullptr, M->d_gslot,
                           nullptr, M->d_fixed, nullptr, M->d_dz, B->stream),

@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(128) quad_adjoint_kernel(
     int nq, const double* __restrict__ xyz, const int* __restrict__ conn,
     const double* __restrict__ props, double pressure, double gamma,
     const double* __restrict__ u, const double* __restrict__ lam, double lam_scale, double w,
-    double* __restrict__ gslot, double* __restrict__ dt) {
+    double* __restrict__ gslot, double* __restrict__ dt, const double* __restrict__ rho,
+    double penal, double* __restrict__ drho) {
   typedef DN<5> D;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nq) return;
@@ -609,6 +610,9 @@ __global__ void __launch_bounds__(128) quad_adjoint_kernel(
     for (int a = 0; a < 4; ++a) gslot[4 * e + a] = Gt.d[a];
   }
   if (dt) dt[e] = Gt.d[4];
+  // SIMP (Eq. simp_eq): E = rho^P E*, and k_e is linear in E, so
+  // d(lambda^T k_e u)/d rho = (P / rho) lambda^T k_e u
+  if (drho) drho[e] = -(penal / rho[e]) * energy.v;
 }
 
 __global__ void __launch_bounds__(128) beam_adjoint_kernel(
@@ -763,10 +767,27 @@ cudaError_t launch_beam_adjoint(int n_beams, const double* xyz, const int* conn,
 cudaError_t launch_quad_adjoint(int n_quads, const double* xyz, const int* conn,
                                 const double* props, double pressure, double gamma,
                                 const double* u, const double* lam, double lam_scale,
-                                double w, double* gslot, double* dt, cudaStream_t s) {
+                                double w, double* gslot, double* dt, cudaStream_t s,
+                                const double* rho, double penal, double* drho) {
   if (n_quads <= 0) return cudaSuccess;
   quad_adjoint_kernel<<<(n_quads + 127) / 128, 128, 0, s>>>(
-      n_quads, xyz, conn, props, pressure, gamma, u, lam, lam_scale, w, gslot, dt);
+      n_quads, xyz, conn, props, pressure, gamma, u, lam, lam_scale, w, gslot, dt, rho, penal,
+      drho);
+  return cudaGetLastError();
+}
+
+// SIMP moduli (Eq. simp_eq): E_e = rho_e^P E*_e into the quads' properties.
+__global__ void simp_kernel(int nq, const double* __restrict__ rho,
+                            const double* __restrict__ E0, double penal,
+                            double* __restrict__ props) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nq) props[5 * e + 1] = ::pow(rho[e], penal) * E0[e];
+}
+
+cudaError_t launch_simp(int n_quads, const double* rho, const double* E0, double penal,
+                        double* props, cudaStream_t s) {
+  if (n_quads <= 0) return cudaSuccess;
+  simp_kernel<<<(n_quads + 127) / 128, 128, 0, s>>>(n_quads, rho, E0, penal, props);
   return cudaGetLastError();
 }
 

@@ -151,7 +151,11 @@ cudaError_t launch_beam_adjoint(int n_beams, const double* xyz, const int* conn,
 cudaError_t launch_quad_adjoint(int n_quads, const double* xyz, const int* conn,
                                 const double* props, double pressure, double gamma,
                                 const double* u, const double* lam, double lam_scale,
-                                double w, double* gslot, double* dt, cudaStream_t s);
+                                double w, double* gslot, double* dt, cudaStream_t s,
+                                const double* rho = nullptr, double penal = 1.0,
+                                double* drho = nullptr);
+cudaError_t launch_simp(int n_quads, const double* rho, const double* E0, double penal,
+                        double* props, cudaStream_t s);
 
 // Launchers (assembly.cu)
 cudaError_t launch_assemble(int n_blocks, const int* cptr, const int* csrc, const double* ke,

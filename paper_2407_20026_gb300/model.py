@@ -118,6 +118,23 @@ class Model:
         tp, tk = _buf(t, torch.float64)
         _lib.check(_lib.load().sso_model_set_design(self._h, zp, tp))
 
+    def set_topology(self, rho=None, penal=3.0):
+        """SIMP densities (Eq. simp_eq): E_j = rho_j^penal E*_j; None restores E*."""
+        rp, rk = _buf(rho, torch.float64)
+        _lib.check(_lib.load().sso_model_set_topology(self._h, rp, float(penal)))
+        self.has_topology = rho is not None
+
+    def topology_gradient(self, device=None):
+        """dJ/drho [n_quads] of the last gradient call."""
+        if device is None:
+            out = np.zeros(self.n_quads)
+            ptr = out.ctypes.data
+        else:
+            out = torch.empty(self.n_quads, dtype=torch.float64, device=device)
+            ptr = out.data_ptr()
+        _lib.check(_lib.load().sso_model_get_topology_gradient(self._h, ptr))
+        return out
+
     def solve(self, opts=None, **kw):
         o = opts if opts is not None else options(**kw)
         st = _lib.Stats()

@@ -255,6 +255,42 @@ def test_autograd_function(sso, orc):
     assert rel(t.grad.cpu().numpy(), ref["dt"] + 0.3 * vol["dt"]) <= TOL_FP64
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_ir", TOL_FP32_IR)])
+@pytest.mark.parametrize("name", ["shell5", "mixed"])
+def test_simp_topology_gradient(sso, orc, name, precision, tol):
+    """SIMP densities (Eq. simp_eq, P = 3): u, C, dC/dz, dC/dt and dC/drho vs
+    the oracle on the same densities; then densities removed again."""
+    m = MODELS[name]()
+    nq = m["quad_conn"].shape[0]
+    rho = np.random.default_rng(4).uniform(0.3, 1.0, nq)
+    ref = orc.simp_gradient(m, rho, 3.0)
+    mdl = sso.Model(m)
+    mdl.set_topology(rho, 3.0)
+    rtol = 1e-10 if precision == "fp64" else 1e-9
+    st = mdl.solve(precision=precision, rtol=rtol)
+    assert st["status"] == 0
+    mdl.gradient(1.0)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= tol
+    assert abs(r["C"] - ref["C"]) <= tol * abs(ref["C"])
+    assert rel(r["dz"], ref["dz"]) <= tol
+    assert rel(r["dt"], ref["dt"]) <= tol
+    assert rel(mdl.topology_gradient(), ref["drho"]) <= tol
+    mdl.set_topology(None)
+    mdl.solve(precision=precision, rtol=rtol)
+    plain = orc.gradient(m)
+    assert rel(mdl.result()["u"], plain["u"]) <= tol
+
+
+def test_simp_rejects_bad_densities(sso):
+    mdl = sso.Model(small_shell(4))
+    nq = mdl.n_quads
+    with pytest.raises(sso.SSOError):
+        mdl.set_topology(np.zeros(nq), 3.0)
+    with pytest.raises(sso.SSOError):
+        mdl.set_topology(np.ones(nq), 0.5)
+
+
 @pytest.mark.parametrize("name", ["shell5", "shell9_clamped", "mixed", "gridshell13"])
 def test_material_volume(sso, orc, name):
     """W = sum A_e t_e and its z, t gradients vs the oracle (element-level
