@@ -179,6 +179,13 @@ void sso_model_destroy(sso_model* model);
  * thicknesses (either may be NULL to keep the current values). */
 sso_status sso_model_set_design(sso_model* model, const double* z, const double* t);
 
+/* The node aggregates of the two-level preconditioner (host only, no device
+ * needed): agg_of_node [n_nodes] (host memory) receives each node's aggregate
+ * in [0, *n_aggregates).  Aggregates grow breadth-first over the node
+ * adjacency from the lowest-numbered free node to ~max(16, n_nodes / 80)
+ * nodes; small leftovers join their best-linked neighbour. */
+sso_status sso_aggregate(const sso_mesh* mesh, int32_t* agg_of_node, int32_t* n_aggregates);
+
 /* SIMP topology variables (Sec. 3.5, Eq. simp_eq): E_j = rho_j^penal E*_j for
  * every quad, E* the moduli the model was created with.  rho [n_quads] (host
  * or device) in (0, 1], penal >= 1; rho NULL restores E*.  Afterwards every

@@ -109,6 +109,7 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_int64)], _i32),
     "sso_model_volume": ([_vp, _vp, _vp, _vp], _i32),
     "sso_model_set_topology": ([_vp, _vp, _f64], _i32),
+    "sso_aggregate": ([ctypes.POINTER(Mesh), _vp, ctypes.POINTER(_i32)], _i32),
     "sso_model_get_topology_gradient": ([_vp, _vp], _i32),
     "sso_batch_setup_times": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64),
                                ctypes.POINTER(_f64), ctypes.POINTER(_f64),

@@ -387,6 +387,82 @@ void build_topology(const HostMesh& m, HostTopo& T) {
   }
 }
 
+// Aggregation of the nodes for the two-level preconditioner: greedy
+// breadth-first growth from the lowest-numbered free node over the block
+// adjacency (the rows of K), each aggregate stopping at `target` nodes;
+// aggregates of fewer than target / 4 nodes are then merged into the
+// neighbouring aggregate they share most block links with (lowest index on a
+// tie).  Deterministic; returns the number of aggregates, agg_of[n] in
+// [0, n_agg) numbered in order of their seeds.
+int aggregate_nodes(int n, const std::vector<int>& row_ptr, const std::vector<int>& col,
+                    int target, std::vector<int>& agg_of) {
+  agg_of.assign(n, -1);
+  std::vector<int> queue;
+  queue.reserve(target);
+  int n_agg = 0;
+  for (int seed = 0; seed < n; ++seed) {
+    if (agg_of[seed] >= 0) continue;
+    queue.clear();
+    queue.push_back(seed);
+    agg_of[seed] = n_agg;
+    for (size_t h = 0; h < queue.size() && (int)queue.size() < target; ++h) {
+      const int v = queue[h];
+      for (int b = row_ptr[v]; b < row_ptr[v + 1] && (int)queue.size() < target; ++b) {
+        const int u = col[b];
+        if (agg_of[u] < 0) {
+          agg_of[u] = n_agg;
+          queue.push_back(u);
+        }
+      }
+    }
+    ++n_agg;
+  }
+  // merge the small ones
+  std::vector<int> size(n_agg, 0);
+  for (int i = 0; i < n; ++i) size[agg_of[i]]++;
+  std::vector<int> remap(n_agg);
+  for (int g = 0; g < n_agg; ++g) remap[g] = g;
+  std::vector<int> links(n_agg, 0);
+  for (int g = 0; g < n_agg; ++g) {
+    if (size[g] * 4 >= target || n_agg == 1) continue;
+    std::vector<int> touched;
+    for (int i = 0; i < n; ++i) {
+      if (agg_of[i] != g) continue;
+      for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        int h = agg_of[col[b]];
+        while (remap[h] != h) h = remap[h];
+        if (h == g) continue;
+        if (links[h]++ == 0) touched.push_back(h);
+      }
+    }
+    int best = -1;
+    for (int h : touched)
+      if (best < 0 || links[h] > links[best] || (links[h] == links[best] && h < best)) best = h;
+    for (int h : touched) links[h] = 0;
+    if (best >= 0) remap[g] = best;
+  }
+  std::vector<int> renum(n_agg, -1);
+  int m = 0;
+  for (int g = 0; g < n_agg; ++g) {
+    int h = g;
+    while (remap[h] != h) h = remap[h];
+    if (h == g) renum[g] = m++;
+  }
+  for (int i = 0; i < n; ++i) {
+    int h = agg_of[i];
+    while (remap[h] != h) h = remap[h];
+    agg_of[i] = renum[h];
+  }
+  return m;
+}
+
+// Aggregate size for a mesh of n nodes: at most kMaxAggregates aggregates
+// (coarse problems of at most 6 kMaxAggregates unknowns), at least 16 nodes each.
+constexpr int kMaxAggregates = 80;
+int aggregate_target(int n) {
+  return std::max(16, (n + kMaxAggregates - 1) / kMaxAggregates);
+}
+
 // Every index the set-up and CG kernels follow, checked against the extents
 // of the arrays it indexes (the SSO_DEBUG_SYNC check).
 bool topology_consistent(const HostMesh& m, const HostTopo& T) {
@@ -1079,6 +1155,20 @@ sso_status sso_model_get(sso_model* M, double* u, double* C, double* dz, double*
   if (lam) CK(cudaMemcpyAsync(lam, M->d_lam, ndof * 8, cudaMemcpyDefault, M->stream));
   CK(cudaStreamSynchronize(M->stream));
   return leave(M);
+}
+
+sso_status sso_aggregate(const sso_mesh* mesh, int32_t* agg_of_node, int32_t* n_aggregates) {
+  if (!agg_of_node || !n_aggregates) return fail(SSO_ERR_INVALID, "NULL argument");
+  ModelPrep P;
+  sso_status st = mesh_to_prep(mesh, P);
+  if (st != SSO_OK) return st;
+  if ((st = validate(P.hm)) != SSO_OK) return st;
+  build_topology(P.hm, P.T);
+  std::vector<int> agg;
+  *n_aggregates = aggregate_nodes(P.hm.n_nodes, P.T.row_ptr, P.T.col,
+                                  aggregate_target(P.hm.n_nodes), agg);
+  std::copy(agg.begin(), agg.end(), agg_of_node);
+  return SSO_OK;
 }
 
 sso_status sso_model_set_topology(sso_model* M, const double* rho, double penal) {

@@ -56,6 +56,16 @@ def options(**kw):
     return o
 
 
+def aggregate(mesh: dict):
+    """(agg_of_node [n_nodes] int32, n_aggregates): the node aggregates of the
+    two-level preconditioner (host only)."""
+    m, keep = mesh_struct(mesh)
+    out = np.zeros(m.n_nodes, np.int32)
+    n = ctypes.c_int32()
+    _lib.check(_lib.load().sso_aggregate(ctypes.byref(m), out.ctypes.data, ctypes.byref(n)))
+    return out, n.value
+
+
 def kernel_launches() -> int:
     return int(_lib.load().sso_kernel_launches())
 
