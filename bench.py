@@ -46,7 +46,8 @@ def parse():
     p.add_argument("--batch", type=int, default=128, help="designs per step")
     p.add_argument("--n-el", type=int, default=64)
     p.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
-    p.add_argument("--precond", default="block_jacobi", choices=["block_jacobi", "jacobi"])
+    p.add_argument("--precond", default="block_jacobi",
+                   choices=["block_jacobi", "jacobi", "two_level"])
     p.add_argument("--rtol", type=float, default=1e-6)
     p.add_argument("--inner-rtol", type=float, default=1e-3)
     p.add_argument("--iters-per-launch", type=int, default=32)
@@ -657,6 +658,7 @@ def main():
     pstats = step_device()
     torch.cuda.synchronize()
     ms_a, ms_b, timed_pairs = batch.kernel_times()
+    setup = batch.setup_times()
     batch.set_profiling(False)
     p_iters = sum(s["iterations"] for s in pstats)
     p_sweeps = sum(s["sweeps"] for s in pstats)
@@ -764,6 +766,16 @@ def main():
                 "launches_timed": a_launches, "kernel_ms_total": ms_a,
                 "kernel_b_ms_total": ms_b,
             },
+            # elapsed per phase of the profiled step; the set-ups of the
+            # designs overlap on a stream pool, so their per-kernel device
+            # times are reported separately, summed over the designs
+            "phase_ms_per_step": {"setup": setup["setup_wall"],
+                                  "cg_kernel_a": ms_a, "cg_kernel_b_and_coarse": ms_b,
+                                  "adjoint_contraction": setup["adjoint"],
+                                  "setup_device_ms_summed": {
+                                      "element_matrices": setup["elements"],
+                                      "assembly": setup["assembly"],
+                                      "preconditioner_and_loads": setup["precond"]}},
             "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy,
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
         }

@@ -76,7 +76,10 @@ typedef struct {
 } sso_mesh;
 
 typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1 } sso_precision;
-typedef enum { SSO_JACOBI = 0, SSO_BLOCK_JACOBI = 1 } sso_precond;
+/* SSO_TWO_LEVEL: block-Jacobi plus a coarse correction over the rigid-body
+ * modes of node aggregates (z = M_b^-1 r + P A_c^-1 P^T r, A_c = P^T K P);
+ * FP32_IR only, batches and models (not the server). */
+typedef enum { SSO_JACOBI = 0, SSO_BLOCK_JACOBI = 1, SSO_TWO_LEVEL = 2 } sso_precond;
 
 /* Solver options.  Convergence is ||f - K u||_2 <= rtol ||f||_2 over all DOFs,
  * with the residual recomputed in FP64 from the FP64 K. */
@@ -182,7 +185,7 @@ sso_status sso_model_set_design(sso_model* model, const double* z, const double*
 /* The node aggregates of the two-level preconditioner (host only, no device
  * needed): agg_of_node [n_nodes] (host memory) receives each node's aggregate
  * in [0, *n_aggregates).  Aggregates grow breadth-first over the node
- * adjacency from the lowest-numbered free node to ~max(16, n_nodes / 80)
+ * adjacency from the lowest-numbered free node to ~max(16, n_nodes / 39)
  * nodes; small leftovers join their best-linked neighbour. */
 sso_status sso_aggregate(const sso_mesh* mesh, int32_t* agg_of_node, int32_t* n_aggregates);
 
@@ -264,15 +267,20 @@ sso_status sso_batch_set_profiling(sso_batch* batch, int32_t enable);
 sso_status sso_batch_kernel_times(const sso_batch* batch, double* ms_a, double* ms_b,
                                   int64_t* launches);
 /* Set-up and adjoint timing while profiling is enabled (same switch and
- * reset): device milliseconds summed over every model set-up of
+ * reset).  The models' set-ups and contraction passes run concurrently on a
+ * pool of up to 16 streams.  ms_elements, ms_assembly and ms_precond are
+ * device milliseconds of each phase summed over every model set-up of
  * sso_batch_solve -- element matrices (Sec. 2.2), assembly of K (Eq. 1),
- * preconditioner + load vector -- and over every contraction pass of
- * sso_batch_gradient (the adjoint sum of Eq. 6 and the per-node gather).
- * setups counts model set-ups timed, gradients the gradient calls.  Any
- * pointer may be NULL. */
+ * preconditioner + load vector -- and so count overlapping work once per
+ * model; ms_setup_wall is the elapsed time of the whole set-up phase (first
+ * set-up launched to last one finished), summed over solves.  ms_adjoint is
+ * the elapsed time of every contraction pass of sso_batch_gradient (the
+ * adjoint sum of Eq. 6 and the per-node gather, all models).  setups counts
+ * model set-ups timed, gradients the gradient calls.  Any pointer may be
+ * NULL. */
 sso_status sso_batch_setup_times(const sso_batch* batch, double* ms_elements,
                                  double* ms_assembly, double* ms_precond, double* ms_adjoint,
-                                 int64_t* setups, int64_t* gradients);
+                                 double* ms_setup_wall, int64_t* setups, int64_t* gradients);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of design evaluations.  Each request is one

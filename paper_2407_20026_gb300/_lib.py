@@ -24,6 +24,7 @@ FP64 = 0
 FP32_IR = 1
 JACOBI = 0
 BLOCK_JACOBI = 1
+TWO_LEVEL = 2
 
 
 class SSOError(RuntimeError):
@@ -112,7 +113,7 @@ SIGNATURES = {
     "sso_aggregate": ([ctypes.POINTER(Mesh), _vp, ctypes.POINTER(_i32)], _i32),
     "sso_model_get_topology_gradient": ([_vp, _vp], _i32),
     "sso_batch_setup_times": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64),
-                               ctypes.POINTER(_f64), ctypes.POINTER(_f64),
+                               ctypes.POINTER(_f64), ctypes.POINTER(_f64), ctypes.POINTER(_f64),
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
                               _i32),
 }

@@ -127,6 +127,10 @@ struct HostMesh {
 
 struct HostTopo {
   std::vector<int> row_ptr, col, brow, diag, cptr, csrc, nptr, nsrc;
+  // two-level preconditioner: node aggregates and, per aggregate pair (g, h),
+  // the K blocks (i, j) with i in g and j in h, in block order
+  int n_agg = 0;
+  std::vector<int> agg_of, agg_ptr, agg_nodes, cg_ptr, cg_src;
 };
 
 }  // namespace
@@ -137,6 +141,7 @@ struct sso_model {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int n_nodes = 0, n_beams = 0, n_quads = 0, n_blocks = 0, n_eb = 0, n_slots = 0, n_tiles = 0;
+  int n_agg = 0;  // node aggregates of the two-level preconditioner
   double pressure = 0.0, gamma = 0.0;
   std::vector<int> h_row_ptr, h_col;
   void* arena = nullptr;
@@ -160,6 +165,13 @@ struct sso_model {
   double *d_vol, *d_vslot, *d_vdz, *d_vdt, *d_V;
   // SIMP topology (Eq. simp_eq): reference moduli E*, densities, dJ/drho
   double *d_E0, *d_rho, *d_drho;
+  // two-level preconditioner: aggregate lists (per topology), per-design
+  // node offsets, coarse matrix and its inverse, coarse vectors, z_b
+  int *d_agg_of, *d_agg_ptr, *d_agg_nodes, *d_cg_ptr, *d_cg_src;
+  double *d_node_r64, *d_Ac;
+  float *d_node_rf, *d_Aci, *d_cw, *d_cy;
+  double* d_cdot;
+  double* d_zb;
   bool has_topology = false;
   double penal = 1.0;
   int* d_err;
@@ -183,11 +195,16 @@ struct sso_batch {
   std::vector<SysDesc> h_sys;
   SysScalars* h_sc = nullptr;   // pinned, n_sys
   int* h_flag = nullptr;        // pinned: [0..1] upload, [2..3] read back
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  int exec_iters[2] = {0, 0};
-  int exec_prof[2] = {0, 0};
-  int grid_a[2] = {0, 0};
-  int grid_b[2] = {0, 0};
+  // CG graphs: [0] FP32, [1] FP64, [2] FP32 with the two-level coarse kernels
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  int exec_iters[3] = {0, 0, 0};
+  int exec_prof[3] = {0, 0, 0};
+  int grid_a[3] = {0, 0, 0};
+  int grid_b[3] = {0, 0, 0};
+  // two-level work lists: every (system, aggregate), every system
+  AggRef* d_aggs = nullptr;
+  int n_aggs = 0;
+  int* d_csys = nullptr;
   cudaEvent_t ev = nullptr;
   // kernel timing (sso_batch_set_profiling): events around every A and B
   // launch inside the captured graph
@@ -198,7 +215,13 @@ struct sso_batch {
   // set-up and adjoint timing: 4 events per model around its element,
   // assembly and preconditioner + load kernels, 2 around the contraction pass
   std::vector<cudaEvent_t> sev;
+  // per-model set-up and adjoint kernels run on a pool of streams (models
+  // are independent), forked from and joined back to the batch stream
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> aux_ev;
+  cudaEvent_t ev_fork = nullptr;
   double prof_ms_el = 0.0, prof_ms_asm = 0.0, prof_ms_pre = 0.0, prof_ms_adj = 0.0;
+  double prof_ms_setup = 0.0;  // fork-to-join wall time of the set-ups
   long long prof_setups = 0, prof_grads = 0;
 };
 
@@ -457,8 +480,9 @@ int aggregate_nodes(int n, const std::vector<int>& row_ptr, const std::vector<in
 }
 
 // Aggregate size for a mesh of n nodes: at most kMaxAggregates aggregates
-// (coarse problems of at most 6 kMaxAggregates unknowns), at least 16 nodes each.
-constexpr int kMaxAggregates = 80;
+// (coarse problems of at most 6 kMaxAggregates = 234 unknowns, whose FP32
+// inverse is formed in one CTA's shared memory), at least 16 nodes each.
+constexpr int kMaxAggregates = COARSE_MAX_AGG;
 int aggregate_target(int n) {
   return std::max(16, (n + kMaxAggregates - 1) / kMaxAggregates);
 }
@@ -526,7 +550,14 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_nodal_load = c.take<double>(ndof);
   M->d_E0 = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_rho = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
-  M->d_ke = c.take<double>((size_t)M->n_eb * 36);
+  const size_t na = (size_t)std::max(M->n_agg, 1);
+  M->d_agg_of = c.take<int>(n);
+  M->d_agg_ptr = c.take<int>(na + 1);
+  M->d_agg_nodes = c.take<int>(n);
+  M->d_cg_ptr = c.take<int>(na * na + 1);
+  M->d_cg_src = c.take<int>(M->n_blocks);
+  // element blocks; after assembly also the Galerkin block products
+  M->d_ke = c.take<double>((size_t)std::max(M->n_eb, M->n_blocks) * 36);
   M->d_fslot = c.take<double>(M->n_slots);
   M->d_gslot = c.take<double>(M->n_slots);
   M->d_K64 = c.take<double>((size_t)M->n_blocks * 36);
@@ -557,6 +588,14 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_vdt = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
   M->d_V = c.take<double>(1);
   M->d_drho = c.take<double>(M->n_quads > 0 ? M->n_quads : 1);
+  M->d_node_r64 = c.take<double>(3 * n);
+  M->d_node_rf = c.take<float>(4 * n);
+  M->d_Ac = c.take<double>(36 * na * na);
+  M->d_Aci = c.take<float>(36 * na * na);
+  M->d_cw = c.take<float>(6 * na);
+  M->d_cy = c.take<float>(6 * na);
+  M->d_cdot = c.take<double>(COARSE_ROW_BLOCKS);
+  M->d_zb = c.take<double>(ndof);
   M->d_err = c.take<int>(1);
   return align_up(c.off, 256);
 }
@@ -565,8 +604,10 @@ sso_status check_options(const sso_options* o) {
   if (!o) return fail(SSO_ERR_INVALID, "options is NULL");
   if (o->precision != SSO_FP64 && o->precision != SSO_FP32_IR)
     return fail(SSO_ERR_INVALID, "precision must be SSO_FP64 or SSO_FP32_IR");
-  if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI)
-    return fail(SSO_ERR_INVALID, "precond must be SSO_JACOBI or SSO_BLOCK_JACOBI");
+  if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI && o->precond != SSO_TWO_LEVEL)
+    return fail(SSO_ERR_INVALID, "precond must be SSO_JACOBI, SSO_BLOCK_JACOBI or SSO_TWO_LEVEL");
+  if (o->precond == SSO_TWO_LEVEL && o->precision != SSO_FP32_IR)
+    return fail(SSO_ERR_INVALID, "SSO_TWO_LEVEL needs SSO_FP32_IR");
   if (!(o->rtol > 0.0) || !(o->inner_rtol >= 0.0) || o->inner_rtol >= 1.0)
     return fail(SSO_ERR_INVALID, "need rtol > 0 and 0 <= inner_rtol < 1");
   if (o->max_iter <= 0 || o->max_sweeps <= 0)
@@ -609,6 +650,11 @@ sso_status setup_model(sso_model* M, int precond, cudaStream_t s,
   CK(cudaMemsetAsync(M->d_err, 0, sizeof(int), s));
   CL(launch_precond(M->n_nodes, precond, M->d_diag, M->d_K64, M->d_M64, M->d_M32, M->d_err, s),
      1);
+  if (precond == SSO_TWO_LEVEL)
+    CL(launch_coarse_setup(M->n_nodes, M->n_agg, M->n_blocks, M->d_agg_ptr, M->d_agg_nodes,
+                           M->d_brow, M->d_col, M->d_cg_ptr, M->d_cg_src, M->d_xyz, M->d_fixed,
+                           M->d_K64, M->d_node_r64, M->d_node_rf, M->d_ke, M->d_Ac, M->d_Aci, s),
+       4);
   CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, M->d_fslot, nullptr,
                         M->d_nodal_load, M->d_fixed, M->d_f, nullptr, s),
      1);
@@ -618,8 +664,8 @@ sso_status setup_model(sso_model* M, int precond, cudaStream_t s,
   return SSO_OK;
 }
 
-sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
-  const int k = fp64 ? 1 : 0;
+sso_status batch_graph(sso_batch* B, bool fp64, int iters, bool two_level = false) {
+  const int k = fp64 ? 1 : two_level ? 2 : 0;
   if (B->exec[k] && B->exec_iters[k] == iters && B->exec_prof[k] == B->profiling) return SSO_OK;
   if (B->exec[k]) {
     cudaGraphExecDestroy(B->exec[k]);
@@ -651,6 +697,14 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters) {
     if (err == cudaSuccess)
       err = launch_pcg_b(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid_b[k],
                          B->stream);
+    if (err == cudaSuccess && two_level) {
+      err = launch_coarse_restrict(B->d_aggs, B->n_aggs, B->d_sys, B->stream);
+      if (err == cudaSuccess)
+        err = launch_coarse_solve(B->d_csys, B->n_sys, B->d_sys, B->d_n_active, B->stream);
+      if (err == cudaSuccess)
+        err = launch_coarse_prolong(B->d_tiles, B->d_n_tiles, B->d_sys,
+                                    std::max(1, std::min(B->n_tiles, 152 * 8)), B->stream);
+    }
     if (err == cudaSuccess && B->profiling)
       err = cudaEventRecordWithFlags(B->pev[2 * it + 2], B->stream, cudaEventRecordExternal);
   }
@@ -674,6 +728,36 @@ sso_status ensure_setup_events(sso_batch* B, size_t n) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     B->sev.push_back(e);
+  }
+  return SSO_OK;
+}
+
+constexpr int kAuxStreams = 16;
+
+// Forks B's pool of streams off its stream (created on first use).
+sso_status fork_aux(sso_batch* B) {
+  if (B->aux.empty()) {
+    const int k = std::min(kAuxStreams, B->n_sys);
+    CK(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+    for (int i = 0; i < k; ++i) {
+      cudaStream_t st;
+      cudaEvent_t ev;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      B->aux.push_back(st);
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      B->aux_ev.push_back(ev);
+    }
+  }
+  CK(cudaEventRecord(B->ev_fork, B->stream));
+  for (cudaStream_t st : B->aux) CK(cudaStreamWaitEvent(st, B->ev_fork, 0));
+  return SSO_OK;
+}
+
+// Orders B's stream after everything issued on the pool.
+sso_status join_aux(sso_batch* B) {
+  for (size_t i = 0; i < B->aux.size(); ++i) {
+    CK(cudaEventRecord(B->aux_ev[i], B->aux[i]));
+    CK(cudaStreamWaitEvent(B->stream, B->aux_ev[i], 0));
   }
   return SSO_OK;
 }
@@ -736,9 +820,10 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
                      B->stream));
   if (n_act > 0) {
-    sso_status st = batch_graph(B, fp64, o->iters_per_launch);
+    const bool two_level = o->precond == SSO_TWO_LEVEL;
+    sso_status st = batch_graph(B, fp64, o->iters_per_launch, two_level);
     if (st != SSO_OK) return st;
-    const int k = fp64 ? 1 : 0;
+    const int k = fp64 ? 1 : two_level ? 2 : 0;
     const long long max_launches = (long long)o->max_iter * 2 / o->iters_per_launch + 4LL * o->max_sweeps + 8;
     long long launches = 0;
     for (;;) {
@@ -915,9 +1000,37 @@ sso_status prepare_model(ModelPrep& P) {
     P.error = "scatter map inconsistent (internal error)";
     return SSO_ERR_INVALID;
   }
+  HostTopo& Tm = P.T;
+  {
+    const int n = hm.n_nodes;
+    // at most COARSE_MAX_AGG aggregates (the coarse inverse lives in shared memory)
+    for (int target = aggregate_target(n);; target += std::max(1, target / 4)) {
+      Tm.n_agg = aggregate_nodes(n, Tm.row_ptr, Tm.col, target, Tm.agg_of);
+      if (Tm.n_agg <= COARSE_MAX_AGG) break;
+    }
+    const int na = Tm.n_agg;
+    Tm.agg_ptr.assign(na + 1, 0);
+    for (int i = 0; i < n; ++i) Tm.agg_ptr[Tm.agg_of[i] + 1]++;
+    for (int g = 0; g < na; ++g) Tm.agg_ptr[g + 1] += Tm.agg_ptr[g];
+    Tm.agg_nodes.resize(n);
+    std::vector<int> fillg(Tm.agg_ptr.begin(), Tm.agg_ptr.end() - 1);
+    for (int i = 0; i < n; ++i) Tm.agg_nodes[fillg[Tm.agg_of[i]]++] = i;
+    const int nb = (int)Tm.col.size();
+    Tm.cg_ptr.assign((size_t)na * na + 1, 0);
+    std::vector<int> key(nb);
+    for (int b = 0; b < nb; ++b) {
+      key[b] = Tm.agg_of[Tm.brow[b]] * na + Tm.agg_of[Tm.col[b]];
+      Tm.cg_ptr[key[b] + 1]++;
+    }
+    for (size_t q = 0; q < (size_t)na * na; ++q) Tm.cg_ptr[q + 1] += Tm.cg_ptr[q];
+    Tm.cg_src.resize(nb);
+    std::vector<int> fillp(Tm.cg_ptr.begin(), Tm.cg_ptr.end() - 1);
+    for (int b = 0; b < nb; ++b) Tm.cg_src[fillp[key[b]]++] = b;
+  }
   const HostTopo& T = P.T;
   sso_model* M = new sso_model();
   P.M = M;
+  M->n_agg = T.n_agg;
   M->n_nodes = hm.n_nodes;
   M->n_beams = hm.n_beams;
   M->n_quads = hm.n_quads;
@@ -954,6 +1067,11 @@ sso_status prepare_model(ModelPrep& P) {
   put(M->d_beam_props, hm.beam_props.data(), hm.beam_props.size() * 8);
   put(M->d_quad_props, hm.quad_props.data(), hm.quad_props.size() * 8);
   put(M->d_nodal_load, hm.nodal_load.data(), hm.nodal_load.size() * 8);
+  put(M->d_agg_of, T.agg_of.data(), T.agg_of.size() * 4);
+  put(M->d_agg_ptr, T.agg_ptr.data(), T.agg_ptr.size() * 4);
+  put(M->d_agg_nodes, T.agg_nodes.data(), T.agg_nodes.size() * 4);
+  put(M->d_cg_ptr, T.cg_ptr.data(), T.cg_ptr.size() * 4);
+  put(M->d_cg_src, T.cg_src.data(), T.cg_src.size() * 4);
   {
     std::vector<double> e0(hm.n_quads), one(hm.n_quads, 1.0);
     for (int e = 0; e < hm.n_quads; ++e) e0[e] = hm.quad_props[5 * (size_t)e + 1];
@@ -1165,8 +1283,10 @@ sso_status sso_aggregate(const sso_mesh* mesh, int32_t* agg_of_node, int32_t* n_
   if ((st = validate(P.hm)) != SSO_OK) return st;
   build_topology(P.hm, P.T);
   std::vector<int> agg;
-  *n_aggregates = aggregate_nodes(P.hm.n_nodes, P.T.row_ptr, P.T.col,
-                                  aggregate_target(P.hm.n_nodes), agg);
+  for (int target = aggregate_target(P.hm.n_nodes);; target += std::max(1, target / 4)) {
+    *n_aggregates = aggregate_nodes(P.hm.n_nodes, P.T.row_ptr, P.T.col, target, agg);
+    if (*n_aggregates <= COARSE_MAX_AGG) break;
+  }
   std::copy(agg.begin(), agg.end(), agg_of_node);
   return SSO_OK;
 }
@@ -1316,9 +1436,27 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     D.n_chunks = n_chunks_of(M);
     D.chunk_cnt = M->d_chunk_cnt;
     D.chunk_part = M->d_chunk_part;
+    D.n_agg = M->n_agg;
+    D.agg_ptr = M->d_agg_ptr;
+    D.agg_nodes = M->d_agg_nodes;
+    D.agg_of = M->d_agg_of;
+    D.fixed = M->d_fixed;
+    D.node_rf = M->d_node_rf;
+    D.Aci = M->d_Aci;
+    D.w = M->d_cw;
+    D.y = M->d_cy;
+    D.cdot = M->d_cdot;
+    D.zb = M->d_zb;
     for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_tile(M, s, k));
   }
   B->n_tiles = (int)tiles.size();
+  std::vector<AggRef> aggs;
+  std::vector<int> csys(n);
+  for (int s = 0; s < n; ++s) {
+    csys[s] = s;
+    for (int g = 0; g < models[s]->n_agg; ++g) aggs.push_back({s, g});
+  }
+  B->n_aggs = (int)aggs.size();
   Carver c(nullptr);
   c.take<SysDesc>(n);
   c.take<SysScalars>(n);
@@ -1326,6 +1464,8 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   c.take<int>(1);
   c.take<int>(2);
   c.take<double>(n);
+  c.take<AggRef>(std::max<size_t>(aggs.size(), 1));
+  c.take<int>(n);
   const size_t bytes = align_up(c.off, 256);
   cudaError_t e = cudaMalloc(&B->arena, bytes);
   if (e != cudaSuccess) {
@@ -1339,6 +1479,8 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   B->d_n_tiles = d.take<int>(1);
   B->d_n_active = d.take<int>(2);
   B->d_dots = d.take<double>(n);
+  B->d_aggs = d.take<AggRef>(std::max<size_t>(aggs.size(), 1));
+  B->d_csys = d.take<int>(n);
   for (int s = 0; s < n; ++s) B->h_sys[s].sc = B->d_sc + s;
   e = cudaMallocHost(&B->h_sc, sizeof(SysScalars) * n);
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 4 * sizeof(int));
@@ -1353,6 +1495,12 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice,
                         B->stream);
+  if (e == cudaSuccess && !aggs.empty())
+    e = cudaMemcpyAsync(B->d_aggs, aggs.data(), aggs.size() * sizeof(AggRef),
+                        cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_csys, csys.data(), csys.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        B->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
   if (e != cudaSuccess) {
     sso_batch_destroy(B);
@@ -1365,10 +1513,16 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
 void sso_batch_destroy(sso_batch* B) {
   if (!B) return;
   if (B->stream) cudaStreamSynchronize(B->stream);
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 3; ++k)
     if (B->exec[k]) cudaGraphExecDestroy(B->exec[k]);
   for (cudaEvent_t e : B->pev) cudaEventDestroy(e);
   for (cudaEvent_t e : B->sev) cudaEventDestroy(e);
+  for (cudaStream_t st : B->aux) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t e : B->aux_ev) cudaEventDestroy(e);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
   if (B->arena) cudaFree(B->arena);
   if (B->h_sc) cudaFreeHost(B->h_sc);
   if (B->h_flag) cudaFreeHost(B->h_flag);
@@ -1381,15 +1535,16 @@ sso_status sso_batch_set_profiling(sso_batch* B, int32_t enable) {
   B->profiling = enable ? 1 : 0;
   B->prof_ms_a = B->prof_ms_b = 0.0;
   B->prof_launches = 0;
-  B->prof_ms_el = B->prof_ms_asm = B->prof_ms_pre = B->prof_ms_adj = 0.0;
+  B->prof_ms_el = B->prof_ms_asm = B->prof_ms_pre = B->prof_ms_adj = B->prof_ms_setup = 0.0;
   B->prof_setups = B->prof_grads = 0;
   return SSO_OK;
 }
 
 sso_status sso_batch_setup_times(const sso_batch* B, double* ms_elements, double* ms_assembly,
-                                 double* ms_precond, double* ms_adjoint, int64_t* setups,
-                                 int64_t* gradients) {
+                                 double* ms_precond, double* ms_adjoint, double* ms_setup_wall,
+                                 int64_t* setups, int64_t* gradients) {
   if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  if (ms_setup_wall) *ms_setup_wall = B->prof_ms_setup;
   if (ms_elements) *ms_elements = B->prof_ms_el;
   if (ms_assembly) *ms_assembly = B->prof_ms_asm;
   if (ms_precond) *ms_precond = B->prof_ms_pre;
@@ -1422,11 +1577,17 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
     CK(cudaStreamWaitEvent(B->stream, M->ev_in, 0));
   }
   const bool prof = B->profiling != 0;
-  if (prof && (st = ensure_setup_events(B, 4 * (size_t)B->n_sys + 2)) != SSO_OK) return st;
+  const size_t ew = 4 * (size_t)B->n_sys + 2;  // set-up wall-time events
+  if (prof && (st = ensure_setup_events(B, ew + 2)) != SSO_OK) return st;
+  if (prof) CK(cudaEventRecord(B->sev[ew], B->stream));
+  if ((st = fork_aux(B)) != SSO_OK) return st;
   for (int s = 0; s < B->n_sys; ++s) {
-    st = setup_model(B->models[s], opts->precond, B->stream, prof ? &B->sev[4 * s] : nullptr);
+    st = setup_model(B->models[s], opts->precond, B->aux[s % B->aux.size()],
+                     prof ? &B->sev[4 * s] : nullptr);
     if (st != SSO_OK) return st;
   }
+  if ((st = join_aux(B)) != SSO_OK) return st;
+  if (prof) CK(cudaEventRecord(B->sev[ew + 1], B->stream));
   std::vector<char> active(B->n_sys, 1);
   sso_status run = batch_run(B, opts, false, active, stats);
   if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
@@ -1449,6 +1610,7 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
       B->prof_ms_asm += elapsed_ms(e[1], e[2]);
       B->prof_ms_pre += elapsed_ms(e[2], e[3]);
     }
+    B->prof_ms_setup += elapsed_ms(B->sev[ew], B->sev[ew + 1]);
     B->prof_setups += B->n_sys;
   }
   for (int s = 0; s < B->n_sys; ++s) {
@@ -1511,24 +1673,26 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
     if ((st = ensure_setup_events(B, e0 + 2)) != SSO_OK) return st;
     CK(cudaEventRecord(B->sev[e0], B->stream));
   }
+  if ((st = fork_aux(B)) != SSO_OK) return st;
   for (int s = 0; s < B->n_sys; ++s) {
     sso_model* M = B->models[s];
+    cudaStream_t as = B->aux[s % B->aux.size()];
     const double ws = w ? w[s] : 1.0;
     const bool has_g = active[s] != 0;
     const double* lam = has_g ? M->d_lam : M->d_u;
     const double lam_scale = has_g ? 1.0 : ws;
     if (!has_g)
-      CL(launch_axpby(6 * M->n_nodes, ws, M->d_u, nullptr, M->d_fixed, M->d_lam, B->stream), 1);
+      CL(launch_axpby(6 * M->n_nodes, ws, M->d_u, nullptr, M->d_fixed, M->d_lam, as), 1);
     CL(launch_beam_adjoint(M->n_beams, M->d_xyz, M->d_beam_conn, M->d_beam_props, M->d_u, lam,
-                           lam_scale, M->d_gslot, B->stream),
+                           lam_scale, M->d_gslot, as),
        M->n_beams > 0);
     CL(launch_quad_adjoint(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props, M->pressure,
                            M->gamma, M->d_u, lam, lam_scale, ws,
-                           M->d_gslot + 2 * (size_t)M->n_beams, M->d_dt, B->stream,
+                           M->d_gslot + 2 * (size_t)M->n_beams, M->d_dt, as,
                            M->d_rho, M->penal, M->has_topology ? M->d_drho : nullptr),
        M->n_quads > 0);
     CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, nullptr, M->d_gslot,
-                          nullptr, M->d_fixed, nullptr, M->d_dz, B->stream),
+                          nullptr, M->d_fixed, nullptr, M->d_dz, as),
        1);
     if (stats && !has_g) {
       stats[s].status = SSO_OK;
@@ -1538,6 +1702,7 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
       stats[s].ms = 0.0;
     }
   }
+  if ((st = join_aux(B)) != SSO_OK) return st;
   if (prof) CK(cudaEventRecord(B->sev[e0 + 1], B->stream));
   CK(cudaStreamSynchronize(B->stream));
   if (prof) {
@@ -1867,6 +2032,17 @@ void fill_sysdesc(SysDesc& D, sso_model* M, int precond) {
   D.n_chunks = n_chunks_of(M);
   D.chunk_cnt = M->d_chunk_cnt;
   D.chunk_part = M->d_chunk_part;
+  D.n_agg = M->n_agg;
+  D.agg_ptr = M->d_agg_ptr;
+  D.agg_nodes = M->d_agg_nodes;
+  D.agg_of = M->d_agg_of;
+  D.fixed = M->d_fixed;
+  D.node_rf = M->d_node_rf;
+  D.Aci = M->d_Aci;
+  D.w = M->d_cw;
+  D.y = M->d_cy;
+  D.cdot = M->d_cdot;
+  D.zb = M->d_zb;
 }
 
 void init_scalars(SysScalars& S, const sso_options& o) {
@@ -1890,6 +2066,8 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
   *out = nullptr;
   sso_status st = check_options(opts);
   if (st != SSO_OK) return st;
+  if (opts->precond == SSO_TWO_LEVEL)
+    return fail(SSO_ERR_INVALID, "the server does not run SSO_TWO_LEVEL");
   if (max_systems <= 0 || max_tiles <= 0 || hbm_budget_bytes == 0)
     return fail(SSO_ERR_INVALID, "need max_systems > 0, max_tiles > 0, budget > 0");
   sso_server* S = new sso_server();

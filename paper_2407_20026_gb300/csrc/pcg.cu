@@ -467,12 +467,22 @@ __device__ __forceinline__ void finish_b(SysScalars* sc, int state, double s1, d
   sc->cnt_b = 0u;
 }
 
+// Two-level preconditioner: kernel B has only z_b = M_b^-1 r; it leaves
+// r^T z_b and r^T r for the coarse kernel, which adds w^T y and updates the
+// scalars (finish_b).
+__device__ __forceinline__ void defer_b(SysScalars* sc, double rz_b, double rr) {
+  sc->rz_b = rz_b;
+  sc->rr_b = rr;
+  sc->coarse_pending = 1;
+  sc->cnt_b = 0u;
+}
+
 // Kernel B, warp level: adds n of this warp's tiles to chunk c of system S.
 // The warp that completes a chunk sums the chunk's tile partials
 // (CHUNK_PER_THREAD contiguous ones per lane); the one that completes the last chunk sums the chunk sums in order
 // and updates the scalars.  Every grouping depends on the system alone.
 __device__ __forceinline__ void b_count(const SysDesc& S, SysScalars* sc, int state, int c, int n,
-                                        int lane, int* n_active, bool fold) {
+                                        int lane, int* n_active, bool fold, bool defer = false) {
   const int m = min(CHUNK, S.n_tiles - c * CHUNK);
   unsigned* cnt = S.chunk_cnt + S.n_chunks;
   double* cpart = S.chunk_part + 2 * (size_t)S.n_chunks;
@@ -491,7 +501,10 @@ __device__ __forceinline__ void b_count(const SysDesc& S, SysScalars* sc, int st
   if (S.n_chunks == 1) {  // the chunk is the system
     if (lane == 0) {
       cnt[c] = 0u;
-      finish_b(sc, state, v1, v2, n_active, fold);
+      if (defer)
+        defer_b(sc, v1, v2);
+      else
+        finish_b(sc, state, v1, v2, n_active, fold);
     }
     return;
   }
@@ -513,7 +526,12 @@ __device__ __forceinline__ void b_count(const SysDesc& S, SysScalars* sc, int st
   }
   a1 = warp_sum(a1);
   a2 = warp_sum(a2);
-  if (lane == 0) finish_b(sc, state, a1, a2, n_active, fold);
+  if (lane == 0) {
+    if (defer)
+      defer_b(sc, a1, a2);
+    else
+      finish_b(sc, state, a1, a2, n_active, fold);
+  }
 }
 
 template <typename T>
@@ -546,7 +564,7 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
       inv_norm = R.state == ST_PCG ? 0.0 : 1.0 / ::sqrt(R.rr64);
       alpha = (T)R.alpha;
       ua = R.alpha * R.scale;
-      block = S.precond == SSO_BLOCK_JACOBI;
+      block = S.precond != SSO_JACOBI;
     }
     if (R.state == ST_DONE) continue;
     const int state = R.state;
@@ -733,7 +751,7 @@ __device__ __forceinline__ BJob make_bjob(const TileDesc* __restrict__ tiles,
     J.R = read_state(J.S->sc);
     J.work = J.R.state == ST_PCG || J.R.state == ST_FOLD ||
              (isfinite(J.R.rr64) && !(J.R.rr64 <= J.R.rtol2 * J.R.ff));
-    J.block = J.S->precond == SSO_BLOCK_JACOBI;
+    J.block = J.S->precond != SSO_JACOBI;
   }
   J.kind = !J.work ? 0 : J.R.state == ST_PCG ? 2
                        : (J.R.state == ST_INIT || J.R.state == ST_RESID) ? 1 : 0;
@@ -808,6 +826,8 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
     const SysDesc& S = *J.S;
     SysScalars* sc = S.sc;
     const int state = J.R.state;
+    // two-level: this kernel writes z_b; the coarse kernels finish z and the scalars
+    const bool defer = S.precond == SSO_TWO_LEVEL && state != ST_FOLD;
     if (state != ST_DONE) {
       const int nn = J.nn;
       const size_t v0 = 6 * (size_t)J.node0;
@@ -883,7 +903,7 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
         }
         __syncwarp();
         store_run((float*)S.r + v0, Vr, 3 * nn, lane);
-        store_run((float*)S.z + v0, Vq, 3 * nn, lane);
+        store_run((float*)(defer ? S.zb : S.z) + v0, Vq, 3 * nn, lane);
         if (state == ST_PCG) store_run((float*)S.dx + v0, Vd, 3 * nn, lane);
       }
       // the stage is free for the copies of the tile after next
@@ -898,13 +918,13 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
       }
       // count the warp's tiles per chunk, flushing when the chunk or the run ends
       if (lt / CHUNK != pend_c) {
-        if (pend_n) b_count(S, sc, state, pend_c, pend_n, lane, n_active, true);
+        if (pend_n) b_count(S, sc, state, pend_c, pend_n, lane, n_active, true, defer);
         pend_c = lt / CHUNK;
         pend_n = 0;
       }
       ++pend_n;
       if (!(nxt < end && JN.sid == J.sid)) {
-        b_count(S, sc, state, pend_c, pend_n, lane, n_active, true);
+        b_count(S, sc, state, pend_c, pend_n, lane, n_active, true, defer);
         pend_c = -1;
         pend_n = 0;
       }
@@ -915,6 +935,175 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
   if (dry && lane == 0)
     for (int st = 0; st < 2; ++st)
       if (last_k[st] >= 0) mbar_wait(&full[w][st], (last_k[st] >> 1) & 1);
+}
+
+// ---------------------------------------------------------------------------
+// Coarse correction of the two-level preconditioner, after kernel B (which
+// wrote z_b = M_b^-1 r and left r^T z_b, r^T r):
+//   restriction   w = P^T r            one warp per (system, aggregate)
+//   coarse solve  y = A_c^-1 w          one CTA per system; r^T z = r^T z_b + w^T y,
+//                                       then the scalar update of kernel B
+//   prolongation  z = z_b + P y         one warp per tile, one thread per node
+// P's block at node i: u = t + theta x r_i, rotation theta (r_i: the node's
+// offset from its aggregate's centroid), zero on fixed DOFs.  FP32 vectors,
+// fixed-order warp trees, w^T y in FP64.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) coarse_restrict_kernel(const AggRef* __restrict__ aggs,
+                                                              int n_aggs,
+                                                              const SysDesc* __restrict__ sys) {
+  pdl_trigger();
+  pdl_wait();
+  const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (k >= n_aggs) return;
+  const AggRef a = aggs[k];
+  const SysDesc& S = sys[a.sys];
+  if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&S.sc->coarse_pending != 1) return;
+  const int b = S.agg_ptr[a.agg], e = S.agg_ptr[a.agg + 1];
+  const float* r = (const float*)S.r;
+  const float4* rf = reinterpret_cast<const float4*>(S.node_rf);
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  constexpr int U = 4;  // members per lane whose loads are in flight together
+  for (int q0 = b + lane; q0 < e; q0 += 32 * U) {
+    int idx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) idx[u] = q0 + 32 * u < e ? S.agg_nodes[q0 + 32 * u] : -1;
+    float4 o[U];
+    float v[U][6];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (idx[u] >= 0) {
+        o[u] = rf[idx[u]];
+        ld6rw(r + 6 * (size_t)idx[u], v[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (idx[u] >= 0) {
+        // B_i^T v: translations v_u; rotations o x v_u + v_theta
+        acc[0] += v[u][0];
+        acc[1] += v[u][1];
+        acc[2] += v[u][2];
+        acc[3] += fmaf(o[u].y, v[u][2], fmaf(-o[u].z, v[u][1], v[u][3]));
+        acc[4] += fmaf(o[u].z, v[u][0], fmaf(-o[u].x, v[u][2], v[u][4]));
+        acc[5] += fmaf(o[u].x, v[u][1], fmaf(-o[u].y, v[u][0], v[u][5]));
+      }
+  }
+#pragma unroll
+  for (int d = 0; d < 6; ++d) acc[d] = warp_sum_f(acc[d]);
+  if (lane == 0)
+#pragma unroll
+    for (int d = 0; d < 6; ++d) S.w[6 * a.agg + d] = acc[d];
+}
+
+// CTA (system, row block): COARSE_ROWS_PER_BLOCK rows of y = A_c^-1 w (two
+// rows per warp, the column loads of both in flight together) and that
+// block's w^T y; the CTA that completes the system's row blocks sums the
+// partials in block order and updates the scalars.
+__global__ void __launch_bounds__(256) coarse_solve_kernel(const int* __restrict__ csys,
+                                                           int n_csys,
+                                                           const SysDesc* __restrict__ sys,
+                                                           int* __restrict__ flags) {
+  __shared__ float ws[COARSE_MAX_N];
+  __shared__ double red[8];
+  __shared__ int s_last;
+  pdl_trigger();
+  pdl_wait();
+  const int si = blockIdx.x / COARSE_ROW_BLOCKS, rb = blockIdx.x - si * COARSE_ROW_BLOCKS;
+  const SysDesc& S = sys[csys[si]];
+  SysScalars* sc = S.sc;
+  if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&sc->coarse_pending != 1) return;
+  const int nc = 6 * S.n_agg;
+  const int row0 = rb * COARSE_ROWS_PER_BLOCK;
+  if (row0 >= nc) return;
+  const int n_blocks = (nc + COARSE_ROWS_PER_BLOCK - 1) / COARSE_ROWS_PER_BLOCK;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k = tid; k < nc; k += blockDim.x) ws[k] = S.w[k];
+  __syncthreads();
+  constexpr int CPL = (COARSE_MAX_N + 31) / 32;  // columns per lane
+  const int ra = row0 + 2 * warp, rbb = ra + 1;
+  float xa[CPL], xb[CPL];
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = lane + 32 * u;
+    xa[u] = (ra < nc && c < nc) ? S.Aci[(size_t)ra * nc + c] : 0.f;
+    xb[u] = (rbb < nc && c < nc) ? S.Aci[(size_t)rbb * nc + c] : 0.f;
+  }
+  float aa = 0.f, ab = 0.f;
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = lane + 32 * u;
+    const float wc = c < nc ? ws[c] : 0.f;
+    aa = fmaf(xa[u], wc, aa);
+    ab = fmaf(xb[u], wc, ab);
+  }
+  aa = warp_sum_f(aa);
+  ab = warp_sum_f(ab);
+  double dot = 0.0;
+  if (lane == 0) {
+    if (ra < nc) {
+      S.y[ra] = aa;
+      dot += (double)aa * (double)ws[ra];
+    }
+    if (rbb < nc) {
+      S.y[rbb] = ab;
+      dot += (double)ab * (double)ws[rbb];
+    }
+    red[warp] = dot;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double part = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part += red[k];
+    S.cdot[rb] = part;
+    __threadfence();
+    const unsigned prev = atomicAdd(&sc->coarse_cnt, 1u);
+    s_last = prev + 1u == (unsigned)n_blocks;
+  }
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  double wy = 0.0;
+  for (int k = 0; k < n_blocks; ++k) wy += __ldcg(S.cdot + k);
+  sc->coarse_cnt = 0u;
+  sc->coarse_pending = 0;
+  finish_b(sc, sc->state, sc->rz_b + wy, sc->rr_b, flags, true);
+}
+
+__global__ void __launch_bounds__(NT) coarse_prolong_kernel(const TileDesc* __restrict__ tiles,
+                                                            const int* __restrict__ n_tiles_ptr,
+                                                            const SysDesc* __restrict__ sys) {
+  pdl_trigger();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int begin, end;
+  tile_range(*n_tiles_ptr, begin, end);
+  pdl_wait();
+  for (int tile = begin + w; tile < end; tile += WARPS) {
+    const TileDesc& td = tiles[tile];
+    const SysDesc& S = sys[td.sys];
+    // after the coarse solve a system in CG needs z (a sweep that just began
+    // or one more iteration); FOLD and DONE do not
+    if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&S.sc->state != ST_PCG) continue;
+    if (lane >= td.nn) continue;
+    const int i = td.node0 + lane;
+    const int g = S.agg_of[i];
+    const float4 o = reinterpret_cast<const float4*>(S.node_rf)[i];
+    const float* y = S.y + 6 * g;
+    const float t0 = y[0], t1 = y[1], t2 = y[2], w0 = y[3], w1 = y[4], w2 = y[5];
+    // u = t + theta x o, rotation theta
+    float c[6] = {fmaf(w1, o.z, fmaf(-w2, o.y, t0)), fmaf(w2, o.x, fmaf(-w0, o.z, t1)),
+                  fmaf(w0, o.y, fmaf(-w1, o.x, t2)), w0, w1, w2};
+    const uint8_t* fx = S.fixed + 6 * (size_t)i;
+    float zb[6];
+    ld6rw((const float*)S.zb + 6 * (size_t)i, zb);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) zb[d] += fx[d] ? 0.f : c[d];
+    st6((float*)S.z + 6 * (size_t)i, zb);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1287,6 +1476,39 @@ cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
   cudaError_t e = b32_attributes();
   if (e != cudaSuccess) return e;
   return launch_cg_kernel(pcg_b32_kernel, grid, NT, B32_SMEM, s, tiles, n_tiles, sys, flags);
+}
+
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, int threads, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+cudaError_t launch_coarse_restrict(const AggRef* aggs, int n_aggs, const SysDesc* sys,
+                                   cudaStream_t s) {
+  if (n_aggs <= 0) return cudaSuccess;
+  return launch_pdl(coarse_restrict_kernel, (n_aggs + 7) / 8, 256, s, aggs, n_aggs, sys);
+}
+
+cudaError_t launch_coarse_solve(const int* csys, int n_csys, const SysDesc* sys, int* flags,
+                                cudaStream_t s) {
+  if (n_csys <= 0) return cudaSuccess;
+  return launch_pdl(coarse_solve_kernel, n_csys * COARSE_ROW_BLOCKS, 256, s, csys, n_csys, sys,
+                    flags);
+}
+
+cudaError_t launch_coarse_prolong(const TileDesc* tiles, const int* n_tiles, const SysDesc* sys,
+                                  int grid, cudaStream_t s) {
+  return launch_pdl(coarse_prolong_kernel, grid, NT, s, tiles, n_tiles, sys);
 }
 
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s) {

@@ -59,6 +59,11 @@ struct SysScalars {
   double inner_rtol2;
   int max_iter;
   int max_sweeps;
+  // two-level preconditioner: kernel B leaves r^T z_b and r^T r here and sets
+  // coarse_pending; the coarse kernel adds w^T y and updates the scalars
+  int coarse_pending;
+  unsigned int coarse_cnt;  // row blocks of the coarse solve done (last-block reduction)
+  double rz_b, rr_b;
 };
 
 // Static description of one tile of a batch (device memory, built once per
@@ -115,6 +120,20 @@ struct SysDesc {
   int n_chunks;
   unsigned* chunk_cnt;  // [2 * n_chunks]: tiles counted per chunk, kernel A then kernel B
   double* chunk_part;   // [4 * n_chunks]: two sums per chunk, kernel A then kernel B
+  // two-level preconditioner (precond == SSO_TWO_LEVEL, FP32 CG):
+  // z = z_b + P A_c^-1 P^T r with z_b the block-Jacobi part and P the rigid-body
+  // modes of each node aggregate
+  int n_agg;              // aggregates; the coarse problem has 6 n_agg unknowns
+  const int* agg_ptr;     // [n_agg + 1] node lists of the aggregates
+  const int* agg_nodes;   // [n_nodes]
+  const int* agg_of;      // [n_nodes]
+  const uint8_t* fixed;   // [6 n_nodes] 1 = fixed DOF
+  const float* node_rf;   // [n_nodes][4] node position minus its aggregate's centroid
+  const float* Aci;       // [6 n_agg][6 n_agg] inverse of the coarse matrix
+  float* w;               // [6 n_agg] P^T r
+  float* y;               // [6 n_agg] A_c^-1 w
+  double* cdot;           // [COARSE_ROW_BLOCKS] w^T y per row block of the coarse solve
+  void* zb;               // [6 n_nodes] z_b (FP32)
   SysScalars* sc;
 };
 
@@ -126,6 +145,15 @@ constexpr int CHUNK = 256;
 constexpr int CHUNK_PER_THREAD = 8;
 static_assert(CHUNK * WARPS == NT * CHUNK_PER_THREAD, "kernel-A chunk: 8 partials per thread");
 static_assert(CHUNK == 32 * CHUNK_PER_THREAD, "kernel-B chunk: 8 partials per lane");
+
+// Two-level preconditioner: at most this many node aggregates per system, so
+// the coarse problem (6 unknowns per aggregate, FP32) fits one CTA's shared
+// memory for its inversion.
+constexpr int COARSE_MAX_AGG = 39;
+constexpr int COARSE_MAX_N = 6 * COARSE_MAX_AGG;
+// The coarse solve y = A_c^-1 w of a system is split into row blocks, one CTA each.
+constexpr int COARSE_ROWS_PER_BLOCK = 16;
+constexpr int COARSE_ROW_BLOCKS = (COARSE_MAX_N + COARSE_ROWS_PER_BLOCK - 1) / COARSE_ROWS_PER_BLOCK;
 
 // Packed symmetric 6x6 (upper triangle by rows, 21 values, 3 zeros of
 // padding so that every node starts on a 16-byte boundary).
@@ -183,6 +211,27 @@ constexpr int STAGE_SLAB_C = 1280;       // column indices (bytes)
 constexpr int STAGE_SLAB_V = 6144;       // one vector halo (bytes)
 constexpr int STAGE_SLAB_R = 256;        // row_ptr run (bytes)
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
+// The coarse correction of the two-level preconditioner, after kernel B:
+// restriction (one warp per (system, aggregate) of `aggs`), coarse solve and
+// scalar update (one CTA per system of `csys`), prolongation (the tiles).
+struct AggRef {
+  int sys, agg;
+};
+cudaError_t launch_coarse_restrict(const AggRef* aggs, int n_aggs, const SysDesc* sys,
+                                   cudaStream_t s);
+cudaError_t launch_coarse_solve(const int* csys, int n_csys, const SysDesc* sys, int* flags,
+                                cudaStream_t s);
+cudaError_t launch_coarse_prolong(const TileDesc* tiles, const int* n_tiles, const SysDesc* sys,
+                                  int grid, cudaStream_t s);
+
+// Coarse set-up of one model (coarse.cu): aggregate geometry, Galerkin matrix
+// A_c = P^T K P (FP64, dense [6 n_agg]^2), its FP32 inverse.
+cudaError_t launch_coarse_setup(int n_nodes, int n_agg, int n_blocks, const int* agg_ptr,
+                                const int* agg_nodes, const int* brow, const int* col,
+                                const int* cg_ptr, const int* cg_src, const double* xyz,
+                                const uint8_t* fixed, const double* K64, double* node_r64,
+                                float* node_rf, double* T, double* Ac, float* Aci,
+                                cudaStream_t s);
 
 // Launchers (spmv.cu): y = K x, *xty = x^T y; partials [ceil(n_nodes/TILE)],
 // counter must be 0 on entry and is 0 again on exit.

@@ -39,7 +39,7 @@ def _stream_ptr(stream):
 def options(**kw):
     """sso_options with the library defaults, overridden by keyword.
 
-    precision: "fp32_ir" | "fp64"; precond: "block_jacobi" | "jacobi"; and the
+    precision: "fp32_ir" | "fp64"; precond: "block_jacobi" | "jacobi" | "two_level"; and the
     numeric fields of ``sso_options``.
     """
     lib = _lib.load()
@@ -49,7 +49,8 @@ def options(**kw):
         if k == "precision":
             v = {"fp64": _lib.FP64, "fp32_ir": _lib.FP32_IR}.get(v, v)
         elif k == "precond":
-            v = {"jacobi": _lib.JACOBI, "block_jacobi": _lib.BLOCK_JACOBI}.get(v, v)
+            v = {"jacobi": _lib.JACOBI, "block_jacobi": _lib.BLOCK_JACOBI,
+                 "two_level": _lib.TWO_LEVEL}.get(v, v)
         if not hasattr(o, k):
             raise TypeError("unknown option %r" % k)
         setattr(o, k, v)
@@ -247,13 +248,16 @@ class Batch:
 
     def setup_times(self):
         """Device ms since profiling was enabled: dict with elements, assembly,
-        precond (+ loads), adjoint (contraction pass), setups, gradients."""
-        v = [ctypes.c_double() for _ in range(4)]
+        precond (+ loads) summed per model, setup_wall (elapsed time of the
+        concurrent set-ups), adjoint (elapsed contraction passes), setups,
+        gradients."""
+        v = [ctypes.c_double() for _ in range(5)]
         n = [ctypes.c_int64() for _ in range(2)]
         _lib.check(_lib.load().sso_batch_setup_times(self._h, *[ctypes.byref(x) for x in v],
                                                      *[ctypes.byref(x) for x in n]))
         return {"elements": v[0].value, "assembly": v[1].value, "precond": v[2].value,
-                "adjoint": v[3].value, "setups": n[0].value, "gradients": n[1].value}
+                "adjoint": v[3].value, "setup_wall": v[4].value, "setups": n[0].value,
+                "gradients": n[1].value}
 
     def gradient(self, w=None, g=None, raise_on_error=True):
         n = len(self.models)

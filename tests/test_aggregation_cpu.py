@@ -36,9 +36,9 @@ def test_aggregates_partition_connected(sso, mesh):
     n = m["xyz"].shape[0]
     agg, n_agg = sso.aggregate(m)
     assert agg.shape == (n,) and agg.min() == 0 and agg.max() == n_agg - 1
-    target = max(16, -(-n // 80))
+    target = max(16, -(-n // 39))
     sizes = np.bincount(agg, minlength=n_agg)
-    assert n_agg <= 2 * 80 and sizes.min() >= 1
+    assert n_agg <= 39 and sizes.min() >= 1
     assert sizes.min() * 4 >= target or n_agg == 1
     adj = _adjacency(m)
     for g in range(n_agg):  # breadth-first search inside the aggregate reaches all of it

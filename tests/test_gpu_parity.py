@@ -255,6 +255,55 @@ def test_autograd_function(sso, orc):
     assert rel(t.grad.cpu().numpy(), ref["dt"] + 0.3 * vol["dt"]) <= TOL_FP64
 
 
+@pytest.mark.parametrize("name", ["shell5", "mixed", "gridshell13", "shell9_clamped"])
+def test_two_level_preconditioner_parity(sso, orc, name):
+    """Block-Jacobi plus the rigid-body coarse correction: the same solution
+    and gradient as the oracle (the preconditioner changes only the path)."""
+    m = MODELS[name]()
+    ref = orc.gradient(m)
+    mdl = sso.Model(m)
+    st = mdl.solve(precision="fp32_ir", precond="two_level", rtol=1e-9)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-9
+    mdl.gradient(1.0)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= TOL_FP32_IR
+    assert abs(r["C"] - ref["C"]) <= TOL_FP32_IR * abs(ref["C"])
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP32_IR
+
+
+def test_two_level_cuts_iterations(sso, orc):
+    m = meshgen.shell(n_el=24, span=20.0, seed=1)
+    its = {}
+    for pc in ("block_jacobi", "two_level"):
+        mdl = sso.Model(m)
+        st = mdl.solve(precision="fp32_ir", precond=pc, rtol=1e-8)
+        assert st["status"] == 0
+        its[pc] = st["iterations"]
+    assert its["two_level"] * 3 < its["block_jacobi"], its
+    ref = orc.gradient(m)
+    assert rel(mdl.result()["u"], ref["u"]) <= TOL_FP32_IR
+
+
+def test_two_level_batch_equals_alone_bitwise(sso):
+    meshes = [small_shell(5), meshgen.gridshell(n_side=12, seed=2), meshgen.shell(n_el=7, seed=3)]
+    opts = sso.options(precision="fp32_ir", precond="two_level", rtol=1e-8)
+    alone = []
+    for m in meshes:
+        mdl = sso.Model(m)
+        mdl.solve(opts)
+        alone.append(mdl.result()["u"])
+    batch = sso.Batch([sso.Model(m) for m in meshes])
+    batch.solve(opts)
+    for a, mdl in zip(alone, batch.models):
+        assert np.array_equal(a, mdl.result()["u"])
+
+
+def test_two_level_needs_fp32_ir(sso):
+    mdl = sso.Model(small_shell(4))
+    with pytest.raises(sso.SSOError):
+        mdl.solve(precision="fp64", precond="two_level")
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("fp32_ir", TOL_FP32_IR)])
 @pytest.mark.parametrize("name", ["shell5", "mixed"])
 def test_simp_topology_gradient(sso, orc, name, precision, tol):
