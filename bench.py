@@ -55,11 +55,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="shell",
-                   choices=["shell", "serving", "gridshell", "large", "training"],
+                   choices=["shell", "serving", "gridshell", "large", "training", "bridge"],
                    help="shell: batches of 64x64 shell designs (default line); serving: "
                         "continuous batching of a grid-shell request stream; gridshell: "
                         "latency of one 10x10 grid-shell evaluation; large: one 512x512 shell; "
-                        "training: MLP through 64 batched 48x48 shell solves per step")
+                        "training: MLP through 64 batched 48x48 shell solves per step; "
+                        "bridge: FEA and sensitivity time of the 100-span arch bridge vs DOF")
+    p.add_argument("--el-per-span", default="2,6,10,20,30,80,1500,2500,4500,6500",
+                   help="bridge workload: elements per span of the 100-span arch bridge")
     p.add_argument("--requests", type=int, default=512, help="serving: requests per run")
     p.add_argument("--rates", default="0.5,0.9",
                    help="serving: Poisson arrival rates as fractions of saturated throughput")
@@ -415,6 +418,110 @@ def run_gridshell(a):
     print(json.dumps(line), flush=True)
 
 
+def run_bridge(a):
+    """The beam-path scaling structure: a 100-span bridge of 30 m x 10 m
+    parabolic arches (Sec. 2.2.4), el_per_span elements per span (1,206 DOF at
+    2 up to 3,900,006 DOF at 6,500).  For each size: FEA (set design, solve,
+    C) and sensitivity analysis (FEA + adjoint dC/dz of every node), medians
+    of 3 runs after a warm-up, with the direct block-tridiagonal solver
+    (SSO_CHAIN, FP64) and, up to 60 k DOF, FP64 block-Jacobi CG to a relative
+    residual of 1e-10.  The oracle's band Cholesky (1 thread) is timed at every
+    size (its sensitivity analysis up to 60 k DOF) as the CPU baseline, and its
+    residual shows the FP64 floor of each size: with 30 m spans cut into
+    elements of a few mm, cond(K) nears 1/eps and no FP64 solve reaches a
+    1e-10 residual (status 4 then reports the solve above rtol)."""
+    torch, sso, local = _gpu_setup()
+    sizes = [int(k) for k in a.el_per_span.split(",") if k]
+    chain = sso.options(precision="fp64", precond="chain", rtol=1e-10, max_sweeps=3)
+    cg = sso.options(precision="fp64", precond="block_jacobi", rtol=1e-10,
+                     iters_per_launch=64, max_iter=4_000_000)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sso.kernel_launches()
+    rows = []
+
+    def timed(mdl, z, opts):
+        mdl.set_design(z)
+        mdl.solve(opts, raise_on_error=False)
+        mdl.gradient()
+        mdl.result()
+        fea, sens = [], []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mdl.set_design(z)
+            st = mdl.solve(opts, raise_on_error=False)
+            C = mdl.result()["C"]
+            fea.append(1000 * (time.perf_counter() - t0))
+            t0 = time.perf_counter()
+            mdl.set_design(z)
+            mdl.solve(opts, raise_on_error=False)
+            mdl.gradient()
+            r = mdl.result()
+            sens.append(1000 * (time.perf_counter() - t0))
+        return st, r, float(np.median(fea)), float(np.median(sens))
+
+    for k in sizes:
+        m = meshgen.arch_bridge(el_per_span=k)
+        z = np.ascontiguousarray(m["xyz"][:, 2])
+        mdl = sso.Model(m)
+        st, r, fea, sens = timed(mdl, z, chain)
+        row = {"el_per_span": k, "dof": 6 * m["xyz"].shape[0],
+               "direct": {"fea_ms": fea, "sensitivity_ms": sens,
+                          "rel_residual": st["rel_residual"], "refinements": st["sweeps"],
+                          "status": st["status"]},
+               "C": float(r["C"])}
+        if not a.no_cpu_baseline:
+            # the oracle's FP64 band Cholesky: time and residual floor at every size
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            u_o, C_o = oracle.solve(m)
+            row["oracle_fea_ms"] = 1000 * (time.perf_counter() - t0)
+            f_o = oracle.load_vector(m)
+            f_o[m["fixed"].ravel().astype(bool)] = 0.0
+            row["oracle_rel_residual"] = float(np.linalg.norm(oracle.residual(m, u_o)) /
+                                               np.linalg.norm(f_o))
+            row["direct_rel_diff_C_vs_oracle"] = abs(row["C"] - C_o) / abs(C_o)
+        if row["dof"] <= 60_000:
+            st2, r2, fea2, sens2 = timed(mdl, z, cg)
+            row["cg"] = {"fea_ms": fea2, "sensitivity_ms": sens2, "iterations": st2["iterations"],
+                         "rel_residual": st2["rel_residual"],
+                         "rel_diff_u_vs_direct": float(np.linalg.norm(r2["u"] - r["u"]) /
+                                                       np.linalg.norm(r["u"]))}
+            if not a.no_cpu_baseline:
+                import oracle
+                oracle.build()
+                t0 = time.perf_counter()
+                ref = oracle.gradient(m)
+                row["oracle_sensitivity_ms"] = 1000 * (time.perf_counter() - t0)
+                row["direct_rel_err_vs_oracle"] = {
+                    "u": float(np.linalg.norm(r["u"] - ref["u"]) / np.linalg.norm(ref["u"])),
+                    "dz": float(np.linalg.norm(r["dz"] - ref["dz"]) / np.linalg.norm(ref["dz"]))}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        del mdl
+    launches = sso.kernel_launches() - l0
+    clk = clocks.stop()
+    big = rows[-1]
+    line = {
+        "metric": "sensitivity analyses/s of the 100-span arch bridge (FEA + adjoint dC/dz)",
+        "value": 1000.0 / big["direct"]["sensitivity_ms"], "unit": "evals/s", "n_gpus": 1,
+        "steps": 3 * len(rows), "warmup": 1, "ms_per_step": big["direct"]["sensitivity_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "100-span arch bridge, %s elements per span; direct "
+                               "block-tridiagonal solve (FP64); value at the largest size"
+                               % a.el_per_span},
+        "sizes": rows, "roofline": None, "clocks": clk, "gpu_launches": int(launches),
+        "e2e": {"value": 1000.0 / big["direct"]["sensitivity_ms"], "unit": "evals/s",
+                "h2d_bytes_per_step": 8 * big["dof"] // 6,
+                "d2h_bytes_per_step": 8 * (big["dof"] + big["dof"] // 6 + 1),
+                "note": "every run uploads z from host and reads u, C, dz back"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_large(a):
     """One large shell: 512 x 512 quads (263,169 nodes, 1,579,014 DOF), all
     edges clamped, 5 kPa pressure; FP32 Jacobi CG with FP64 refinement to a
@@ -568,7 +675,7 @@ def run_training(a):
 
 def run_workload(a):
     {"serving": run_serving, "gridshell": run_gridshell, "large": run_large,
-     "training": run_training}[a.workload](a)
+     "training": run_training, "bridge": run_bridge}[a.workload](a)
 
 
 def main():

@@ -78,8 +78,19 @@ typedef struct {
 typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1 } sso_precision;
 /* SSO_TWO_LEVEL: block-Jacobi plus a coarse correction over the rigid-body
  * modes of node aggregates (z = M_b^-1 r + P A_c^-1 P^T r, A_c = P^T K P);
- * FP32_IR only, batches and models (not the server). */
-typedef enum { SSO_JACOBI = 0, SSO_BLOCK_JACOBI = 1, SSO_TWO_LEVEL = 2 } sso_precond;
+ * FP32_IR only, batches and models (not the server).
+ * SSO_CHAIN: no CG: K u = f is solved exactly by block cyclic reduction in
+ * FP64 (K factored once per assembly, every solve and adjoint solve reusing
+ * the factors).  Only for a block-tridiagonal K, i.e. every element joins
+ * nodes numbered consecutively (a chain of beam-columns: arches, multi-span
+ * bridges, cantilevers); other models return SSO_ERR_INVALID.  FP64 only;
+ * batches and models (not the server).  While the FP64 residual is above
+ * rtol the solution is refined with the same factors (u += K^-1 (f - K u)),
+ * up to max_sweeps times or until the residual stops falling; the stats
+ * report 0 CG iterations, the refinements as sweeps, and the residual. */
+typedef enum {
+  SSO_JACOBI = 0, SSO_BLOCK_JACOBI = 1, SSO_TWO_LEVEL = 2, SSO_CHAIN = 3
+} sso_precond;
 
 /* Solver options.  Convergence is ||f - K u||_2 <= rtol ||f||_2 over all DOFs,
  * with the residual recomputed in FP64 from the FP64 K. */

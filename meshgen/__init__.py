@@ -284,6 +284,39 @@ def arch2d(n_el: int = 99, span: float = 10.0, rise: float = 5.0, E: float = 1.9
     return model
 
 
+def arch_bridge(n_spans: int = 100, el_per_span: int = 2, span: float = 30.0,
+                rise: float = 10.0, E: float = 2.0e11, nu: float = 0.3, A: float = 4.3e-3,
+                Iy: float = 6.6e-5, Iz: float = 3.3e-6, unit_weight: float = 7.85e4) -> dict:
+    """Multi-span bridge of 2D parabolic arches of beam-columns in the XZ plane
+    (the scaling structure of Sec. 2.2.4): n_spans arches of span x rise
+    placed end to end along X, each cut into el_per_span equal-plan-length
+    elements; consecutive arches share their pier node.  Every pier is a pin
+    with the support vector of Listing 1 (ux, uy, uz, rx, rz fixed, ry free).
+    Loads: self-weight as downward nodal loads, unit_weight * A times half the
+    length of each element touching a node.  6 (n_spans el_per_span + 1) DOF:
+    1,206 for 100 spans of 2 elements, about 3.9 million for 6,500.
+    """
+    n_el = n_spans * el_per_span
+    n_nodes = n_el + 1
+    x = np.arange(n_nodes) * (span / el_per_span)
+    xi = (np.arange(n_nodes) % el_per_span) / el_per_span  # position within the span
+    z = 4.0 * rise * xi * (1.0 - xi)
+    model = empty_model(n_nodes)
+    model["xyz"] = np.stack([x, np.zeros_like(x), z], axis=1)
+    conn = np.stack([np.arange(n_el), np.arange(1, n_nodes)], axis=1).astype(np.int32)
+    G = E / (2.0 * (1.0 + nu))
+    model["beam_conn"] = conn
+    model["beam_props"] = np.tile(np.array([E, G, Iy, Iz, Iy + Iz, A]), (n_el, 1))
+    piers = np.arange(0, n_nodes, el_per_span)
+    model["fixed"][piers] = (1, 1, 1, 1, 0, 1)
+    length = np.linalg.norm(np.diff(model["xyz"], axis=0), axis=1)
+    w = np.zeros(n_nodes)
+    w[:-1] += 0.5 * length
+    w[1:] += 0.5 * length
+    model["nodal_load"][:, 2] = -unit_weight * A * w
+    return model
+
+
 def barrel_arch(n_el: int = 20, span: float = 19.0, rise: float = 4.5, E: float = 1.99e8,
                 nu: float = 0.2, t: float = 0.25, load: float = -500e3) -> dict:
     """Parabolic barrel arch of quads (Sec. 2.2.3): parabola along X, extruded

@@ -25,6 +25,7 @@ FP32_IR = 1
 JACOBI = 0
 BLOCK_JACOBI = 1
 TWO_LEVEL = 2
+CHAIN = 3
 
 
 class SSOError(RuntimeError):

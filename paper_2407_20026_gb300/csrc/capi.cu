@@ -131,6 +131,10 @@ struct HostTopo {
   // the K blocks (i, j) with i in g and j in h, in block order
   int n_agg = 0;
   std::vector<int> agg_of, agg_ptr, agg_nodes, cg_ptr, cg_src;
+  // block (i, i+1) of every node or -1, and whether every block lies within
+  // one of the diagonal (a chain)
+  std::vector<int> chain_up;
+  bool is_chain = false;
 };
 
 }  // namespace
@@ -174,6 +178,12 @@ struct sso_model {
   double* d_zb;
   bool has_topology = false;
   double penal = 1.0;
+  // SSO_CHAIN: the pattern is block-tridiagonal; workspace of the factors
+  // (allocated on first use), assembly count when they were formed
+  bool is_chain = false;
+  int* d_chain_up;        // [n_nodes] block (i, i+1) or -1
+  double* d_chain_ws = nullptr;
+  long long assembly_gen = 0, chain_gen = -1;
   int* d_err;
   bool assembled = false, solved = false;
   int assembled_precond = -1;
@@ -556,6 +566,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_agg_nodes = c.take<int>(n);
   M->d_cg_ptr = c.take<int>(na * na + 1);
   M->d_cg_src = c.take<int>(M->n_blocks);
+  M->d_chain_up = c.take<int>(n);
   // element blocks; after assembly also the Galerkin block products
   M->d_ke = c.take<double>((size_t)std::max(M->n_eb, M->n_blocks) * 36);
   M->d_fslot = c.take<double>(M->n_slots);
@@ -604,10 +615,14 @@ sso_status check_options(const sso_options* o) {
   if (!o) return fail(SSO_ERR_INVALID, "options is NULL");
   if (o->precision != SSO_FP64 && o->precision != SSO_FP32_IR)
     return fail(SSO_ERR_INVALID, "precision must be SSO_FP64 or SSO_FP32_IR");
-  if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI && o->precond != SSO_TWO_LEVEL)
-    return fail(SSO_ERR_INVALID, "precond must be SSO_JACOBI, SSO_BLOCK_JACOBI or SSO_TWO_LEVEL");
+  if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI && o->precond != SSO_TWO_LEVEL &&
+      o->precond != SSO_CHAIN)
+    return fail(SSO_ERR_INVALID,
+                "precond must be SSO_JACOBI, SSO_BLOCK_JACOBI, SSO_TWO_LEVEL or SSO_CHAIN");
   if (o->precond == SSO_TWO_LEVEL && o->precision != SSO_FP32_IR)
     return fail(SSO_ERR_INVALID, "SSO_TWO_LEVEL needs SSO_FP32_IR");
+  if (o->precond == SSO_CHAIN && o->precision != SSO_FP64)
+    return fail(SSO_ERR_INVALID, "SSO_CHAIN needs SSO_FP64");
   if (!(o->rtol > 0.0) || !(o->inner_rtol >= 0.0) || o->inner_rtol >= 1.0)
     return fail(SSO_ERR_INVALID, "need rtol > 0 and 0 <= inner_rtol < 1");
   if (o->max_iter <= 0 || o->max_sweeps <= 0)
@@ -661,6 +676,7 @@ sso_status setup_model(sso_model* M, int precond, cudaStream_t s,
   if (ev) CK(cudaEventRecord(ev[3], s));
   M->assembled = true;
   M->assembled_precond = precond;
+  ++M->assembly_gen;
   return SSO_OK;
 }
 
@@ -782,8 +798,87 @@ sso_status accumulate_profile(sso_batch* B, int iters) {
 
 // Runs the batched CG over the systems with active[s] != 0, solving
 // K x = b with b = (adjoint ? rhs : f), x = (adjoint ? lam : u).
+// SSO_CHAIN: every active system solved directly (factors formed once per
+// assembly); while its FP64 residual is above rtol, refined with the same
+// factors (x += K^-1 (b - K x)), at most max_sweeps times or until the
+// residual stops falling.
+sso_status chain_run(sso_batch* B, const sso_options* o, bool adjoint,
+                     const std::vector<char>& active, sso_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<double> norms(2 * (size_t)B->n_sys, 0.0);
+  std::vector<int> sweeps(B->n_sys, 0);
+  for (int s = 0; s < B->n_sys; ++s) {
+    sso_model* M = B->models[s];
+    SysDesc& D = B->h_sys[s];
+    D.precond = o->precond;
+    D.b = adjoint ? M->d_rhs : M->d_f;
+    D.x = adjoint ? M->d_lam : M->d_u;
+    if (!active[s]) continue;
+    if (!M->is_chain)
+      return fail(SSO_ERR_INVALID, "SSO_CHAIN needs a block-tridiagonal K (every element joining "
+                                   "consecutively numbered nodes)");
+    const int n = M->n_nodes;
+    if (!M->d_chain_ws) {
+      const size_t bytes = sizeof(double) * (chain_workspace_doubles(n) + residual_partials(n) + 2);
+      cudaError_t e = cudaMalloc(&M->d_chain_ws, bytes);
+      if (e != cudaSuccess) {
+        M->d_chain_ws = nullptr;
+        return cuda_fail(e, "cudaMalloc(chain workspace)");
+      }
+    }
+    double* part = M->d_chain_ws + chain_workspace_doubles(n);
+    double* out = part + residual_partials(n);
+    if (M->chain_gen != M->assembly_gen) {
+      CL(launch_chain_factor(n, M->d_diag, M->d_chain_up, M->d_K64, M->d_chain_ws, M->d_err,
+                             B->stream),
+         1);
+      M->chain_gen = M->assembly_gen;
+    }
+    CL(launch_chain_solve(n, M->d_chain_ws, D.b, D.x, M->d_err, B->stream), 1);
+    double prev = HUGE_VAL;
+    for (;;) {
+      CL(launch_residual_norms(n, M->d_row_ptr, M->d_col, M->d_K64, D.x, D.b, M->d_r64, part, out,
+                               B->stream),
+         2);
+      CK(cudaMemcpyAsync(&norms[2 * (size_t)s], out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                         B->stream));
+      CK(cudaStreamSynchronize(B->stream));
+      const double rr = norms[2 * (size_t)s], bb = norms[2 * (size_t)s + 1];
+      if (!(rr > o->rtol * o->rtol * bb) || !(rr < 0.25 * prev) || sweeps[s] >= o->max_sweeps)
+        break;
+      prev = rr;
+      ++sweeps[s];
+      CL(launch_chain_solve(n, M->d_chain_ws, M->d_r64, M->d_dx, M->d_err, B->stream), 1);
+      CL(launch_axpby(6 * n, 1.0, M->d_dx, D.x, M->d_fixed, D.x, B->stream), 1);
+    }
+  }
+  CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * B->n_sys,
+                     cudaMemcpyHostToDevice, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  sso_status first_bad = SSO_OK;
+  for (int s = 0; s < B->n_sys; ++s) {
+    if (!active[s]) continue;
+    const double rr = norms[2 * (size_t)s], bb = norms[2 * (size_t)s + 1];
+    const bool ok = std::isfinite(rr) && rr <= o->rtol * o->rtol * bb;
+    const sso_status st = ok ? SSO_OK : SSO_ERR_NOT_CONVERGED;
+    if (st != SSO_OK && first_bad == SSO_OK) first_bad = st;
+    if (stats) {
+      stats[s].status = st;
+      stats[s].iterations = 0;
+      stats[s].sweeps = sweeps[s];
+      stats[s].rel_residual = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+      stats[s].ms = ms;
+    }
+  }
+  if (first_bad != SSO_OK) g_last_error = "direct chain solve above rtol (loss of accuracy)";
+  return first_bad;
+}
+
 sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
                      const std::vector<char>& active, sso_stats* stats) {
+  if (o->precond == SSO_CHAIN) return chain_run(B, o, adjoint, active, stats);
   const auto t0 = std::chrono::steady_clock::now();
   const bool fp64 = o->precision == SSO_FP64;
   const double inner = fp64 ? 0.0 : o->inner_rtol;
@@ -1027,9 +1122,21 @@ sso_status prepare_model(ModelPrep& P) {
     std::vector<int> fillp(Tm.cg_ptr.begin(), Tm.cg_ptr.end() - 1);
     for (int b = 0; b < nb; ++b) Tm.cg_src[fillp[key[b]]++] = b;
   }
+  {
+    const int n = hm.n_nodes;
+    Tm.chain_up.assign(n, -1);
+    Tm.is_chain = true;
+    for (int i = 0; i < n; ++i)
+      for (int b = Tm.row_ptr[i]; b < Tm.row_ptr[i + 1]; ++b) {
+        const int j = Tm.col[b];
+        if (j > i + 1 || j < i - 1) Tm.is_chain = false;
+        if (j == i + 1) Tm.chain_up[i] = b;
+      }
+  }
   const HostTopo& T = P.T;
   sso_model* M = new sso_model();
   P.M = M;
+  M->is_chain = T.is_chain;
   M->n_agg = T.n_agg;
   M->n_nodes = hm.n_nodes;
   M->n_beams = hm.n_beams;
@@ -1072,6 +1179,7 @@ sso_status prepare_model(ModelPrep& P) {
   put(M->d_agg_nodes, T.agg_nodes.data(), T.agg_nodes.size() * 4);
   put(M->d_cg_ptr, T.cg_ptr.data(), T.cg_ptr.size() * 4);
   put(M->d_cg_src, T.cg_src.data(), T.cg_src.size() * 4);
+  put(M->d_chain_up, T.chain_up.data(), T.chain_up.size() * 4);
   {
     std::vector<double> e0(hm.n_quads), one(hm.n_quads, 1.0);
     for (int e = 0; e < hm.n_quads; ++e) e0[e] = hm.quad_props[5 * (size_t)e + 1];
@@ -1224,6 +1332,7 @@ void sso_model_destroy(sso_model* M) {
   if (M->self_batch) sso_batch_destroy(M->self_batch);
   if (M->stream) cudaStreamSynchronize(M->stream);
   if (M->arena && M->own_arena) cudaFree(M->arena);
+  if (M->d_chain_ws) cudaFree(M->d_chain_ws);
   if (M->ev_in) cudaEventDestroy(M->ev_in);
   if (M->ev_out) cudaEventDestroy(M->ev_out);
   if (M->stream) cudaStreamDestroy(M->stream);
@@ -2066,8 +2175,9 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
   *out = nullptr;
   sso_status st = check_options(opts);
   if (st != SSO_OK) return st;
-  if (opts->precond == SSO_TWO_LEVEL)
-    return fail(SSO_ERR_INVALID, "the server does not run SSO_TWO_LEVEL");
+  if (opts->precond == SSO_TWO_LEVEL || opts->precond == SSO_CHAIN)
+    return fail(SSO_ERR_INVALID, "the server runs the CG preconditioners only (not SSO_TWO_LEVEL "
+                                 "or SSO_CHAIN)");
   if (max_systems <= 0 || max_tiles <= 0 || hbm_budget_bytes == 0)
     return fail(SSO_ERR_INVALID, "need max_systems > 0, max_tiles > 0, budget > 0");
   sso_server* S = new sso_server();

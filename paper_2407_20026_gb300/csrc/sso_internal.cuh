@@ -233,6 +233,21 @@ cudaError_t launch_coarse_setup(int n_nodes, int n_agg, int n_blocks, const int*
                                 float* node_rf, double* T, double* Ac, float* Aci,
                                 cudaStream_t s);
 
+// Direct solve of a block-tridiagonal K by block cyclic reduction (chain.cu).
+// ws: chain_workspace_doubles(n) doubles; up[i]: index of block (i, i+1) in
+// the BSR arrays or -1; err set on a non-positive pivot.
+size_t chain_workspace_doubles(int n);
+cudaError_t launch_chain_factor(int n, const int* diag, const int* up, const double* K64,
+                                double* ws, int* err, cudaStream_t s);
+cudaError_t launch_chain_solve(int n, double* ws, const double* b, double* x, int* err,
+                               cudaStream_t s);
+// r = b - K64 x (if r is not NULL), out[0] = ||r||^2, out[1] = ||b||^2 (FP64,
+// fixed order); part: residual_partials(n) doubles of scratch.
+size_t residual_partials(int n);
+cudaError_t launch_residual_norms(int n, const int* row_ptr, const int* col, const double* K64,
+                                  const double* x, const double* b, double* r, double* part,
+                                  double* out, cudaStream_t s);
+
 // Launchers (spmv.cu): y = K x, *xty = x^T y; partials [ceil(n_nodes/TILE)],
 // counter must be 0 on entry and is 0 again on exit.
 cudaError_t launch_bsr_spmv(int n_nodes, const int* row_ptr, const int* col, const double* K,

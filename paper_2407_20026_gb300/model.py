@@ -39,7 +39,7 @@ def _stream_ptr(stream):
 def options(**kw):
     """sso_options with the library defaults, overridden by keyword.
 
-    precision: "fp32_ir" | "fp64"; precond: "block_jacobi" | "jacobi" | "two_level"; and the
+    precision: "fp32_ir" | "fp64"; precond: "block_jacobi" | "jacobi" | "two_level" | "chain"; and the
     numeric fields of ``sso_options``.
     """
     lib = _lib.load()
@@ -50,7 +50,7 @@ def options(**kw):
             v = {"fp64": _lib.FP64, "fp32_ir": _lib.FP32_IR}.get(v, v)
         elif k == "precond":
             v = {"jacobi": _lib.JACOBI, "block_jacobi": _lib.BLOCK_JACOBI,
-                 "two_level": _lib.TWO_LEVEL}.get(v, v)
+                 "two_level": _lib.TWO_LEVEL, "chain": _lib.CHAIN}.get(v, v)
         if not hasattr(o, k):
             raise TypeError("unknown option %r" % k)
         setattr(o, k, v)
@@ -146,10 +146,12 @@ class Model:
         _lib.check(_lib.load().sso_model_get_topology_gradient(self._h, ptr))
         return out
 
-    def solve(self, opts=None, **kw):
+    def solve(self, opts=None, raise_on_error=True, **kw):
         o = opts if opts is not None else options(**kw)
         st = _lib.Stats()
-        _lib.check(_lib.load().sso_model_solve(self._h, ctypes.byref(o), ctypes.byref(st)))
+        code = _lib.load().sso_model_solve(self._h, ctypes.byref(o), ctypes.byref(st))
+        if raise_on_error:
+            _lib.check(code)
         self.last_stats = st.as_dict()
         return self.last_stats
 
