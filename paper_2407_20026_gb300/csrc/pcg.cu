@@ -731,11 +731,19 @@ struct BJob {
   int kind;  // 2: PCG (M and four vectors staged), 1: INIT / RESID (M staged), 0: none
 };
 
-__device__ __forceinline__ BJob make_bjob(const TileDesc* __restrict__ tiles,
-                                          const SysDesc* __restrict__ sys, int tile,
-                                          const BJob* prev) {
-  BJob J;
+// The fields of a tile descriptor a warp of kernel B needs, loaded a tile
+// ahead of their use.
+struct BTile {
+  int sys, node0, nn;
+};
+__device__ __forceinline__ BTile load_btile(const TileDesc* __restrict__ tiles, int tile) {
   const TileDesc& td = tiles[tile];
+  return BTile{td.sys, td.node0, td.nn};
+}
+
+__device__ __forceinline__ BJob make_bjob(const BTile& td, const SysDesc* __restrict__ sys,
+                                          int tile, const BJob* prev) {
+  BJob J;
   J.tile = tile;
   J.sid = td.sys;
   J.node0 = td.node0;
@@ -801,17 +809,20 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
   int k = 0, pend_c = -1, pend_n = 0, last_k[2] = {-1, -1};
   bool dry = false;
   BJob J;
+  BTile pf;  // descriptor of the warp's tile after next
   if (begin + w < end) {
-    J = make_bjob(tiles, sys, begin + w, nullptr);
+    J = make_bjob(load_btile(tiles, begin + w), sys, begin + w, nullptr);
     if (lane == 0) issue_bjob(J, stages, &full[w][0]);
     last_k[0] = 0;
+    if (begin + w + WARPS < end) pf = load_btile(tiles, begin + w + WARPS);
   }
   for (int tile = begin + w; tile < end; tile += WARPS, ++k) {
     const int s = k & 1;
     const int nxt = tile + WARPS;
     BJob JN;
     if (nxt < end) {
-      JN = make_bjob(tiles, sys, nxt, &J);
+      JN = make_bjob(pf, sys, nxt, &J);
+      if (nxt + WARPS < end) pf = load_btile(tiles, nxt + WARPS);
       if (dry) JN.kind = 0;
       if (lane == 0) issue_bjob(JN, stages + (s ^ 1) * B32_STAGE, &full[w][s ^ 1]);
       last_k[s ^ 1] = k + 1;
@@ -1159,6 +1170,7 @@ struct StageInfo {
   int state, mode, first, parity;  // mode 1: the tile's data is in the stage
   float beta;
   int sys, node0, nn, j0, cb, rb;
+  int run_end;  // the next tile of the CTA's range belongs to another system (or there is none)
   // halo runs in the stage: column c sits at slot c + shift[k] (nodes) for the
   // last run k whose first node is <= c (first nodes of unused runs: INT_MAX)
   int v1, v2, sh0, sh1, sh2;
@@ -1194,13 +1206,18 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     int cur = -1, issued = 0;
     RunState R;
     R.state = ST_DONE;
+    // each tile's descriptor is loaded one tile ahead, so that its latency
+    // overlaps the wait for a free stage
+    TileDesc td_next;
+    if (begin < end) td_next = tiles[begin];
     for (int tile = begin, k = 0; tile < end; ++tile, ++k) {
       const int s = k % ST_STAGES, use = k / ST_STAGES;
+      const TileDesc td = td_next;
+      if (tile + 1 < end) td_next = tiles[tile + 1];
       if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
         atomicExch(flags + 1, 1);
         break;
       }
-      const TileDesc td = tiles[tile];
       const SysDesc* S = sys + td.sys;
       if (td.sys != cur) {
         cur = td.sys;
@@ -1218,6 +1235,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.j0 = td.j0;
       inf.cb = td.cb;
       inf.rb = td.rb;
+      inf.run_end = tile + 1 >= end || td_next.sys != td.sys;
       inf.v1 = td.nv[1] ? td.vlo[1] : INT_MAX;
       inf.v2 = td.nv[2] ? td.vlo[2] : INT_MAX;
       inf.sh0 = -td.vlo[0];
@@ -1284,6 +1302,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     if (dry) {
       inf.sys = tiles[tile].sys;
       inf.state = read_state(sys[inf.sys].sc).state;
+      inf.run_end = tile + 1 >= end || tiles[tile + 1].sys != inf.sys;
     }
     const SysDesc& S = sys[inf.sys];
     SysScalars* sc = S.sc;
@@ -1397,7 +1416,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       dst[1] = part_b;
     }
     ++run;
-    if (tile + 1 < end && tiles[tile + 1].sys == inf.sys) continue;
+    if (!inf.run_end) continue;
     const int r1 = tile - S.tile0 + 1;
     consumer_sync();
     const bool count = !s_abort;
