@@ -53,7 +53,9 @@ typedef enum {
   SSO_ERR_INVALID = 1,       /* bad argument, index out of range, degenerate element */
   SSO_ERR_OOM = 2,           /* device allocation failed or over the memory budget */
   SSO_ERR_SINGULAR = 3,      /* CG breakdown: p^T K p <= 0 or non-finite (K not SPD, e.g. a mechanism) */
-  SSO_ERR_NOT_CONVERGED = 4, /* iteration or refinement-sweep cap reached before rtol */
+  SSO_ERR_NOT_CONVERGED = 4, /* iteration or refinement-sweep cap reached before rtol, or
+                                 the FP64 residual no longer falls (rtol below what K and
+                                 FP64 resolve) */
   SSO_ERR_TIMEOUT = 5,       /* wall-clock cap reached */
   SSO_ERR_CUDA = 6,          /* a CUDA runtime call failed */
   SSO_ERR_NOT_READY = 7      /* result not available yet (serving poll) */
@@ -98,7 +100,10 @@ typedef struct {
   int32_t precision;         /* sso_precision */
   int32_t precond;           /* sso_precond */
   double rtol;               /* outer relative residual target */
-  double inner_rtol;         /* FP32 inner CG: residual reduction per refinement sweep */
+  double inner_rtol;         /* FP32 inner CG: residual reduction per refinement sweep (a
+                                sweep that lowers the FP64 residual less than 4x makes the
+                                system's later sweeps 10x tighter, down to 1e-6; after that
+                                such a sweep ends the solve with SSO_ERR_NOT_CONVERGED) */
   int32_t max_iter;          /* cap on CG iterations summed over sweeps */
   int32_t max_sweeps;        /* cap on refinement sweeps (FP64 residual recomputations) */
   int32_t iters_per_launch;  /* CG iterations per captured CUDA-graph launch */
