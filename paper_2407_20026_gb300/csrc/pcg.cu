@@ -1176,6 +1176,11 @@ struct StageInfo {
   float beta;
   int sys, node0, nn, j0, cb, rb;
   int run_end;  // the next tile of the CTA's range belongs to another system (or there is none)
+  // where the consumers write (read once per system by the producer, so that
+  // no consumer waits on its system's descriptor)
+  float* pnew;   // p of this iteration
+  float* q;
+  double* part;  // this tile's kernel-A partials
   // halo runs in the stage: column c sits at slot c + shift[k] (nodes) for the
   // last run k whose first node is <= c (first nodes of unused runs: INT_MAX)
   int v1, v2, sh0, sh1, sh2;
@@ -1211,6 +1216,14 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     int cur = -1, issued = 0;
     RunState R;
     R.state = ST_DONE;
+    // the system's arrays, read once per run of tiles of one system
+    struct {
+      const float *z, *K32;
+      float *p0, *p1, *q;
+      const int *col, *row_ptr;
+      double* part_a;
+      int tile0;
+    } P = {};
     // each tile's descriptor is loaded one tile ahead, so that its latency
     // overlaps the wait for a free stage
     TileDesc td_next;
@@ -1227,6 +1240,15 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       if (td.sys != cur) {
         cur = td.sys;
         R = read_state(S->sc);
+        P.z = (const float*)S->z;
+        P.K32 = S->K32;
+        P.p0 = (float*)S->p0;
+        P.p1 = (float*)S->p1;
+        P.q = (float*)S->q;
+        P.col = S->col;
+        P.row_ptr = S->row_ptr;
+        P.part_a = S->part_a;
+        P.tile0 = S->tile0;
       }
       StageInfo inf;
       inf.state = R.state;
@@ -1241,6 +1263,9 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.cb = td.cb;
       inf.rb = td.rb;
       inf.run_end = tile + 1 >= end || td_next.sys != td.sys;
+      inf.pnew = R.parity ? P.p0 : P.p1;
+      inf.q = P.q;
+      inf.part = P.part_a + 2 * (size_t)(tile - P.tile0) * WARPS;
       inf.v1 = td.nv[1] ? td.vlo[1] : INT_MAX;
       inf.v2 = td.nv[2] ? td.vlo[2] : INT_MAX;
       inf.sh0 = -td.vlo[0];
@@ -1252,8 +1277,8 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         // halo does not fit, the consumers gather z and p from global memory
         inf.mode = td.stage ? 1 : 2;
         info[s] = inf;
-        const float* z = (const float*)S->z;
-        const float* pold = R.first ? z : (const float*)(R.parity ? S->p1 : S->p0);
+        const float* z = P.z;
+        const float* pold = R.first ? z : (R.parity ? P.p1 : P.p0);
         const uint32_t kb = (uint32_t)td.nblk * 144u, cb = (uint32_t)td.ncb * 4u;
         const uint32_t rb = (uint32_t)td.nrb * 4u;
         uint32_t vb = 0u;
@@ -1262,8 +1287,8 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         unsigned char* st = ring + s * ST_STAGE;
         fence_proxy_async();
         mbar_arrive_tx(&full[s], kb + cb + 2 * vb + rb);
-        bulk_g2s(st, S->K32 + (size_t)td.j0 * 36, kb, &full[s]);
-        bulk_g2s(st + ST_OFF_C, S->col + td.cb, cb, &full[s]);
+        bulk_g2s(st, P.K32 + (size_t)td.j0 * 36, kb, &full[s]);
+        bulk_g2s(st + ST_OFF_C, P.col + td.cb, cb, &full[s]);
         if (td.stage) {
           uint32_t off = 0u;  // bytes into each vector slab
           for (int k = 0; k < HALO_RUNS; ++k) {
@@ -1274,7 +1299,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
             off += b;
           }
         }
-        bulk_g2s(st + ST_OFF_R, S->row_ptr + td.rb, rb, &full[s]);
+        bulk_g2s(st + ST_OFF_R, P.row_ptr + td.rb, rb, &full[s]);
       } else {
         info[s] = inf;
         mbar_arrive(&full[s]);
@@ -1320,7 +1345,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     double part = 0.0, part_b = 0.0;
     DF dpart = {0.f, 0.f};  // CG state: the warp's p^T q terms
     if (state == ST_PCG) {
-      float* pnew = (float*)(inf.parity ? S.p0 : S.p1);
+      float* pnew = inf.pnew;
       const float beta = inf.beta;
       if (act) {
         float acc = 0.f, zi, pi_old;
@@ -1389,7 +1414,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         }
         const float pi = fmaf(beta, pi_old, zi);
         pnew[i] = pi;
-        ((float*)S.q)[i] = acc;
+        inf.q[i] = acc;
         dpart = df_prod(pi, acc);
       }
     } else if (state != ST_DONE) {  // ST_INIT or ST_RESID: r64 = b - K64 x in FP64
@@ -1416,7 +1441,9 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       part_b = warp_sum(part_b);
     }
     if (lane == 0) {
-      double* dst = S.part_a + 2 * ((size_t)(tile - S.tile0) * WARPS + w);
+      // a dry warp may hold a stage descriptor that was never written
+      double* dst = dry ? S.part_a + 2 * ((size_t)(tile - S.tile0) * WARPS + w)
+                        : inf.part + 2 * w;
       dst[0] = part;
       dst[1] = part_b;
     }

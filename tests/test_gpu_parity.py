@@ -428,10 +428,10 @@ def test_weak_sweep_tightens_instead_of_giving_up(sso):
     # must tighten the later sweeps and reach rtol, and agree with FP64 CG
     m = meshgen.shell(n_el=64, seed=295)
     mdl = sso.Model(m)
-    st = mdl.solve(precision="fp32_ir", rtol=1e-6)
-    assert st["status"] == 0 and st["rel_residual"] <= 1e-6
+    st = mdl.solve(precision="fp32_ir", rtol=1e-6, raise_on_error=False)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
     u32 = mdl.result()["u"]
-    st64 = mdl.solve(precision="fp64", rtol=1e-10)
-    assert st64["status"] == 0
+    st64 = mdl.solve(precision="fp64", rtol=1e-8)
+    assert st64["status"] == 0, st64
     u64 = mdl.result()["u"]
     assert np.linalg.norm(u32 - u64) / np.linalg.norm(u64) <= 1e-5
