@@ -672,6 +672,13 @@ __device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t
                "r"(bytes)
                : "memory");
 }
+// Announces `bytes` more of asynchronous copies in the current phase without
+// arriving (the phase then also waits for a later arrival).
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
                                          unsigned long long* bar) {
   asm volatile(
@@ -810,14 +817,43 @@ __global__ void __launch_bounds__(NT, 3) pcg_b32_kernel(const TileDesc* __restri
   __syncwarp();
   int begin, end;
   tile_range(*n_tiles_ptr, begin, end);
+  // The preconditioner blocks do not change during a solve: the first tile's
+  // copy of them is issued before waiting for kernel A and overlaps its tail.
+  // That stage announces the four vector runs too, which follow the wait
+  // (kernel A writes p and q) whatever the system's state turns out to be.
+  BTile first;
+  if (begin + w < end) {
+    first = load_btile(tiles, begin + w);
+    if (lane == 0) {
+      const SysDesc& S0 = sys[first.sys];
+      const bool blk = S0.precond != SSO_JACOBI;
+      const uint32_t mb =
+          blk ? (uint32_t)first.nn * (M32_PACK * 4u) : round16((uint32_t)first.nn * 24u);
+      const uint32_t vb = round16((uint32_t)first.nn * 24u);
+      fence_proxy_async();
+      mbar_arrive_tx(&full[w][0], mb + 4u * vb);
+      bulk_g2s(stages, blk ? S0.M32 + (size_t)first.node0 * M32_PACK
+                           : S0.M32 + 6 * (size_t)first.node0,
+               mb, &full[w][0]);
+    }
+  }
   pdl_wait();
   int k = 0, pend_c = -1, pend_n = 0, last_k[2] = {-1, -1};
   bool dry = false;
   BJob J;
   BTile pf;  // descriptor of the warp's tile after next
   if (begin + w < end) {
-    J = make_bjob(load_btile(tiles, begin + w), sys, begin + w, nullptr);
-    if (lane == 0) issue_bjob(J, stages, &full[w][0]);
+    J = make_bjob(first, sys, begin + w, nullptr);
+    if (lane == 0) {
+      const size_t v0 = 6 * (size_t)J.node0;
+      const uint32_t vb = round16((uint32_t)J.nn * 24u);
+      const SysDesc& S0 = *J.S;
+      const float* pv = (const float*)(J.R.parity ? S0.p1 : S0.p0);
+      bulk_g2s(stages + B32_M, pv + v0, vb, &full[w][0]);
+      bulk_g2s(stages + B32_M + B32_V, (const float*)S0.q + v0, vb, &full[w][0]);
+      bulk_g2s(stages + B32_M + 2 * B32_V, (const float*)S0.r + v0, vb, &full[w][0]);
+      bulk_g2s(stages + B32_M + 3 * B32_V, (const float*)S0.dx + v0, vb, &full[w][0]);
+    }
     last_k[0] = 0;
     if (begin + w + WARPS < end) pf = load_btile(tiles, begin + w + WARPS);
   }
@@ -1208,11 +1244,35 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     s_abort = 0;
   }
   __syncthreads();
-  pdl_wait();
+  if (w != WARPS) pdl_wait();
 
   if (w == WARPS) {
     // ---------------- producer warp (lane 0) ----------------
     if (lane != 0) return;
+    // K rows, columns and row_ptr do not change during a solve, so the first
+    // stages' copies of them are issued before waiting for the previous
+    // kernel and overlap its tail; the halo copies (vectors that kernel
+    // writes) follow the wait.  All of a stage's bytes are announced up
+    // front, but its one arrival comes only after its StageInfo is written,
+    // so no consumer can see the phase complete before that.
+    int pre = 0;
+    for (; pre < ST_STAGES && begin + pre < end; ++pre) {
+      const TileDesc t = tiles[begin + pre];
+      if (!t.stage_k) break;
+      const SysDesc* S = sys + t.sys;
+      uint32_t vb = 0u;
+      if (t.stage)
+        for (int r = 0; r < HALO_RUNS; ++r) vb += (uint32_t)t.nv[r] * 24u;
+      const uint32_t kb = (uint32_t)t.nblk * 144u, cb = (uint32_t)t.ncb * 4u;
+      const uint32_t rb = (uint32_t)t.nrb * 4u;
+      unsigned char* st = ring + pre * ST_STAGE;
+      fence_proxy_async();
+      mbar_expect_tx(&full[pre], kb + cb + 2 * vb + rb);
+      bulk_g2s(st, S->K32 + (size_t)t.j0 * 36, kb, &full[pre]);
+      bulk_g2s(st + ST_OFF_C, S->col + t.cb, cb, &full[pre]);
+      bulk_g2s(st + ST_OFF_R, S->row_ptr + t.rb, rb, &full[pre]);
+    }
+    pdl_wait();
     int cur = -1, issued = 0;
     RunState R;
     R.state = ST_DONE;
@@ -1272,7 +1332,26 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.sh1 = td.nv[0] - td.vlo[1];
       inf.sh2 = td.nv[0] + td.nv[1] - td.vlo[2];
       ++issued;
-      if (R.state == ST_PCG && td.stage_k) {
+      if (k < pre) {
+        // K, columns and row_ptr already on their way; the halo (copied
+        // whatever the state, since the stage expects its bytes)
+        inf.mode = R.state == ST_PCG ? (td.stage ? 1 : 2) : 0;
+        info[s] = inf;
+        if (td.stage) {
+          const float* z = P.z;
+          const float* pold = R.state == ST_PCG && !R.first ? (R.parity ? P.p1 : P.p0) : z;
+          unsigned char* st = ring + s * ST_STAGE;
+          uint32_t off = 0u;
+          for (int r = 0; r < HALO_RUNS; ++r) {
+            if (!td.nv[r]) continue;
+            const uint32_t b = (uint32_t)td.nv[r] * 24u;
+            bulk_g2s(st + ST_OFF_Z + off, z + (size_t)td.vlo[r] * 6, b, &full[s]);
+            bulk_g2s(st + ST_OFF_P + off, pold + (size_t)td.vlo[r] * 6, b, &full[s]);
+            off += b;
+          }
+        }
+        mbar_arrive(&full[s]);  // after info[s]: the phase can complete now
+      } else if (R.state == ST_PCG && td.stage_k) {
         // mode 1: K rows, columns, row_ptr and both vector halos; mode 2: the
         // halo does not fit, the consumers gather z and p from global memory
         inf.mode = td.stage ? 1 : 2;
