@@ -151,6 +151,28 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def rank_seeds(rank, world, batch):
+    """Design seeds of one rank: ranks evaluate disjoint batches (weak scaling,
+    no data-path collective)."""
+    assert 0 <= rank < world
+    return [rank * batch + i for i in range(batch)]
+
+
+def slowest(seconds, world, dist=None, device=None):
+    """The job's time: the maximum of every rank's time (one all-reduce)."""
+    if world <= 1:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, batch, steps, seconds):
+    """Whole-job throughput: the designs of all ranks over the slowest rank's time."""
+    return world * batch * steps / seconds
+
+
 def kernel_traffic(kernel_file, key):
     """ncu DRAM bytes per launch of the dominant kernel, if the committed
     summary was taken on the current source of that kernel (else None)."""
@@ -702,7 +724,7 @@ def main():
     _build.build()
 
     B = a.batch
-    seeds = [rank * B + i for i in range(B)]
+    seeds = rank_seeds(rank, world, B)
     meshes = [design_model(a.n_el, s) for s in seeds]
     models = [sso.Model(m) for m in meshes]
     batch = sso.Batch(models)
@@ -769,12 +791,8 @@ def main():
     batch.set_profiling(False)
     p_iters = sum(s["iterations"] for s in pstats)
     p_sweeps = sum(s["sweeps"] for s in pstats)
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * a.steps / (total_ms / 1000.0)
+    total_ms = slowest(float(sum(step_ms)), world, dist, dev)
+    value = job_rate(world, B, a.steps, total_ms / 1000.0)
 
     # algorithmic bytes of kernel A over the timed region
     n_nodes = models[0].n_nodes
@@ -819,14 +837,10 @@ def main():
         for k in range(a.steps):
             step_e2e()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = slowest(time.perf_counter() - t0, world, dist, dev)
         h2d = B * (n_nodes + nq) * 8
         d2h = B * (6 * n_nodes + n_nodes + nq + 1) * 8
-        e2e = {"value": world * B * a.steps / e2e_s, "unit": "evals/s",
+        e2e = {"value": job_rate(world, B, a.steps, e2e_s), "unit": "evals/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)

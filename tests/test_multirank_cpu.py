@@ -1,0 +1,58 @@
+"""The bench's multi-GPU bookkeeping on CPU: two gloo ranks.  Ranks evaluate
+disjoint batches of designs (weak scaling, no data-path collective), the job's
+time is the slowest rank's (one max all-reduce), and the reported value is the
+designs of all ranks over that time."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, batch, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        seeds = bench.rank_seeds(rank, world, batch)
+        every = [None] * world
+        dist.all_gather_object(every, seeds)
+        local = 1.0 + 0.5 * rank  # rank-dependent step time (seconds)
+        job = bench.slowest(local, world, dist)
+        rate = bench.job_rate(world, batch, 3, job)
+        out.put((rank, every, job, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_seeds_time_and_rate():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    world, batch = 2, 8
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, batch, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, every, job, rate in res:
+        flat = [s for seeds in every for s in seeds]
+        assert sorted(flat) == list(range(world * batch))  # disjoint and complete
+        assert every[rank] == list(range(rank * batch, (rank + 1) * batch))
+        assert job == 1.5  # the slowest rank's time, on every rank
+        assert rate == world * batch * 3 / 1.5
