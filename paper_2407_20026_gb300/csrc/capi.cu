@@ -203,6 +203,14 @@ struct sso_batch {
   int* d_n_active = nullptr;
   double* d_dots = nullptr;
   std::vector<SysDesc> h_sys;
+  // the full tile list; while a solve runs, the device list may hold only the
+  // tiles of systems still iterating (compacted), with tile0 moved to match
+  std::vector<TileDesc> h_tiles;
+  std::vector<int> h_tile0;
+  std::vector<TileDesc> h_work;  // compacted list being uploaded (kept alive until synced)
+  int n_listed = 0;              // systems whose tiles the device list holds
+  int n_work = 0;                // tiles in h_work (uploaded from here)
+  bool compacted = false;
   SysScalars* h_sc = nullptr;   // pinned, n_sys
   int* h_flag = nullptr;        // pinned: [0..1] upload, [2..3] read back
   // CG graphs: [0] FP32, [1] FP64, [2] FP32 with the two-level coarse kernels
@@ -882,6 +890,14 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   const auto t0 = std::chrono::steady_clock::now();
   const bool fp64 = o->precision == SSO_FP64;
   const double inner = fp64 ? 0.0 : o->inner_rtol;
+  if (B->compacted) {  // the previous solve left a compacted list: restore the full one
+    CK(cudaMemcpyAsync(B->d_tiles, B->h_tiles.data(), B->h_tiles.size() * sizeof(TileDesc),
+                       cudaMemcpyHostToDevice, B->stream));
+    CK(cudaMemcpyAsync(B->d_n_tiles, &B->n_tiles, sizeof(int), cudaMemcpyHostToDevice,
+                       B->stream));
+    for (int s = 0; s < B->n_sys; ++s) B->h_sys[s].tile0 = B->h_tile0[s];
+    B->compacted = false;
+  }
   int n_act = 0;
   for (int s = 0; s < B->n_sys; ++s) {
     sso_model* M = B->models[s];
@@ -910,6 +926,7 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
                      cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemcpyAsync(B->d_sc, B->h_sc, sizeof(SysScalars) * B->n_sys, cudaMemcpyHostToDevice,
                      B->stream));
+  B->n_listed = B->n_sys;
   B->h_flag[0] = n_act;
   B->h_flag[1] = 0;
   CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
@@ -942,6 +959,37 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
         if (ms > o->timeout_ms) break;
       }
       if (launches > max_launches) break;  // caps are enforced on the device; belt and braces
+      // Systems have left since the tile list was last built: list only the
+      // tiles of those still iterating, so that every CTA keeps working on
+      // them instead of a few CTAs holding all of the remaining ones.  Each
+      // system's tiles stay contiguous and in order (tile0 moves with them),
+      // so its results do not change.
+      const int n_now = B->h_flag[2];
+      if (B->n_listed - n_now >= std::max(1, B->n_listed / 16)) {
+        CK(cudaMemcpyAsync(B->h_sc, B->d_sc, sizeof(SysScalars) * B->n_sys,
+                           cudaMemcpyDeviceToHost, B->stream));
+        CK(cudaStreamSynchronize(B->stream));
+        B->h_work.clear();
+        int listed = 0;
+        for (int s = 0; s < B->n_sys; ++s) {
+          if (B->h_sc[s].state == ST_DONE) continue;
+          B->h_sys[s].tile0 = (int)B->h_work.size();
+          const int t0s = B->h_tile0[s], nt = B->models[s]->n_tiles;
+          B->h_work.insert(B->h_work.end(), B->h_tiles.begin() + t0s,
+                           B->h_tiles.begin() + t0s + nt);
+          ++listed;
+        }
+        B->n_work = (int)B->h_work.size();
+        if (B->n_work > 0)
+          CK(cudaMemcpyAsync(B->d_tiles, B->h_work.data(), B->h_work.size() * sizeof(TileDesc),
+                             cudaMemcpyHostToDevice, B->stream));
+        CK(cudaMemcpyAsync(B->d_n_tiles, &B->n_work, sizeof(int), cudaMemcpyHostToDevice,
+                           B->stream));
+        CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * B->n_sys,
+                           cudaMemcpyHostToDevice, B->stream));
+        B->compacted = true;
+        B->n_listed = listed;
+      }
     }
   }
   CK(cudaMemcpyAsync(B->h_sc, B->d_sc, sizeof(SysScalars) * B->n_sys, cudaMemcpyDeviceToHost,
@@ -1559,6 +1607,9 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_tile(M, s, k));
   }
   B->n_tiles = (int)tiles.size();
+  B->h_tiles = tiles;
+  B->h_tile0.resize(n);
+  for (int s = 0; s < n; ++s) B->h_tile0[s] = B->h_sys[s].tile0;
   std::vector<AggRef> aggs;
   std::vector<int> csys(n);
   for (int s = 0; s < n; ++s) {
