@@ -320,8 +320,10 @@ def run_serving(a):
     srv.close()
 
     # the plain path: one request at a time, FP64 CG, same rtol
-    o64 = sso.options(precision="fp64", precond=a.precond, rtol=a.rtol,
-                      iters_per_launch=a.iters_per_launch)
+    # (the two-level preconditioner is FP32-only: the plain path then uses block-Jacobi)
+    o64 = sso.options(precision="fp64",
+                      precond="block_jacobi" if a.precond == "two_level" else a.precond,
+                      rtol=a.rtol, iters_per_launch=a.iters_per_launch)
     idx = list(range(min(a.alone_sample, len(meshes))))
     w = sso.Model(warm[0]["mesh"])
     w.solve(o64)
@@ -361,6 +363,8 @@ def run_serving(a):
                       "server_host_phases": phases},
         "poisson": poisson,
         "one_at_a_time_fp64": {"evals_per_s": alone, "requests": len(idx),
+                               "precond": "block_jacobi" if a.precond == "two_level"
+                               else a.precond,
                                "mean_dof": float(np.mean([dofs[i] for i in idx])),
                                "speedup_of_serving": sat / alone},
         "roofline": None,

@@ -80,7 +80,7 @@ typedef struct {
 typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1 } sso_precision;
 /* SSO_TWO_LEVEL: block-Jacobi plus a coarse correction over the rigid-body
  * modes of node aggregates (z = M_b^-1 r + P A_c^-1 P^T r, A_c = P^T K P);
- * FP32_IR only, batches and models (not the server).
+ * FP32_IR only; batches, models and the server.
  * SSO_CHAIN: no CG: K u = f is solved exactly by block cyclic reduction in
  * FP64 (K factored once per assembly, every solve and adjoint solve reusing
  * the factors).  Only for a block-tridiagonal K, i.e. every element joins
@@ -311,8 +311,10 @@ sso_status sso_batch_setup_times(const sso_batch* batch, double* ms_elements,
  * run on a second stream and overlap the CG), and when a system has converged
  * it computes its gradient, stores the result on the host and releases its
  * memory.  A request's result is bit-identical to solving it alone with the
- * same options (sso_model_solve + sso_model_gradient(w, NULL)).  The server
- * runs on streams of its own; every call returns with the host-visible state
+ * same options (sso_model_solve + sso_model_gradient(w, NULL)).  Every
+ * preconditioner but SSO_CHAIN is served (SSO_TWO_LEVEL: the coarse set-up
+ * runs with the request's other set-up kernels).  The server runs on streams
+ * of its own; every call returns with the host-visible state
  * up to date.  Not thread-safe.
  */
 typedef struct sso_server sso_server;

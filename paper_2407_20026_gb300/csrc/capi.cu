@@ -173,7 +173,7 @@ struct sso_model {
   // node offsets, coarse matrix and its inverse, coarse vectors, z_b
   int *d_agg_of, *d_agg_ptr, *d_agg_nodes, *d_cg_ptr, *d_cg_src;
   double *d_node_r64, *d_Ac;
-  float *d_node_rf, *d_Aci, *d_cw, *d_cy;
+  float *d_node_rf, *d_Aci, *d_cw, *d_cy, *d_gj;
   double* d_cdot;
   double* d_zb;
   bool has_topology = false;
@@ -219,10 +219,13 @@ struct sso_batch {
   int exec_prof[3] = {0, 0, 0};
   int grid_a[3] = {0, 0, 0};
   int grid_b[3] = {0, 0, 0};
-  // two-level work lists: every (system, aggregate), every system
+  // two-level work lists: every (system, aggregate), every system; their
+  // lengths on the device (d_ccount[0], [1]) and the CTAs of their kernels
   AggRef* d_aggs = nullptr;
   int n_aggs = 0;
   int* d_csys = nullptr;
+  int* d_ccount = nullptr;
+  int grid_restrict = 0, grid_csolve = 0;
   cudaEvent_t ev = nullptr;
   // kernel timing (sso_batch_set_profiling): events around every A and B
   // launch inside the captured graph
@@ -611,6 +614,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_node_rf = c.take<float>(4 * n);
   M->d_Ac = c.take<double>(36 * na * na);
   M->d_Aci = c.take<float>(36 * na * na);
+  M->d_gj = c.take<float>(2 * (size_t)coarse_padded_n((int)na) * coarse_padded_n((int)na));
   M->d_cw = c.take<float>(6 * na);
   M->d_cy = c.take<float>(6 * na);
   M->d_cdot = c.take<double>(COARSE_ROW_BLOCKS);
@@ -676,8 +680,9 @@ sso_status setup_model(sso_model* M, int precond, cudaStream_t s,
   if (precond == SSO_TWO_LEVEL)
     CL(launch_coarse_setup(M->n_nodes, M->n_agg, M->n_blocks, M->d_agg_ptr, M->d_agg_nodes,
                            M->d_brow, M->d_col, M->d_cg_ptr, M->d_cg_src, M->d_xyz, M->d_fixed,
-                           M->d_K64, M->d_node_r64, M->d_node_rf, M->d_ke, M->d_Ac, M->d_Aci, s),
-       4);
+                           M->d_K64, M->d_node_r64, M->d_node_rf, M->d_ke, M->d_Ac, M->d_gj,
+                           M->d_Aci, s),
+       coarse_setup_launches(M->n_agg));
   CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, M->d_fslot, nullptr,
                         M->d_nodal_load, M->d_fixed, M->d_f, nullptr, s),
      1);
@@ -722,9 +727,11 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters, bool two_level = fals
       err = launch_pcg_b(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid_b[k],
                          B->stream);
     if (err == cudaSuccess && two_level) {
-      err = launch_coarse_restrict(B->d_aggs, B->n_aggs, B->d_sys, B->stream);
+      err = launch_coarse_restrict(B->d_aggs, B->d_ccount, B->grid_restrict, B->d_sys,
+                                   B->stream);
       if (err == cudaSuccess)
-        err = launch_coarse_solve(B->d_csys, B->n_sys, B->d_sys, B->d_n_active, B->stream);
+        err = launch_coarse_solve(B->d_csys, B->d_ccount + 1, B->grid_csolve, B->d_sys,
+                                  B->d_n_active, B->stream);
       if (err == cudaSuccess)
         err = launch_coarse_prolong(B->d_tiles, B->d_n_tiles, B->d_sys,
                                     std::max(1, std::min(B->n_tiles, 152 * 8)), B->stream);
@@ -940,7 +947,7 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
     long long launches = 0;
     for (;;) {
       CK(cudaGraphLaunch(B->exec[k], B->stream));
-      g_launches += 2ull * (unsigned long long)o->iters_per_launch;
+      g_launches += (two_level ? 5ull : 2ull) * (unsigned long long)o->iters_per_launch;
       CK(cudaMemcpyAsync(B->h_flag + 2, B->d_n_active, 2 * sizeof(int),
                          cudaMemcpyDeviceToHost, B->stream));
       CK(cudaEventRecord(B->ev, B->stream));
@@ -1626,6 +1633,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   c.take<double>(n);
   c.take<AggRef>(std::max<size_t>(aggs.size(), 1));
   c.take<int>(n);
+  c.take<int>(2);
   const size_t bytes = align_up(c.off, 256);
   cudaError_t e = cudaMalloc(&B->arena, bytes);
   if (e != cudaSuccess) {
@@ -1641,6 +1649,10 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   B->d_dots = d.take<double>(n);
   B->d_aggs = d.take<AggRef>(std::max<size_t>(aggs.size(), 1));
   B->d_csys = d.take<int>(n);
+  B->d_ccount = d.take<int>(2);
+  B->grid_restrict = (B->n_aggs + 7) / 8;  // one warp per (system, aggregate)
+  B->grid_csolve = n * COARSE_ROW_BLOCKS;  // one CTA per work item
+  const int ccount[2] = {B->n_aggs, n};
   for (int s = 0; s < n; ++s) B->h_sys[s].sc = B->d_sc + s;
   e = cudaMallocHost(&B->h_sc, sizeof(SysScalars) * n);
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 4 * sizeof(int));
@@ -1661,6 +1673,8 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(B->d_csys, csys.data(), csys.size() * sizeof(int), cudaMemcpyHostToDevice,
                         B->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_ccount, ccount, sizeof(ccount), cudaMemcpyHostToDevice, B->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
   if (e != cudaSuccess) {
     sso_batch_destroy(B);
@@ -2029,6 +2043,9 @@ sso_status batch_with_capacity(cudaStream_t stream, int max_sys, int max_tiles,
   c.take<int>(1);
   c.take<int>(2);
   c.take<double>(max_sys);
+  c.take<AggRef>((size_t)max_sys * COARSE_MAX_AGG);
+  c.take<int>(max_sys);
+  c.take<int>(2);
   const size_t bytes = align_up(c.off, 256);
   cudaError_t e = cudaMalloc(&B->arena, bytes);
   if (e != cudaSuccess) {
@@ -2042,6 +2059,20 @@ sso_status batch_with_capacity(cudaStream_t stream, int max_sys, int max_tiles,
   B->d_n_tiles = d.take<int>(1);
   B->d_n_active = d.take<int>(2);
   B->d_dots = d.take<double>(max_sys);
+  // two-level lists of the running systems (lengths on the device, rewritten
+  // with the tile list); the coarse kernels loop over them on a fixed grid
+  B->d_aggs = d.take<AggRef>((size_t)max_sys * COARSE_MAX_AGG);
+  B->d_csys = d.take<int>(max_sys);
+  B->d_ccount = d.take<int>(2);
+  B->n_aggs = max_sys * COARSE_MAX_AGG;
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::max(sms, 1);
+    B->grid_restrict = std::min((B->n_aggs + 7) / 8, 8 * sms);
+    B->grid_csolve = std::min(max_sys * COARSE_ROW_BLOCKS, 4 * sms);
+  }
   for (int s = 0; s < max_sys; ++s) B->h_sys[s].sc = B->d_sc + s;
   e = cudaMallocHost(&B->h_sc, sizeof(SysScalars) * max_sys);
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_flag, 4 * sizeof(int));
@@ -2066,7 +2097,11 @@ struct sso_server {
   sso_options opts;
   size_t budget = 0, used = 0;
   int max_sys = 0, max_tiles = 0;
-  cudaStream_t cg_stream = nullptr, setup_stream = nullptr;
+  cudaStream_t cg_stream = nullptr;
+  // set-up streams, taken in turn by admitted requests so that their set-up
+  // kernels (the single-CTA coarse inverse among them) overlap one another
+  std::vector<cudaStream_t> setup_streams;
+  int next_setup = 0;
   sso_batch* B = nullptr;
   DevPool pool;                // model arenas
   PinnedRing ring;             // upload staging
@@ -2098,6 +2133,7 @@ struct sso_server {
 
 namespace {
 constexpr int kIdleAdmit = 16;  // requests admitted per step while no CG graph runs
+constexpr int kSetupStreams = 8;  // set-up streams of a server
 constexpr size_t kRingBytes = 64u << 20;  // pinned upload staging of a server
 
 void prep_worker(sso_server* S) {
@@ -2161,6 +2197,21 @@ sso_status server_upload_tables(sso_server* S, std::vector<std::vector<TileDesc>
     CK(cudaMemcpyAsync(B->d_tiles, tiles.data(), n * sizeof(TileDesc), cudaMemcpyHostToDevice,
                        B->stream));
   CK(cudaMemcpyAsync(B->d_n_tiles, &n, sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  std::vector<AggRef> aggs;
+  int ccount[2] = {0, 0};
+  if (S->opts.precond == SSO_TWO_LEVEL) {
+    for (int slot : S->running)
+      for (int g = 0; g < S->slot_req[slot]->M->n_agg; ++g) aggs.push_back({slot, g});
+    ccount[0] = (int)aggs.size();
+    ccount[1] = (int)S->running.size();
+    if (!aggs.empty())
+      CK(cudaMemcpyAsync(B->d_aggs, aggs.data(), aggs.size() * sizeof(AggRef),
+                         cudaMemcpyHostToDevice, B->stream));
+    if (!S->running.empty())
+      CK(cudaMemcpyAsync(B->d_csys, S->running.data(), S->running.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, B->stream));
+  }
+  CK(cudaMemcpyAsync(B->d_ccount, ccount, sizeof(ccount), cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(SysDesc) * S->max_sys,
                      cudaMemcpyHostToDevice, B->stream));
   CK(cudaStreamSynchronize(B->stream));  // the host vectors above are temporaries
@@ -2226,9 +2277,8 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
   *out = nullptr;
   sso_status st = check_options(opts);
   if (st != SSO_OK) return st;
-  if (opts->precond == SSO_TWO_LEVEL || opts->precond == SSO_CHAIN)
-    return fail(SSO_ERR_INVALID, "the server runs the CG preconditioners only (not SSO_TWO_LEVEL "
-                                 "or SSO_CHAIN)");
+  if (opts->precond == SSO_CHAIN)
+    return fail(SSO_ERR_INVALID, "the server runs the CG preconditioners only (not SSO_CHAIN)");
   if (max_systems <= 0 || max_tiles <= 0 || hbm_budget_bytes == 0)
     return fail(SSO_ERR_INVALID, "need max_systems > 0, max_tiles > 0, budget > 0");
   sso_server* S = new sso_server();
@@ -2244,7 +2294,11 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
   const int n_workers = (int)std::min(8u, std::max(1u, hw));
   for (int k = 0; k < n_workers; ++k) S->workers.emplace_back(prep_worker, S);
   cudaError_t e = cudaStreamCreateWithFlags(&S->cg_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < kSetupStreams && e == cudaSuccess; ++k) {
+    cudaStream_t st2 = nullptr;
+    e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) S->setup_streams.push_back(st2);
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&S->h_up, sizeof(SysScalars) * max_systems);
   if (e != cudaSuccess) {
     sso_server_destroy(S);
@@ -2283,7 +2337,7 @@ void sso_server_destroy(sso_server* S) {
   S->cv_work.notify_all();
   for (std::thread& t : S->workers) t.join();
   if (S->cg_stream) cudaStreamSynchronize(S->cg_stream);
-  if (S->setup_stream) cudaStreamSynchronize(S->setup_stream);
+  for (cudaStream_t st2 : S->setup_streams) cudaStreamSynchronize(st2);
   for (auto& kv : S->reqs) {
     ServerReq* R = kv.second;
     if (R->M) sso_model_destroy(R->M);
@@ -2295,7 +2349,7 @@ void sso_server_destroy(sso_server* S) {
   S->ring.release_all();
   if (S->h_up) cudaFreeHost(S->h_up);
   if (S->cg_stream) cudaStreamDestroy(S->cg_stream);
-  if (S->setup_stream) cudaStreamDestroy(S->setup_stream);
+  for (cudaStream_t st2 : S->setup_streams) cudaStreamDestroy(st2);
   delete S;
 }
 
@@ -2326,7 +2380,8 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
   if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
   sso_batch* B = S->B;
   const bool fp64 = S->opts.precision == SSO_FP64;
-  const int k = fp64 ? 1 : 0;
+  const bool two_level = S->opts.precond == SSO_TWO_LEVEL;
+  const int k = fp64 ? 1 : two_level ? 2 : 0;
   const int iters = S->opts.iters_per_launch;
   sso_status st;
   // 1. one graph launch of CG iterations over the running systems
@@ -2346,9 +2401,9 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
     B->h_flag[1] = 0;
     CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
                        B->stream));
-    if ((st = batch_graph(B, fp64, iters)) != SSO_OK) return st;
+    if ((st = batch_graph(B, fp64, iters, two_level)) != SSO_OK) return st;
     CK(cudaGraphLaunch(B->exec[k], B->stream));
-    g_launches += 2ull * (unsigned long long)iters;
+    g_launches += (two_level ? 5ull : 2ull) * (unsigned long long)iters;
     if ((st = debug_check(B->stream, "server: CG graph")) != SSO_OK) return st;
     CK(cudaMemcpyAsync(B->h_flag + 2, B->d_n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                        B->stream));
@@ -2422,8 +2477,10 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
     if (re != cudaSuccess) return cuda_fail(re, "upload staging");
     if (staged) std::memcpy(staged, R->prep->image.data(), R->prep->prefix);
     sso_model* M = nullptr;
-    st = create_model_device(*R->prep, nullptr, false, S->setup_stream, &M, arena, staged);
-    if (staged) CK(S->ring.mark(staged, R->prep->prefix, S->setup_stream));
+    cudaStream_t ss = S->setup_streams[S->next_setup];
+    S->next_setup = (S->next_setup + 1) % (int)S->setup_streams.size();
+    st = create_model_device(*R->prep, nullptr, false, ss, &M, arena, staged);
+    if (staged) CK(S->ring.mark(staged, R->prep->prefix, ss));
     lap2(S->ms_admit_device);
     if (st != SSO_OK) S->pool.release(arena, bytes);
     if (st == SSO_ERR_CUDA) return st;  // the device, not the request, failed
@@ -2437,12 +2494,12 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
       continue;
     }
     S->queue.pop_front();
-    if ((st = debug_check(S->setup_stream, "server: before set-up")) != SSO_OK) return st;
-    if ((st = setup_model(M, S->opts.precond, S->setup_stream)) != SSO_OK) return st;
-    CK(cudaMemsetAsync(M->d_u, 0, sizeof(double) * 6 * (size_t)M->n_nodes, S->setup_stream));
-    if ((st = debug_check(S->setup_stream, "server: set-up kernels")) != SSO_OK) return st;
+    if ((st = debug_check(ss, "server: before set-up")) != SSO_OK) return st;
+    if ((st = setup_model(M, S->opts.precond, ss)) != SSO_OK) return st;
+    CK(cudaMemsetAsync(M->d_u, 0, sizeof(double) * 6 * (size_t)M->n_nodes, ss));
+    if ((st = debug_check(ss, "server: set-up kernels")) != SSO_OK) return st;
     CK(cudaEventCreateWithFlags(&R->ev_setup, cudaEventDisableTiming));
-    CK(cudaEventRecord(R->ev_setup, S->setup_stream));
+    CK(cudaEventRecord(R->ev_setup, ss));
     lap2(S->ms_admit_setup);
     R->M = M;
     R->bytes = bytes;

@@ -7,8 +7,11 @@
 // X_i theta = theta x r_i, its rows of fixed DOFs zeroed.  The coarse matrix
 // A_c = P^T K P is formed from the FP64 K block by block (Galerkin) and summed
 // per aggregate pair in a fixed order; its inverse is formed in FP32 by
-// Gauss-Jordan elimination in one CTA's shared memory (A_c is SPD; modes with
-// no stiffness -- an aggregate whose DOFs are all fixed -- are dropped).
+// blocked Gauss-Jordan elimination without pivoting (A_c is SPD, so every
+// pivot block -- a diagonal block of a Schur complement -- is SPD too; modes
+// with no stiffness -- an aggregate whose DOFs are all fixed -- are dropped).
+#include <algorithm>
+
 #include "sso_internal.cuh"
 
 namespace sso {
@@ -98,87 +101,202 @@ __global__ void __launch_bounds__(128) galerkin_product_kernel(
   }
 }
 
-// One thread per entry of an aggregate pair's 6x6 block of A_c: the sum of
-// that entry over the pair's K blocks, in the order of the host-built list.
-__global__ void galerkin_gather_kernel(int n_agg, const int* __restrict__ cg_ptr,
-                                       const int* __restrict__ cg_src,
-                                       const double* __restrict__ T, double* __restrict__ Ac) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long pairs = (long long)n_agg * n_agg;
-  if (t >= pairs * 36) return;
-  const int p = (int)(t / 36), e = (int)(t - 36LL * p);
-  const int g = p / n_agg, h = p - g * n_agg;
-  double s = 0.0;
-  for (int k = cg_ptr[p]; k < cg_ptr[p + 1]; ++k) s += T[(size_t)cg_src[k] * 36 + e];
-  const int nc = 6 * n_agg;
-  Ac[(size_t)(6 * g + e / 6) * nc + 6 * h + e % 6] = s;
+// One CTA per aggregate pair: its 6x6 block of A_c, each entry the sum of
+// that entry over the pair's K blocks.  Group q of 36 threads (one per entry)
+// sums the list's blocks q, q + G, q + 2G, ... (four running sums, loads in
+// flight together), then the group sums are added in group order.
+constexpr int kGatherGroups = 14;
+__global__ void __launch_bounds__(36 * kGatherGroups) galerkin_gather_kernel(
+    int n_agg, const int* __restrict__ cg_ptr, const int* __restrict__ cg_src,
+    const double* __restrict__ T, double* __restrict__ Ac) {
+  constexpr int G = kGatherGroups;
+  __shared__ double part[G][36];
+  const int p = blockIdx.x, g = p / n_agg, h = p - g * n_agg;
+  const int t = threadIdx.x, q = t / 36, ent = t - 36 * q;
+  const int b = cg_ptr[p], e = cg_ptr[p + 1];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = b + q;
+  for (; k + 3 * G < e; k += 4 * G) {
+    const int s0 = cg_src[k], s1 = cg_src[k + G], s2 = cg_src[k + 2 * G], s3 = cg_src[k + 3 * G];
+    a0 += T[(size_t)s0 * 36 + ent];
+    a1 += T[(size_t)s1 * 36 + ent];
+    a2 += T[(size_t)s2 * 36 + ent];
+    a3 += T[(size_t)s3 * 36 + ent];
+  }
+  for (; k < e; k += G) a0 += T[(size_t)cg_src[k] * 36 + ent];
+  part[q][ent] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (t < 36) {
+    double sum = 0.0;
+#pragma unroll
+    for (int j = 0; j < G; ++j) sum += part[j][t];
+    const int nc = 6 * n_agg;
+    Ac[(size_t)(6 * g + t / 6) * nc + 6 * h + t % 6] = sum;
+  }
 }
 
-// One CTA: A_c^-1 in FP32 by Gauss-Jordan elimination in shared memory.
-constexpr int kInvThreads = 1024;
-__global__ void __launch_bounds__(kInvThreads) coarse_invert_kernel(int nc,
+// Blocked Gauss-Jordan inverse of A_c in FP32.  The work matrix W is A_c
+// padded to np = 32 nb rows with the identity, and with the rows and columns
+// of dead modes (diagonal <= 1e-9 of the largest) replaced by the identity.
+// Block step k (one launch, one CTA per 32x32 tile (i, j), reading W_in and
+// writing W_out):
+//   P = W_kk^-1                       (each CTA, unblocked Gauss-Jordan)
+//   R_j = P W_kj (j != k), R_k = P
+//   W_kj <- R_j;   W_ij <- [j != k] W_ij - W_ik R_j  (i != k)
+// After the nb steps W = A_c^-1 (the standard in-place block Gauss-Jordan
+// inversion); Aci = its symmetric part, zero on dead modes.
+constexpr int GJ = 32;
+constexpr int GJ_THREADS = 256;
+
+// The largest FP32 diagonal entry of A_c (every thread of the CTA gets it).
+__device__ float coarse_diag_max(int nc, const double* __restrict__ Ac, float* red) {
+  const int tid = threadIdx.x;
+  float m = 0.f;
+  for (int k = tid; k < nc; k += blockDim.x) m = fmaxf(m, (float)Ac[(size_t)k * nc + k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+  return m;
+}
+
+__device__ __forceinline__ bool coarse_dead(int nc, const double* __restrict__ Ac, int k,
+                                            float dmax) {
+  return !((float)Ac[(size_t)k * nc + k] > 1e-9f * dmax);
+}
+
+__global__ void __launch_bounds__(GJ_THREADS) coarse_gj_load_kernel(int nc, int np,
                                                                     const double* __restrict__ Ac,
-                                                                    float* __restrict__ Aci) {
-  extern __shared__ float A[];  // nc * nc
-  __shared__ float f[COARSE_MAX_N];
-  __shared__ int dead[COARSE_MAX_N];
-  __shared__ float dmax;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  for (int k = tid; k < nc * nc; k += blockDim.x) A[k] = (float)Ac[k];
-  __syncthreads();
-  if (tid == 0) {
-    float m = 0.f;
-    for (int k = 0; k < nc; ++k) m = fmaxf(m, A[k * nc + k]);
-    dmax = m;
+                                                                    float* __restrict__ W) {
+  __shared__ float red[GJ_THREADS / 32];
+  __shared__ int dead_r[GJ], dead_c[GJ];
+  const float dmax = coarse_diag_max(nc, Ac, red);
+  const int r0 = GJ * blockIdx.y, c0 = GJ * blockIdx.x, tid = threadIdx.x;
+  if (tid < GJ) {
+    const int r = r0 + tid, c = c0 + tid;
+    dead_r[tid] = r >= nc || coarse_dead(nc, Ac, r, dmax);
+    dead_c[tid] = c >= nc || coarse_dead(nc, Ac, c, dmax);
   }
   __syncthreads();
-  for (int k = tid; k < nc; k += blockDim.x) dead[k] = !(A[k * nc + k] > 1e-9f * dmax);
+  for (int e = tid; e < GJ * GJ; e += GJ_THREADS) {
+    const int lr = e / GJ, lc = e % GJ, r = r0 + lr, c = c0 + lc;
+    float v;
+    if (dead_r[lr] || dead_c[lc])
+      v = r == c ? 1.f : 0.f;
+    else
+      v = (float)Ac[(size_t)r * nc + c];
+    W[(size_t)r * np + c] = v;
+  }
+}
+
+__global__ void __launch_bounds__(GJ_THREADS) coarse_gj_step_kernel(int np, int k,
+                                                                    const float* __restrict__ Win,
+                                                                    float* __restrict__ Wout) {
+  __shared__ float P[GJ][GJ + 1], X[GJ][GJ + 1], Y[GJ][GJ + 1], R[GJ][GJ + 1];
+  __shared__ float f[GJ], prow[GJ];
+  const int bi = blockIdx.y, bj = blockIdx.x, tid = threadIdx.x;
+  const int lc = tid % GJ, lr0 = tid / GJ;  // rows lr0 + 8u, column lc
+  constexpr int RPT = GJ * GJ / GJ_THREADS;
+  const size_t kk0 = (size_t)GJ * k;
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int lr = lr0 + (GJ_THREADS / GJ) * u;
+    P[lr][lc] = Win[(kk0 + lr) * np + kk0 + lc];
+    if (bj != k) X[lr][lc] = Win[(kk0 + lr) * np + (size_t)GJ * bj + lc];
+    if (bi != k) Y[lr][lc] = Win[((size_t)GJ * bi + lr) * np + kk0 + lc];
+  }
+  float wij[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int lr = lr0 + (GJ_THREADS / GJ) * u;
+    wij[u] = (bi != k && bj != k) ? Win[((size_t)GJ * bi + lr) * np + (size_t)GJ * bj + lc] : 0.f;
+  }
   __syncthreads();
-  for (int r = warp; r < nc; r += nw)
-    for (int c = lane; c < nc; c += 32)
-      if (dead[r] || dead[c]) A[r * nc + c] = r == c ? 1.f : 0.f;
-  __syncthreads();
-  for (int kk = 0; kk < nc; ++kk) {
-    for (int r = tid; r < nc; r += blockDim.x) f[r] = A[r * nc + kk];
+  // P <- P^-1: per pivot m, the pivot row scaled by 1/p_mm, every other row
+  // r less f_r times it (f: column m before the step)
+  for (int m = 0; m < GJ; ++m) {
+    if (tid < GJ)
+      f[tid] = P[tid][m];
+    else if (tid < 2 * GJ)
+      prow[tid - GJ] = P[m][tid - GJ];
     __syncthreads();
-    const float inv = 1.f / f[kk];
-    for (int c = tid; c < nc; c += blockDim.x)
-      A[kk * nc + c] = c == kk ? inv : A[kk * nc + c] * inv;
-    __syncthreads();
-    for (int r = warp; r < nc; r += nw) {
-      if (r == kk) continue;
-      const float fr = f[r];
-      for (int c = lane; c < nc; c += 32)
-        A[r * nc + c] = c == kk ? -fr * inv : fmaf(-fr, A[kk * nc + c], A[r * nc + c]);
+    const float inv = 1.f / f[m];
+    const float pr = lc == m ? inv : prow[lc] * inv;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int lr = lr0 + (GJ_THREADS / GJ) * u;
+      P[lr][lc] = lr == m ? pr : fmaf(-f[lr], pr, lc == m ? 0.f : P[lr][lc]);
     }
     __syncthreads();
   }
-  for (int r = warp; r < nc; r += nw)
-    for (int c = lane; c < nc; c += 32) {
-      float v = 0.5f * (A[r * nc + c] + A[c * nc + r]);
-      if (dead[r] || dead[c]) v = 0.f;
-      Aci[(size_t)r * nc + c] = v;
+  // R = P X (or P)
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int lr = lr0 + (GJ_THREADS / GJ) * u;
+    float acc = 0.f;
+    if (bj == k) {
+      acc = P[lr][lc];
+    } else {
+#pragma unroll 8
+      for (int m = 0; m < GJ; ++m) acc = fmaf(P[lr][m], X[m][lc], acc);
     }
+    R[lr][lc] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int lr = lr0 + (GJ_THREADS / GJ) * u;
+    float v;
+    if (bi == k) {
+      v = R[lr][lc];
+    } else {
+      v = wij[u];
+#pragma unroll 8
+      for (int m = 0; m < GJ; ++m) v = fmaf(-Y[lr][m], R[m][lc], v);
+    }
+    Wout[((size_t)GJ * bi + lr) * np + (size_t)GJ * bj + lc] = v;
+  }
+}
+
+__global__ void __launch_bounds__(GJ_THREADS) coarse_gj_store_kernel(int nc, int np,
+                                                                     const double* __restrict__ Ac,
+                                                                     const float* __restrict__ W,
+                                                                     float* __restrict__ Aci) {
+  __shared__ float red[GJ_THREADS / 32];
+  __shared__ int dead_r[GJ], dead_c[GJ];
+  const float dmax = coarse_diag_max(nc, Ac, red);
+  const int r0 = GJ * blockIdx.y, c0 = GJ * blockIdx.x, tid = threadIdx.x;
+  if (tid < GJ) {
+    const int r = r0 + tid, c = c0 + tid;
+    dead_r[tid] = r >= nc || coarse_dead(nc, Ac, r, dmax);
+    dead_c[tid] = c >= nc || coarse_dead(nc, Ac, c, dmax);
+  }
+  __syncthreads();
+  for (int e = tid; e < GJ * GJ; e += GJ_THREADS) {
+    const int lr = e / GJ, lc = e % GJ, r = r0 + lr, c = c0 + lc;
+    if (r >= nc || c >= nc) continue;
+    float v = 0.5f * (W[(size_t)r * np + c] + W[(size_t)c * np + r]);
+    if (dead_r[lr] || dead_c[lc]) v = 0.f;
+    Aci[(size_t)r * nc + c] = v;
+  }
 }
 
 }  // namespace
+
+int coarse_padded_n(int n_agg) { return GJ * ((6 * std::max(n_agg, 1) + GJ - 1) / GJ); }
+
+int coarse_setup_launches(int n_agg) { return 5 + coarse_padded_n(n_agg) / GJ; }
 
 cudaError_t launch_coarse_setup(int n_nodes, int n_agg, int n_blocks, const int* agg_ptr,
                                 const int* agg_nodes, const int* brow, const int* col,
                                 const int* cg_ptr, const int* cg_src, const double* xyz,
                                 const uint8_t* fixed, const double* K64, double* node_r64,
-                                float* node_rf, double* T, double* Ac, float* Aci,
+                                float* node_rf, double* T, double* Ac, float* W, float* Aci,
                                 cudaStream_t s) {
   if (n_agg <= 0 || n_agg > COARSE_MAX_AGG || n_nodes <= 0) return cudaErrorInvalidValue;
-  static bool attr = false;
-  const int nc = 6 * n_agg;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(coarse_invert_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         COARSE_MAX_N * COARSE_MAX_N * (int)sizeof(float));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const int nc = 6 * n_agg, np = coarse_padded_n(n_agg), nb = np / GJ;
   coarse_geom_kernel<<<(n_agg * 32 + 127) / 128, 128, 0, s>>>(n_agg, agg_ptr, agg_nodes, xyz,
                                                                node_r64, node_rf);
   cudaError_t e = cudaGetLastError();
@@ -186,11 +304,18 @@ cudaError_t launch_coarse_setup(int n_nodes, int n_agg, int n_blocks, const int*
   galerkin_product_kernel<<<(n_blocks + 127) / 128, 128, 0, s>>>(n_blocks, brow, col, K64, fixed,
                                                                   node_r64, T);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long entries = 36LL * n_agg * n_agg;
-  galerkin_gather_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, s>>>(n_agg, cg_ptr, cg_src,
-                                                                           T, Ac);
+  galerkin_gather_kernel<<<n_agg * n_agg, 36 * kGatherGroups, 0, s>>>(n_agg, cg_ptr, cg_src, T,
+                                                                      Ac);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  coarse_invert_kernel<<<1, kInvThreads, (size_t)nc * nc * sizeof(float), s>>>(nc, Ac, Aci);
+  const dim3 tiles(nb, nb);
+  float* w[2] = {W, W + (size_t)np * np};
+  coarse_gj_load_kernel<<<tiles, GJ_THREADS, 0, s>>>(nc, np, Ac, w[0]);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int k = 0; k < nb; ++k) {
+    coarse_gj_step_kernel<<<tiles, GJ_THREADS, 0, s>>>(np, k, w[k & 1], w[(k + 1) & 1]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  coarse_gj_store_kernel<<<tiles, GJ_THREADS, 0, s>>>(nc, np, Ac, w[nb & 1], Aci);
   return cudaGetLastError();
 }
 

@@ -1006,57 +1006,61 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 }
 
 __global__ void __launch_bounds__(256) coarse_restrict_kernel(const AggRef* __restrict__ aggs,
-                                                              int n_aggs,
+                                                              const int* __restrict__ n_aggs_ptr,
                                                               const SysDesc* __restrict__ sys) {
   pdl_trigger();
   pdl_wait();
-  const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (k >= n_aggs) return;
-  const AggRef a = aggs[k];
-  const SysDesc& S = sys[a.sys];
-  if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&S.sc->coarse_pending != 1) return;
-  const int b = S.agg_ptr[a.agg], e = S.agg_ptr[a.agg + 1];
-  const float* r = (const float*)S.r;
-  const float4* rf = reinterpret_cast<const float4*>(S.node_rf);
-  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  constexpr int U = 4;  // members per lane whose loads are in flight together
-  for (int q0 = b + lane; q0 < e; q0 += 32 * U) {
-    int idx[U];
+  const int lane = threadIdx.x & 31;
+  const int n_aggs = *n_aggs_ptr, stride = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < n_aggs; k += stride) {
+    const AggRef a = aggs[k];
+    const SysDesc& S = sys[a.sys];
+    if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&S.sc->coarse_pending != 1) continue;
+    const int b = S.agg_ptr[a.agg], e = S.agg_ptr[a.agg + 1];
+    const float* r = (const float*)S.r;
+    const float4* rf = reinterpret_cast<const float4*>(S.node_rf);
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    constexpr int U = 4;  // members per lane whose loads are in flight together
+    for (int q0 = b + lane; q0 < e; q0 += 32 * U) {
+      int idx[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) idx[u] = q0 + 32 * u < e ? S.agg_nodes[q0 + 32 * u] : -1;
-    float4 o[U];
-    float v[U][6];
+      for (int u = 0; u < U; ++u) idx[u] = q0 + 32 * u < e ? S.agg_nodes[q0 + 32 * u] : -1;
+      float4 o[U];
+      float v[U][6];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (idx[u] >= 0) {
-        o[u] = rf[idx[u]];
-        ld6rw(r + 6 * (size_t)idx[u], v[u]);
-      }
+      for (int u = 0; u < U; ++u)
+        if (idx[u] >= 0) {
+          o[u] = rf[idx[u]];
+          ld6rw(r + 6 * (size_t)idx[u], v[u]);
+        }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (idx[u] >= 0) {
-        // B_i^T v: translations v_u; rotations o x v_u + v_theta
-        acc[0] += v[u][0];
-        acc[1] += v[u][1];
-        acc[2] += v[u][2];
-        acc[3] += fmaf(o[u].y, v[u][2], fmaf(-o[u].z, v[u][1], v[u][3]));
-        acc[4] += fmaf(o[u].z, v[u][0], fmaf(-o[u].x, v[u][2], v[u][4]));
-        acc[5] += fmaf(o[u].x, v[u][1], fmaf(-o[u].y, v[u][0], v[u][5]));
-      }
+      for (int u = 0; u < U; ++u)
+        if (idx[u] >= 0) {
+          // B_i^T v: translations v_u; rotations o x v_u + v_theta
+          acc[0] += v[u][0];
+          acc[1] += v[u][1];
+          acc[2] += v[u][2];
+          acc[3] += fmaf(o[u].y, v[u][2], fmaf(-o[u].z, v[u][1], v[u][3]));
+          acc[4] += fmaf(o[u].z, v[u][0], fmaf(-o[u].x, v[u][2], v[u][4]));
+          acc[5] += fmaf(o[u].x, v[u][1], fmaf(-o[u].y, v[u][0], v[u][5]));
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 6; ++d) acc[d] = warp_sum_f(acc[d]);
+    if (lane == 0)
+#pragma unroll
+      for (int d = 0; d < 6; ++d) S.w[6 * a.agg + d] = acc[d];
   }
-#pragma unroll
-  for (int d = 0; d < 6; ++d) acc[d] = warp_sum_f(acc[d]);
-  if (lane == 0)
-#pragma unroll
-    for (int d = 0; d < 6; ++d) S.w[6 * a.agg + d] = acc[d];
 }
 
-// CTA (system, row block): COARSE_ROWS_PER_BLOCK rows of y = A_c^-1 w (two
-// rows per warp, the column loads of both in flight together) and that
+// Work item (system, row block): COARSE_ROWS_PER_BLOCK rows of y = A_c^-1 w
+// (two rows per warp, the column loads of both in flight together) and that
 // block's w^T y; the CTA that completes the system's row blocks sums the
-// partials in block order and updates the scalars.
+// partials in block order and updates the scalars.  The item count is read
+// from the device (a server's list changes between launches of one graph);
+// each CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...
 __global__ void __launch_bounds__(256) coarse_solve_kernel(const int* __restrict__ csys,
-                                                           int n_csys,
+                                                           const int* __restrict__ n_csys_ptr,
                                                            const SysDesc* __restrict__ sys,
                                                            int* __restrict__ flags) {
   __shared__ float ws[COARSE_MAX_N];
@@ -1064,66 +1068,71 @@ __global__ void __launch_bounds__(256) coarse_solve_kernel(const int* __restrict
   __shared__ int s_last;
   pdl_trigger();
   pdl_wait();
-  const int si = blockIdx.x / COARSE_ROW_BLOCKS, rb = blockIdx.x - si * COARSE_ROW_BLOCKS;
-  const SysDesc& S = sys[csys[si]];
-  SysScalars* sc = S.sc;
-  if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&sc->coarse_pending != 1) return;
-  const int nc = 6 * S.n_agg;
-  const int row0 = rb * COARSE_ROWS_PER_BLOCK;
-  if (row0 >= nc) return;
-  const int n_blocks = (nc + COARSE_ROWS_PER_BLOCK - 1) / COARSE_ROWS_PER_BLOCK;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int k = tid; k < nc; k += blockDim.x) ws[k] = S.w[k];
-  __syncthreads();
-  constexpr int CPL = (COARSE_MAX_N + 31) / 32;  // columns per lane
-  const int ra = row0 + 2 * warp, rbb = ra + 1;
-  float xa[CPL], xb[CPL];
+  const int n_items = *n_csys_ptr * COARSE_ROW_BLOCKS;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int si = item / COARSE_ROW_BLOCKS, rb = item - si * COARSE_ROW_BLOCKS;
+    const SysDesc& S = sys[csys[si]];
+    SysScalars* sc = S.sc;
+    if (S.precond != SSO_TWO_LEVEL || *(volatile const int*)&sc->coarse_pending != 1) continue;
+    const int nc = 6 * S.n_agg;
+    const int row0 = rb * COARSE_ROWS_PER_BLOCK;
+    if (row0 >= nc) continue;
+    const int n_blocks = (nc + COARSE_ROWS_PER_BLOCK - 1) / COARSE_ROWS_PER_BLOCK;
+    __syncthreads();  // ws, red and s_last of the CTA's previous item are consumed
+    for (int k = tid; k < nc; k += blockDim.x) ws[k] = S.w[k];
+    __syncthreads();
+    constexpr int CPL = (COARSE_MAX_N + 31) / 32;  // columns per lane
+    const int ra = row0 + 2 * warp, rbb = ra + 1;
+    float xa[CPL], xb[CPL];
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    const int c = lane + 32 * u;
-    xa[u] = (ra < nc && c < nc) ? S.Aci[(size_t)ra * nc + c] : 0.f;
-    xb[u] = (rbb < nc && c < nc) ? S.Aci[(size_t)rbb * nc + c] : 0.f;
-  }
-  float aa = 0.f, ab = 0.f;
-#pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    const int c = lane + 32 * u;
-    const float wc = c < nc ? ws[c] : 0.f;
-    aa = fmaf(xa[u], wc, aa);
-    ab = fmaf(xb[u], wc, ab);
-  }
-  aa = warp_sum_f(aa);
-  ab = warp_sum_f(ab);
-  double dot = 0.0;
-  if (lane == 0) {
-    if (ra < nc) {
-      S.y[ra] = aa;
-      dot += (double)aa * (double)ws[ra];
+    for (int u = 0; u < CPL; ++u) {
+      const int c = lane + 32 * u;
+      xa[u] = (ra < nc && c < nc) ? S.Aci[(size_t)ra * nc + c] : 0.f;
+      xb[u] = (rbb < nc && c < nc) ? S.Aci[(size_t)rbb * nc + c] : 0.f;
     }
-    if (rbb < nc) {
-      S.y[rbb] = ab;
-      dot += (double)ab * (double)ws[rbb];
-    }
-    red[warp] = dot;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double part = 0.0;
+    float aa = 0.f, ab = 0.f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) part += red[k];
-    S.cdot[rb] = part;
-    __threadfence();
-    const unsigned prev = atomicAdd(&sc->coarse_cnt, 1u);
-    s_last = prev + 1u == (unsigned)n_blocks;
+    for (int u = 0; u < CPL; ++u) {
+      const int c = lane + 32 * u;
+      const float wc = c < nc ? ws[c] : 0.f;
+      aa = fmaf(xa[u], wc, aa);
+      ab = fmaf(xb[u], wc, ab);
+    }
+    aa = warp_sum_f(aa);
+    ab = warp_sum_f(ab);
+    double dot = 0.0;
+    if (lane == 0) {
+      if (ra < nc) {
+        S.y[ra] = aa;
+        dot += (double)aa * (double)ws[ra];
+      }
+      if (rbb < nc) {
+        S.y[rbb] = ab;
+        dot += (double)ab * (double)ws[rbb];
+      }
+      red[warp] = dot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double part = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) part += red[k];
+      S.cdot[rb] = part;
+      __threadfence();
+      const unsigned prev = atomicAdd(&sc->coarse_cnt, 1u);
+      s_last = prev + 1u == (unsigned)n_blocks;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+      __threadfence();
+      double wy = 0.0;
+      for (int k = 0; k < n_blocks; ++k) wy += __ldcg(S.cdot + k);
+      sc->coarse_cnt = 0u;
+      sc->coarse_pending = 0;
+      finish_b(sc, sc->state, sc->rz_b + wy, sc->rr_b, flags, true);
+    }
   }
-  __syncthreads();
-  if (!s_last || tid != 0) return;
-  __threadfence();
-  double wy = 0.0;
-  for (int k = 0; k < n_blocks; ++k) wy += __ldcg(S.cdot + k);
-  sc->coarse_cnt = 0u;
-  sc->coarse_pending = 0;
-  finish_b(sc, sc->state, sc->rz_b + wy, sc->rr_b, flags, true);
 }
 
 __global__ void __launch_bounds__(NT) coarse_prolong_kernel(const TileDesc* __restrict__ tiles,
@@ -1623,17 +1632,16 @@ static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, int threads, cu
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-cudaError_t launch_coarse_restrict(const AggRef* aggs, int n_aggs, const SysDesc* sys,
-                                   cudaStream_t s) {
-  if (n_aggs <= 0) return cudaSuccess;
-  return launch_pdl(coarse_restrict_kernel, (n_aggs + 7) / 8, 256, s, aggs, n_aggs, sys);
+cudaError_t launch_coarse_restrict(const AggRef* aggs, const int* n_aggs, int grid,
+                                   const SysDesc* sys, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  return launch_pdl(coarse_restrict_kernel, grid, 256, s, aggs, n_aggs, sys);
 }
 
-cudaError_t launch_coarse_solve(const int* csys, int n_csys, const SysDesc* sys, int* flags,
-                                cudaStream_t s) {
-  if (n_csys <= 0) return cudaSuccess;
-  return launch_pdl(coarse_solve_kernel, n_csys * COARSE_ROW_BLOCKS, 256, s, csys, n_csys, sys,
-                    flags);
+cudaError_t launch_coarse_solve(const int* csys, const int* n_csys, int grid, const SysDesc* sys,
+                                int* flags, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  return launch_pdl(coarse_solve_kernel, grid, 256, s, csys, n_csys, sys, flags);
 }
 
 cudaError_t launch_coarse_prolong(const TileDesc* tiles, const int* n_tiles, const SysDesc* sys,

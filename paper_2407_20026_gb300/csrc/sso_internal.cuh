@@ -213,24 +213,29 @@ constexpr int STAGE_SLAB_R = 256;        // row_ptr run (bytes)
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
 // The coarse correction of the two-level preconditioner, after kernel B:
 // restriction (one warp per (system, aggregate) of `aggs`), coarse solve and
-// scalar update (one CTA per system of `csys`), prolongation (the tiles).
+// scalar update (COARSE_ROW_BLOCKS work items per system of `csys`),
+// prolongation (the tiles).  The list lengths are read from the device
+// (*n_aggs, *n_csys); `grid` CTAs loop over the items.
 struct AggRef {
   int sys, agg;
 };
-cudaError_t launch_coarse_restrict(const AggRef* aggs, int n_aggs, const SysDesc* sys,
-                                   cudaStream_t s);
-cudaError_t launch_coarse_solve(const int* csys, int n_csys, const SysDesc* sys, int* flags,
-                                cudaStream_t s);
+cudaError_t launch_coarse_restrict(const AggRef* aggs, const int* n_aggs, int grid,
+                                   const SysDesc* sys, cudaStream_t s);
+cudaError_t launch_coarse_solve(const int* csys, const int* n_csys, int grid, const SysDesc* sys,
+                                int* flags, cudaStream_t s);
 cudaError_t launch_coarse_prolong(const TileDesc* tiles, const int* n_tiles, const SysDesc* sys,
                                   int grid, cudaStream_t s);
 
 // Coarse set-up of one model (coarse.cu): aggregate geometry, Galerkin matrix
-// A_c = P^T K P (FP64, dense [6 n_agg]^2), its FP32 inverse.
+// A_c = P^T K P (FP64, dense [6 n_agg]^2), its FP32 inverse.  W: scratch of
+// 2 coarse_padded_n(n_agg)^2 floats; coarse_setup_launches(n_agg) kernels.
+int coarse_padded_n(int n_agg);
+int coarse_setup_launches(int n_agg);
 cudaError_t launch_coarse_setup(int n_nodes, int n_agg, int n_blocks, const int* agg_ptr,
                                 const int* agg_nodes, const int* brow, const int* col,
                                 const int* cg_ptr, const int* cg_src, const double* xyz,
                                 const uint8_t* fixed, const double* K64, double* node_r64,
-                                float* node_rf, double* T, double* Ac, float* Aci,
+                                float* node_rf, double* T, double* Ac, float* W, float* Aci,
                                 cudaStream_t s);
 
 // Direct solve of a block-tridiagonal K by block cyclic reduction (chain.cu).

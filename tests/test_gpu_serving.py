@@ -120,3 +120,33 @@ def test_stream_driver(sso):
     results, elapsed = run_stream(srv, reqs, time_limit_s=120)
     assert all(r is not None and r["stats"]["status"] == 0 for r in results)
     assert all(r["latency_arrival_ms"] >= r["latency_ms"] - 1.0 for r in results)
+
+
+def test_two_level_server_results_equal_alone(sso):
+    """Two-level requests admitted and retired while others iterate (the
+    coarse work lists are rebuilt as the resident set changes) give the bits
+    of the same request solved alone with the two-level preconditioner."""
+    from paper_2407_20026_gb300.serve import Server
+    reqs = _requests()
+    opts = sso.options(precision="fp32_ir", precond="two_level", rtol=1e-8, iters_per_launch=16)
+    alone, iters = [], []
+    for req in reqs:
+        mdl = sso.Model(req["mesh"])
+        iters.append(mdl.solve(opts)["iterations"])
+        mdl.gradient(req["w"])
+        alone.append(mdl.result())
+    srv = Server(opts, max_systems=5)
+    got = _serve(srv, reqs, waves=[2, 5, 3])
+    for r, a, it in zip(got, alone, iters):
+        assert r["stats"]["status"] == 0
+        assert r["stats"]["iterations"] == it
+        for key in ("u", "dz", "dt"):
+            assert np.array_equal(r[key], a[key]), key
+        assert r["C"] == a["C"]
+    srv.close()
+
+
+def test_server_rejects_the_direct_chain_solver(sso):
+    from paper_2407_20026_gb300.serve import Server
+    with pytest.raises(sso.SSOError):
+        Server(sso.options(precision="fp64", precond="chain"))
