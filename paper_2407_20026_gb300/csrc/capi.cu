@@ -219,6 +219,15 @@ struct sso_batch {
   int exec_prof[3] = {0, 0, 0};
   int grid_a[3] = {0, 0, 0};
   int grid_b[3] = {0, 0, 0};
+  // kernel A's CTAs per resident CTA slot.  A server's systems are in
+  // different states at once (FP32 CG tiles next to FP64 residual and
+  // initial tiles, which cost several times more), so a contiguous split of
+  // its tile list leaves some CTAs with far more work than others; with 8x as
+  // many CTAs as fit, each one short, the hardware block scheduler evens the
+  // load out (each CTA still takes at least 16 tiles while more than one wave
+  // of the resident slots is busy).  A batch's systems move in step, and there
+  // one wave is faster.
+  int grid_a_mult = 1;
   // two-level work lists: every (system, aggregate), every system; their
   // lengths on the device (d_ccount[0], [1]) and the CTAs of their kernels
   AggRef* d_aggs = nullptr;
@@ -703,6 +712,7 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters, bool two_level = fals
   if (B->grid_a[k] == 0) {
     int ga = 1, gb = 1;
     pcg_grid_limits(fp64, &ga, &gb);
+    ga *= B->grid_a_mult;
     B->grid_a[k] = std::max(1, std::min(B->n_tiles, ga));
     B->grid_b[k] = std::max(1, std::min(B->n_tiles, gb));
   }
@@ -720,7 +730,7 @@ sso_status batch_graph(sso_batch* B, bool fp64, int iters, bool two_level = fals
     err = cudaEventRecordWithFlags(B->pev[0], B->stream, cudaEventRecordExternal);
   for (int it = 0; it < iters && err == cudaSuccess; ++it) {
     err = launch_pcg_a(fp64, B->d_tiles, B->d_n_tiles, B->d_sys, B->d_n_active, B->grid_a[k],
-                       B->stream);
+                       B->grid_a_mult, B->stream);
     if (err == cudaSuccess && B->profiling)
       err = cudaEventRecordWithFlags(B->pev[2 * it + 1], B->stream, cudaEventRecordExternal);
     if (err == cudaSuccess)
@@ -2035,6 +2045,7 @@ sso_status batch_with_capacity(cudaStream_t stream, int max_sys, int max_tiles,
   B->stream = stream;
   B->n_sys = max_sys;
   B->n_tiles = max_tiles;  // sizes the graph's grids; the live count is on the device
+  B->grid_a_mult = 8;
   B->h_sys.assign(max_sys, SysDesc{});
   Carver c(nullptr);
   c.take<SysDesc>(max_sys);

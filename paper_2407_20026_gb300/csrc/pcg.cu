@@ -154,9 +154,16 @@ __device__ __forceinline__ T row_dot(const T* __restrict__ K, const int* __restr
   return acc;
 }
 
-// The CTA's contiguous range of tiles.
-__device__ __forceinline__ void tile_range(int n_tiles, int& begin, int& end) {
-  const int per = (n_tiles + (int)gridDim.x - 1) / (int)gridDim.x;
+// The CTA's contiguous range of tiles.  A grid of `mult` CTAs per resident
+// CTA slot cuts a long list into short ranges that the block scheduler hands
+// out as SMs free up; a range is never cut below kMinTilesPerCta tiles (a
+// CTA's fixed costs would dominate), nor made longer than one wave of the
+// resident slots would make it.  With mult = 1 this is the even split.
+constexpr int kMinTilesPerCta = 16;
+__device__ __forceinline__ void tile_range(int n_tiles, int& begin, int& end, int mult = 1) {
+  const int g = (int)gridDim.x, res = max(1, g / max(mult, 1));
+  const int per_all = (n_tiles + g - 1) / g, per_res = (n_tiles + res - 1) / res;
+  const int per = min(per_res, max(per_all, kMinTilesPerCta));
   begin = (int)blockIdx.x * per;
   end = min(n_tiles, begin + per);
 }
@@ -297,7 +304,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const TileDesc* __restrict__ tiles,
                                                       const int* __restrict__ n_tiles_ptr,
                                                       const SysDesc* __restrict__ sys,
-                                                      int* __restrict__ flags) {
+                                                      int* __restrict__ flags, int grid_mult) {
   __shared__ double red[WARPS];
   __shared__ int s_last;
   pdl_trigger();
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(NT, 3) pcg_a_kernel(const TileDesc* __restrict
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int ln = w * NODES_PER_WARP + lane / 6, rr = lane % 6;
   int begin, end;
-  tile_range(*n_tiles_ptr, begin, end);
+  tile_range(*n_tiles_ptr, begin, end, grid_mult);
   pdl_wait();
   int run = 0, cur = -1;
   RunState R;
@@ -1233,7 +1240,7 @@ struct StageInfo {
 
 __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     const TileDesc* __restrict__ tiles, const int* __restrict__ n_tiles_ptr,
-    const SysDesc* __restrict__ sys, int* __restrict__ flags) {
+    const SysDesc* __restrict__ sys, int* __restrict__ flags, int grid_mult) {
   extern __shared__ __align__(128) unsigned char ring[];
   __shared__ __align__(8) unsigned long long full[ST_STAGES], empty[ST_STAGES];
   __shared__ StageInfo info[ST_STAGES];
@@ -1243,7 +1250,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
   int* n_active = flags;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   int begin, end;
-  tile_range(*n_tiles_ptr, begin, end);
+  tile_range(*n_tiles_ptr, begin, end, grid_mult);
   if (t == 0) {
     for (int s = 0; s < ST_STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -1580,11 +1587,9 @@ static cudaError_t b32_attributes() {
 }
 
 // A CG kernel launched with programmatic stream serialisation (see pdl_wait).
-static cudaError_t launch_cg_kernel(void (*kernel)(const TileDesc*, const int*, const SysDesc*,
-                                                   int*),
-                                    int grid, int threads, int smem, cudaStream_t s,
-                                    const TileDesc* tiles, const int* n_tiles,
-                                    const SysDesc* sys, int* flags) {
+template <typename... Args>
+static cudaError_t launch_cg_kernel(void (*kernel)(Args...), int grid, int threads, int smem,
+                                    cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)threads);
@@ -1595,26 +1600,30 @@ static cudaError_t launch_cg_kernel(void (*kernel)(const TileDesc*, const int*, 
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, tiles, n_tiles, sys, flags);
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 cudaError_t launch_pcg_a(bool fp64, const TileDesc* tiles, const int* n_tiles,
-                         const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
+                         const SysDesc* sys, int* flags, int grid, int grid_mult,
+                         cudaStream_t s) {
   if (fp64)
-    return launch_cg_kernel(pcg_a_kernel<double>, grid, NT, 0, s, tiles, n_tiles, sys, flags);
+    return launch_cg_kernel<const TileDesc*, const int*, const SysDesc*, int*, int>(
+        pcg_a_kernel<double>, grid, NT, 0, s, tiles, n_tiles, sys, flags, grid_mult);
   cudaError_t e = staged_attributes();
   if (e != cudaSuccess) return e;
-  return launch_cg_kernel(pcg_a_staged_kernel, grid, ST_THREADS, ST_SMEM, s, tiles, n_tiles,
-                          sys, flags);
+  return launch_cg_kernel<const TileDesc*, const int*, const SysDesc*, int*, int>(
+      pcg_a_staged_kernel, grid, ST_THREADS, ST_SMEM, s, tiles, n_tiles, sys, flags, grid_mult);
 }
 
 cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
                          const SysDesc* sys, int* flags, int grid, cudaStream_t s) {
   if (fp64)
-    return launch_cg_kernel(pcg_b_kernel<double>, grid, NT, 0, s, tiles, n_tiles, sys, flags);
+    return launch_cg_kernel<const TileDesc*, const int*, const SysDesc*, int*>(
+        pcg_b_kernel<double>, grid, NT, 0, s, tiles, n_tiles, sys, flags);
   cudaError_t e = b32_attributes();
   if (e != cudaSuccess) return e;
-  return launch_cg_kernel(pcg_b32_kernel, grid, NT, B32_SMEM, s, tiles, n_tiles, sys, flags);
+  return launch_cg_kernel<const TileDesc*, const int*, const SysDesc*, int*>(
+      pcg_b32_kernel, grid, NT, B32_SMEM, s, tiles, n_tiles, sys, flags);
 }
 
 template <typename... Args>

@@ -200,9 +200,11 @@ cudaError_t launch_axpby(int n, double a, const double* x, const double* y, cons
 
 // Launchers (pcg.cu)
 // flags[0] = systems still iterating, flags[1] = device-side failure (a bounded
-// wait that gave up); grid sizes from pcg_grid_limits.
+// wait that gave up); grid sizes from pcg_grid_limits.  Kernel A's grid may be
+// grid_mult times the resident CTA count (its tile ranges then shorten).
 cudaError_t launch_pcg_a(bool fp64, const TileDesc* tiles, const int* n_tiles,
-                         const SysDesc* sys, int* flags, int grid, cudaStream_t s);
+                         const SysDesc* sys, int* flags, int grid, int grid_mult,
+                         cudaStream_t s);
 cudaError_t launch_pcg_b(bool fp64, const TileDesc* tiles, const int* n_tiles,
                          const SysDesc* sys, int* flags, int grid, cudaStream_t s);
 // Staging-buffer limits of the FP32 kernel A (a tile is staged when it fits).
