@@ -511,7 +511,7 @@ int aggregate_nodes(int n, const std::vector<int>& row_ptr, const std::vector<in
 
 // Aggregate size for a mesh of n nodes: at most kMaxAggregates aggregates
 // (coarse problems of at most 6 kMaxAggregates = 234 unknowns, whose FP32
-// inverse is formed in one CTA's shared memory), at least 16 nodes each.
+// inverse is read in every CG iteration), at least 16 nodes each.
 constexpr int kMaxAggregates = COARSE_MAX_AGG;
 int aggregate_target(int n) {
   return std::max(16, (n + kMaxAggregates - 1) / kMaxAggregates);
@@ -1163,7 +1163,7 @@ sso_status prepare_model(ModelPrep& P) {
   HostTopo& Tm = P.T;
   {
     const int n = hm.n_nodes;
-    // at most COARSE_MAX_AGG aggregates (the coarse inverse lives in shared memory)
+    // at most COARSE_MAX_AGG aggregates (the coarse inverse is read every iteration)
     for (int target = aggregate_target(n);; target += std::max(1, target / 4)) {
       Tm.n_agg = aggregate_nodes(n, Tm.row_ptr, Tm.col, target, Tm.agg_of);
       if (Tm.n_agg <= COARSE_MAX_AGG) break;

@@ -146,9 +146,10 @@ constexpr int CHUNK_PER_THREAD = 8;
 static_assert(CHUNK * WARPS == NT * CHUNK_PER_THREAD, "kernel-A chunk: 8 partials per thread");
 static_assert(CHUNK == 32 * CHUNK_PER_THREAD, "kernel-B chunk: 8 partials per lane");
 
-// Two-level preconditioner: at most this many node aggregates per system, so
-// the coarse problem (6 unknowns per aggregate, FP32) fits one CTA's shared
-// memory for its inversion.
+// Two-level preconditioner: at most this many node aggregates per system.  The
+// coarse solve reads all of A_c^-1 (FP32, [6 n_agg]^2, here <= 219 KB) in every
+// CG iteration and holds w in shared memory and 8 columns of two rows per lane
+// in registers, so the coarse space stays small.
 constexpr int COARSE_MAX_AGG = 39;
 constexpr int COARSE_MAX_N = 6 * COARSE_MAX_AGG;
 // The coarse solve y = A_c^-1 w of a system is split into row blocks, one CTA each.
