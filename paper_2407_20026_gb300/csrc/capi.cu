@@ -2110,7 +2110,8 @@ struct sso_server {
   int max_sys = 0, max_tiles = 0;
   cudaStream_t cg_stream = nullptr;
   // set-up streams, taken in turn by admitted requests so that their set-up
-  // kernels (the single-CTA coarse inverse among them) overlap one another
+  // kernels (element matrices, assembly, preconditioner, coarse space)
+  // overlap one another
   std::vector<cudaStream_t> setup_streams;
   int next_setup = 0;
   sso_batch* B = nullptr;
