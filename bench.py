@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=3, help="oracle designs in cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-two-level", action="store_true",
+                   help="default line: skip the two-level preconditioner sub-record")
     p.add_argument("--workload", default="shell",
                    choices=["shell", "serving", "gridshell", "large", "training", "bridge"],
                    help="shell: batches of 64x64 shell designs (default line); serving: "
@@ -79,12 +81,18 @@ def design_model(n_el, seed):
 
 
 def workload_name(a):
+    """The workload both arms run (the same text on the oracle's line)."""
     n = a.n_el
     dof = 6 * (n + 1) ** 2
-    return ("shell %dx%d quads (%d DOF), %d designs/step, %s %s CG + FP64 refinement to rtol %g, "
-            "solve + adjoint dC/dz, dC/dt" % (n, n, dof, a.batch,
-                                               "FP32" if a.precision == "fp32_ir" else "FP64",
-                                               a.precond, a.rtol))
+    return ("shell %dx%d quads (%d DOF), seeded designs (z bump, t ~ U[0.05, 0.2]), self-weight, "
+            "corners pinned: solve + adjoint dC/dz, dC/dt at <=1e-6 rel err vs FP64"
+            % (n, n, dof))
+
+
+def solver_name(a):
+    return ("%s %s CG%s to rtol %g, %d designs per batched step"
+            % ("FP32" if a.precision == "fp32_ir" else "FP64", a.precond,
+               " + FP64 refinement" if a.precision == "fp32_ir" else "", a.rtol, a.batch))
 
 
 class ClockSampler:
@@ -151,6 +159,61 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (the oracle's machine)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in ln:
+                v = ln.split(":", 1)[1].strip()
+                model = v if model is None else model + " " + v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"cpu_model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
+def rel_errors(got, ref, keys=("u", "dz", "dt")):
+    """Relative 2-norm errors of GPU results against the oracle's, and of C."""
+    out = {}
+    for k in keys:
+        if k in got and k in ref and np.size(ref[k]):
+            nr = np.linalg.norm(ref[k])
+            out[k] = float(np.linalg.norm(np.asarray(got[k]) - ref[k]) / (nr if nr > 0 else 1.0))
+    if "C" in got and "C" in ref:
+        out["C"] = abs(float(got["C"]) - ref["C"]) / abs(ref["C"])
+    return out
+
+
+def max_errors(errs):
+    """Per-quantity maximum over a list of rel_errors dicts."""
+    keys = sorted({k for e in errs for k in e})
+    return {k: max(e[k] for e in errs if k in e) for k in keys}
+
+
+def oracle_gradients(meshes, w=1.0):
+    """Oracle results of several models in threads (ctypes releases the GIL).
+    Returns (results, seconds, threads)."""
+    import concurrent.futures
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    n = max(1, min(len(meshes), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(n) as ex:
+        res = list(ex.map(lambda m: oracle.gradient(m, w=w), meshes))
+    return res, time.perf_counter() - t0, n
+
+
 def rank_seeds(rank, world, batch):
     """Design seeds of one rank: ranks evaluate disjoint batches (weak scaling,
     no data-path collective)."""
@@ -166,6 +229,31 @@ def slowest(seconds, world, dist=None, device=None):
     t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_replicas(cmd, n, stdout=None):
+    """Runs `cmd` as n replica ranks on this node (rank r on GPU r), as
+    torch.distributed.run would: RANK, LOCAL_RANK, WORLD_SIZE and a 127.0.0.1
+    rendezvous in the environment.  Rank 0's stdout goes to `stdout` (default:
+    this process's); the other ranks' stdout is discarded.  Returns the first
+    non-zero exit code of any rank, else 0."""
+    port = free_port()
+    procs = []
+    for r in range(n):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(n),
+                   LOCAL_WORLD_SIZE=str(n), GROUP_RANK="0", MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port))
+        out = stdout if r == 0 else subprocess.DEVNULL
+        procs.append(subprocess.Popen(cmd, env=env, stdout=out))
+    codes = [p.wait() for p in procs]
+    return next((c for c in codes if c != 0), 0)
 
 
 def job_rate(world, batch, steps, seconds):
@@ -202,14 +290,8 @@ def cpu_oracle_sample(a, n_designs, gpu_results=None):
     if gpu_results:
         for i, ref in enumerate(refs):
             if i in gpu_results:
-                g = gpu_results[i]
-
-                def rel(x, y):
-                    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
-                errs.append({"u": rel(g["u"], ref["u"]),
-                             "C": abs(g["C"] - ref["C"]) / abs(ref["C"]),
-                             "dz": rel(g["dz"], ref["dz"]), "dt": rel(g["dt"], ref["dt"])})
-    return n_designs / dt, dt, errs
+                errs.append(rel_errors(gpu_results[i], ref))
+    return n_designs / dt, dt, errs, refs
 
 
 def run_reference(a):
@@ -232,11 +314,13 @@ def run_reference(a):
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1000 * total / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(a).replace("%d designs/step" % a.batch,
-                                                        "1 design/step"),
-                   "oracle": "FP64 band Cholesky + dual-number adjoint, single thread"},
+        "config": {"workload": workload_name(a),
+                   "solver": "oracle: FP64 band Cholesky + dual-number adjoint (Eq. 6), "
+                             "single thread, 1 design per step",
+                   "host": host_cpu()},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d designs of the workload, one per step" % a.steps},
+                         "sample": "%d designs of the workload (seeds 0..%d), one per step"
+                                   % (a.steps, a.steps - 1), **host_cpu()},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -301,6 +385,15 @@ def run_serving(a):
     clk = clocks.stop()
     failed = [i for i, r in enumerate(res) if r["stats"]["status"] != 0]
     sat = len(meshes) / elapsed
+    accuracy = None
+    if not a.no_cpu_baseline:
+        # a seeded sample of 8 requests (sizes across the stream) against the oracle
+        pick = sorted(np.random.default_rng(7).choice(len(meshes), min(8, len(meshes)),
+                                                      replace=False).tolist())
+        refs, o_s, o_threads = oracle_gradients([meshes[i] for i in pick])
+        errs = [rel_errors(res[i], ref, keys=("u", "dz")) for i, ref in zip(pick, refs)]
+        accuracy = {"requests": pick, "dof": [dofs[i] for i in pick], **max_errors(errs),
+                    "oracle_seconds": o_s, "oracle_threads": o_threads}
     iters = [r["stats"]["iterations"] for r in res]
     lat_sat = [r["latency_ms"] for r in res]
 
@@ -362,6 +455,7 @@ def run_serving(a):
                       "pcg_dof_per_s": float(np.dot(iters, dofs)) / elapsed,
                       "server_host_phases": phases},
         "poisson": poisson,
+        "accuracy_vs_oracle": accuracy,
         "one_at_a_time_fp64": {"evals_per_s": alone, "requests": len(idx),
                                "precond": "block_jacobi" if a.precond == "two_level"
                                else a.precond,
@@ -410,6 +504,7 @@ def run_gridshell(a):
     launches = sso.kernel_launches() - l0
     clk = clocks.stop()
     cpu = None
+    err = None
     if not a.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -419,12 +514,9 @@ def run_gridshell(a):
             ref = oracle.gradient(m)
             k += 1
         dt = time.perf_counter() - t0
-        err = {"u": float(np.linalg.norm(r["u"] - ref["u"]) / np.linalg.norm(ref["u"])),
-               "C": abs(r["C"] - ref["C"]) / abs(ref["C"]),
-               "dz": float(np.linalg.norm(r["dz"] - ref["dz"]) / np.linalg.norm(ref["dz"]))}
+        err = rel_errors(r, ref, keys=("u", "dz"))
         cpu = {"value": k / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": "%d evaluations of the same design, %.1f s" % (k, dt),
-               "accuracy_of_gpu": err}
+               "sample": "%d evaluations of the same design, %.1f s" % (k, dt), **host_cpu()}
     line = {
         "metric": METRIC, "value": a.repeats / total, "unit": "evals/s", "n_gpus": 1,
         "steps": a.repeats, "warmup": max(a.warmup, 3), "ms_per_step": 1000 * total / a.repeats,
@@ -435,6 +527,7 @@ def run_gridshell(a):
                    "l2": "problem fits L2 (latency workload)"},
         "latency_us": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "min": float(min(lat))},
         "cg_iterations": st["iterations"],
+        "accuracy_vs_oracle": err if cpu else None,
         "roofline": None, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(launches),
         "e2e": {"value": a.repeats / total, "unit": "evals/s",
@@ -599,6 +692,23 @@ def run_large(a):
     bytes_resid = nb * (36 * 8 + 4) + (n + 1) * 4 + 3 * (6 * n * 8)
     alg = s0["iterations"] * bytes_pcg + s0["sweeps"] * bytes_resid
     ach = alg / (ms_a / 1e3) / 1e9 if ms_a > 0 else None
+    accuracy = None
+    if not a.no_cpu_baseline:
+        # the oracle's element-by-element K applied to the GPU's u (FP64, host)
+        import oracle
+        oracle.build()
+        res_u = mdl.result()
+        fx = m["fixed"].ravel().astype(bool)
+        f_o = oracle.load_vector(m)
+        f_o[fx] = 0.0
+        r_o = oracle.residual(m, res_u["u"])
+        r_o[fx] = 0.0
+        accuracy = {"oracle_rel_residual_of_gpu_u": float(np.linalg.norm(r_o) /
+                                                          np.linalg.norm(f_o)),
+                    "C_vs_oracle_f_dot_u_rel": abs(res_u["C"] - float(f_o @ res_u["u"])) /
+                    abs(res_u["C"]),
+                    "note": "no direct oracle solve at this size; the oracle's K bounds the "
+                            "GPU solution's residual"}
     n_eb = mdl.n_elem_blocks
     asm_bytes = n_eb * (288 + 4) + (nb + 1) * 4 + nb * 8 + 6 * n + nb * (288 + 144)
     asm_gbs = asm_bytes / (su["assembly"] / 1e3) / 1e9 if su["assembly"] > 0 else None
@@ -623,7 +733,7 @@ def run_large(a):
         "assembly": {"ms": su["assembly"], "alg_bytes": asm_bytes, "achieved_gbs": asm_gbs,
                      "frac": asm_gbs / peak_gbs if asm_gbs else None},
         "elements_ms": su["elements"], "precond_loads_ms": su["precond"],
-        "adjoint_contraction_ms": su["adjoint"],
+        "adjoint_contraction_ms": su["adjoint"], "accuracy_vs_oracle": accuracy,
         "cpu_baseline": None, "clocks": clk, "gpu_launches": int(launches),
         "e2e": None,
     }
@@ -680,6 +790,34 @@ def run_training(a):
     el = time.perf_counter() - t0
     launches = sso.kernel_launches() - l0
     clk = clocks.stop()
+    accuracy = None
+    if not a.no_cpu_baseline:
+        # the current MLP's designs: C and d(C + 0.1 V)/dz, dt of 4 of them vs the oracle
+        zc = (z0 + 0.25 * torch.tanh(mlp(latents)).double()).detach().requires_grad_(True)
+        tc = t.clone().requires_grad_(True)
+        u, C, V = BatchSSOFunction.apply(batch, zc, tc, opts)
+        (C + 0.1 * V).sum().backward()
+        import oracle
+        oracle.build()
+        pick = [0, 21, 42, 63]
+        models = []
+        for i in pick:
+            mi = dict(base)
+            xyz = np.array(base["xyz"], copy=True)
+            xyz[:, 2] = zc[i].detach().cpu().numpy()
+            mi["xyz"] = xyz
+            models.append(mi)
+        refs, o_s, _ = oracle_gradients(models)
+        errs = []
+        for k, i in enumerate(pick):
+            vol = oracle.volume(models[k])
+            ref = {"C": refs[k]["C"], "dz": refs[k]["dz"] + 0.1 * vol["dz"],
+                   "dt": refs[k]["dt"] + 0.1 * vol["dt"]}
+            got = {"C": float(C[i].detach()), "dz": zc.grad[i].cpu().numpy(),
+                   "dt": tc.grad[i].cpu().numpy()}
+            errs.append(rel_errors(got, ref, keys=("dz", "dt")))
+        accuracy = {"designs": pick, **max_errors(errs), "oracle_seconds": o_s,
+                    "note": "gradients of C + 0.1 V after the timed steps"}
     line = {
         "metric": "training steps/sec (64 shell solves + adjoint per step)",
         "value": a.steps / el, "unit": "steps/s", "n_gpus": 1, "steps": a.steps,
@@ -692,7 +830,7 @@ def run_training(a):
                                                                  a.precond, a.rtol),
                    "l2": "64 x K (%.0f MB) > L2" % (B * batch.models[0].n_blocks * 144 / 1e6)},
         "design_evals_per_s": B * a.steps / el,
-        "loss_first": losses[0], "loss_last": losses[-1],
+        "loss_first": losses[0], "loss_last": losses[-1], "accuracy_vs_oracle": accuracy,
         "roofline": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": int(launches),
         "e2e": None,
     }
@@ -706,6 +844,10 @@ def run_workload(a):
 
 def main():
     a = parse()
+    if a.impl == "ours" and a.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one replica rank per GPU (the path shards by design; no data-path collective)
+        sys.exit(launch_replicas([sys.executable, os.path.abspath(__file__), *sys.argv[1:]],
+                                 a.gpus))
     if a.impl == "reference":
         run_reference(a)
         return
@@ -719,7 +861,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl")
+        # the only collective is the max of the ranks' times
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -847,20 +990,61 @@ def main():
         e2e = {"value": job_rate(world, B, a.steps, e2e_s), "unit": "evals/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # results of the graded path for the oracle comparison (before any other solve)
+    n_cmp = min(a.cpu_sample, B)
+    gres = {i: models[i].result() for i in range(n_cmp)} if rank == 0 else {}
+
+    # the two-level preconditioner on the same designs (not the graded value)
+    two_level = None
+    if a.precond == "block_jacobi" and a.precision == "fp32_ir" and not a.no_two_level:
+        o2 = sso.options(precision=a.precision, precond="two_level", rtol=a.rtol,
+                         inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch)
+
+        def step_two_level():
+            for i, mdl in enumerate(models):
+                mdl.set_design(z_dev[i], t_dev[i])
+            st = batch.solve(o2)
+            batch.gradient()
+            return st
+
+        step_two_level()
+        torch.cuda.synchronize()
+        k2 = max(1, min(a.steps, 3))
+        tl_ms, tl_iters = [], 0
+        for k in range(k2):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st2 = step_two_level()
+            e1.record(stream)
+            e1.synchronize()
+            tl_ms.append(e0.elapsed_time(e1))
+            if any(s["status"] != 0 for s in st2):
+                raise RuntimeError("two-level solve failed")
+            tl_iters += sum(s["iterations"] for s in st2)
+        tl_total = slowest(float(sum(tl_ms)), world, dist, dev)
+        two_level = {"value": job_rate(world, B, k2, tl_total / 1000.0), "unit": "evals/s",
+                     "steps": k2, "ms_per_step": tl_total / k2,
+                     "cg_iterations_per_design": tl_iters / (B * k2),
+                     "precond": "block-Jacobi + rigid-body coarse space of node aggregates"}
+        if rank == 0:
+            gres_tl = {i: models[i].result() for i in range(n_cmp)}
+
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     accuracy = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        gres = {}
-        for i in range(min(a.cpu_sample, B)):
-            r = models[i].result()
-            gres[i] = r
-        v, secs, errs = cpu_oracle_sample(a, min(a.cpu_sample, B), gres)
+        v, secs, errs, refs = cpu_oracle_sample(a, n_cmp, gres)
         cpu = {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle",
                "sample": "%d designs of the workload (seeds 0..%d), %.1f s" %
-                         (min(a.cpu_sample, B), min(a.cpu_sample, B) - 1, secs)}
+                         (n_cmp, n_cmp - 1, secs), **host_cpu()}
         if errs:
-            accuracy = {k: max(e[k] for e in errs) for k in errs[0]}
+            accuracy = max_errors(errs)
+            accuracy["designs"] = n_cmp
+        if two_level is not None:
+            errs2 = [rel_errors(gres_tl[i], refs[i]) for i in range(n_cmp)]
+            two_level["accuracy_vs_oracle"] = max_errors(errs2)
 
     if rank == 0:
         lat = np.array(step_ms)
@@ -870,7 +1054,8 @@ def main():
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "designs_per_step": B,
+            "config": {"workload": workload_name(a), "solver": solver_name(a),
+                       "designs_per_step": B,
                        "dof_per_design": 6 * n_nodes, "precision": a.precision,
                        "precond": a.precond, "rtol": a.rtol, "inner_rtol": a.inner_rtol,
                        "l2": "flushed between steps (256 MB write); working set > L2",
@@ -901,7 +1086,7 @@ def main():
                                       "element_matrices": setup["elements"],
                                       "assembly": setup["assembly"],
                                       "preconditioner_and_loads": setup["precond"]}},
-            "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy,
+            "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "two_level": two_level,
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
         }
         print(json.dumps(line), flush=True)

@@ -163,22 +163,25 @@ sso_status sso_bsr_spmv(int32_t n_nodes, const int32_t* d_row_ptr, const int32_t
                         void* stream);
 
 /* The same product as sso_bsr_spmv for callers that cannot allocate device
- * memory: for example code running while another component records a CUDA
- * graph and treats any allocation as an error, latency-critical loops that
- * cannot take the allocator's synchronisation, or applications whose whole
- * device memory belongs to their own pool.  The paper has no counterpart; it
- * is an interface for such callers.
+ * memory: a plug-in that its host application gives a fixed device-memory
+ * budget and forbids to allocate beyond it, a real-time loop that cannot take
+ * the allocator's latency or the synchronisation that cudaMalloc / cudaFree
+ * may imply, or an application whose device memory all belongs to its own
+ * pool allocator.  The paper has no counterpart; it is an interface for such
+ * callers.
  *
  * Nothing is allocated: the partial sums live in a fixed array compiled into
- * the library (about 512 KiB, held on every GPU that loads the library until the
- * process exits), which limits n_nodes to 2,097,152 (larger n_nodes returns
- * SSO_ERR_INVALID).  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  Every call shares the array and it keeps
- * the last call's contents (the completion counter is cleared by each call):
- * calls whose kernels overlap on the GPU -- different streams or host threads
- * -- race and must be serialised by the caller.  Results are bit-identical to
- * sso_bsr_spmv.  Only enqueues work on `stream`. */
+ * the library (about 512 KiB, held on every GPU that loads the library until
+ * the process exits), which limits n_nodes to 2,097,152 (larger n_nodes
+ * returns SSO_ERR_INVALID with a message).  Every call looks up that array's
+ * device address (cudaGetSymbolAddress, with the caller's device current); the
+ * first call in a context may load the library's device code there, so make
+ * that first call before any stream capture.  Every call shares the array and
+ * it keeps the last call's contents (the completion counter is cleared by each
+ * call): calls whose kernels overlap on the GPU -- different streams or host
+ * threads -- race and must be serialised by the caller.  Results are
+ * bit-identical to sso_bsr_spmv (same kernel, same fixed summation order).
+ * Only enqueues work on `stream`. */
 sso_status sso_bsr_spmv_noalloc(int32_t n_nodes, const int32_t* d_row_ptr, const int32_t* d_col,
                                 const double* d_K, const double* d_x, double* d_y,
                                 double* d_xty, void* stream);

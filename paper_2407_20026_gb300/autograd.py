@@ -9,6 +9,9 @@ g = gu)`` gives the C and u part directly (one adjoint solve if gu is
 non-zero, none otherwise since K is symmetric); the V part is gV times the
 volume gradient computed in the forward pass.
 
+With t = None the thicknesses stay as they are and backward returns no
+gradient for them.
+
 A model holds one solution at a time: backward must run before the same model
 is solved again.
 """
@@ -30,6 +33,7 @@ class SSOFunction(torch.autograd.Function):
         vol = mdl.volume(device=z.device)
         ctx.mdl = mdl
         ctx.device = z.device
+        ctx.t_given = t is not None
         ctx.vdz = vol["dz"]
         ctx.vdt = vol["dt"]
         C = torch.tensor(r["C"], dtype=torch.float64, device=z.device)
@@ -48,7 +52,7 @@ class SSOFunction(torch.autograd.Function):
         if gV is not None:
             dz = dz + gV.to(torch.float64) * ctx.vdz
             dt = dt + gV.to(torch.float64) * ctx.vdt
-        return None, dz, dt, None
+        return None, dz, (dt if ctx.t_given else None), None
 
 
 class BatchSSOFunction(torch.autograd.Function):
@@ -71,6 +75,7 @@ class BatchSSOFunction(torch.autograd.Function):
             vdt.append(v["dt"])
         ctx.batch = batch
         ctx.device = z.device
+        ctx.t_given = t is not None
         ctx.vdz = torch.stack(vdz)
         ctx.vdt = torch.stack(vdt)
         return (torch.stack(us), torch.tensor(Cs, dtype=torch.float64, device=z.device),
@@ -95,4 +100,4 @@ class BatchSSOFunction(torch.autograd.Function):
             gv = gV.to(torch.float64).reshape(n, 1)
             dz = dz + gv * ctx.vdz
             dt = dt + gv * ctx.vdt
-        return None, dz, dt, None
+        return None, dz, (dt if ctx.t_given else None), None

@@ -422,16 +422,97 @@ def test_scattered_numbering_fallback_path(sso, orc):
     assert rel(r["dt"], ref["dt"]) <= TOL_FP32_IR
 
 
-def test_weak_sweep_tightens_instead_of_giving_up(sso):
-    # seed 295 of the 64 x 64 shell family: with the default inner tolerance
-    # one refinement sweep lowers the FP64 residual less than 4x; the solve
-    # must tighten the later sweeps and reach rtol, and agree with FP64 CG
-    m = meshgen.shell(n_el=64, seed=295)
+def _oracle_gradients(orc, meshes, w=1.0, gs=None):
+    """Oracle results of several models, computed in threads (the oracle is a
+    C library called through ctypes, which releases the GIL)."""
+    import concurrent.futures
+    gs = gs if gs is not None else [None] * len(meshes)
+    with concurrent.futures.ThreadPoolExecutor(len(meshes)) as ex:
+        return list(ex.map(lambda mg: orc.gradient(mg[0], w=w, g=mg[1]), zip(meshes, gs)))
+
+
+BENCH_SEEDS = [0, 1, 2, 3, 295]
+
+
+def test_bench_configuration_against_oracle(sso, orc):
+    """The bench's exact configuration -- 64 x 64 shell designs in one batch,
+    FP32 block-Jacobi CG inside FP64 refinement to rtol 1e-6 with inner
+    tolerance 1e-3, 32 iterations per graph launch -- against the oracle at the
+    FP32+IR tolerance.  Seed 295 is the design whose refinement sweep stalls at
+    the default inner tolerance: the solve must tighten its later sweeps and
+    still land within the tolerance."""
+    meshes = [meshgen.shell(n_el=64, seed=s) for s in BENCH_SEEDS]
+    batch = sso.Batch([sso.Model(m) for m in meshes])
+    opts = sso.options(precision="fp32_ir", precond="block_jacobi", rtol=1e-6,
+                       inner_rtol=1e-3, iters_per_launch=32)
+    stats = batch.solve(opts, raise_on_error=False)
+    batch.gradient()
+    refs = _oracle_gradients(orc, meshes)
+    for s, st, mdl, ref in zip(BENCH_SEEDS, stats, batch.models, refs):
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-6, (s, st)
+        r = mdl.result()
+        assert rel(r["u"], ref["u"]) <= TOL_FP32_IR, s
+        assert abs(r["C"] - ref["C"]) <= TOL_FP32_IR * abs(ref["C"]), s
+        assert rel(r["dz"], ref["dz"]) <= TOL_FP32_IR, s
+        assert rel(r["dt"], ref["dt"]) <= TOL_FP32_IR, s
+
+
+@pytest.mark.parametrize("name", ["shell5", "mixed", "gridshell13"])
+def test_general_objective_adjoint_fp32_ir(sso, orc, name):
+    """J = w C + g^T u with the adjoint solve K lambda = w f + g (Eq. 5) taken by
+    the FP32 CG inside FP64 refinement, against the oracle."""
+    m = MODELS[name]()
+    rng = np.random.default_rng(13)
+    g = rng.normal(size=6 * m["xyz"].shape[0]) * 1e3
+    ref = orc.gradient(m, w=0.5, g=g)
     mdl = sso.Model(m)
-    st = mdl.solve(precision="fp32_ir", rtol=1e-6, raise_on_error=False)
-    assert st["status"] == 0 and st["rel_residual"] <= 1e-6, st
-    u32 = mdl.result()["u"]
-    st64 = mdl.solve(precision="fp64", rtol=1e-8)
-    assert st64["status"] == 0, st64
-    u64 = mdl.result()["u"]
-    assert np.linalg.norm(u32 - u64) / np.linalg.norm(u64) <= 1e-5
+    st = mdl.solve(precision="fp32_ir", rtol=1e-9)
+    assert st["status"] == 0
+    st = mdl.gradient(0.5, g)
+    assert st["status"] == 0
+    r = mdl.result()
+    free = ~m["fixed"].ravel().astype(bool)
+    assert rel(r["u"], ref["u"]) <= TOL_FP32_IR
+    assert rel(r["lam"][free], ref["lam"][free]) <= TOL_FP32_IR
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP32_IR
+    if m["quad_conn"].shape[0]:
+        assert rel(r["dt"], ref["dt"]) <= TOL_FP32_IR
+
+
+def test_batched_autograd_general_objective_fp32_ir(sso, orc):
+    """BatchSSOFunction with an upstream gradient on u (J_i = 0.7 C_i + g_i^T u_i
+    + 0.1 V_i): each design's adjoint is a real FP32+IR solve, against the
+    oracle."""
+    from paper_2407_20026_gb300.autograd import BatchSSOFunction
+    meshes = [meshgen.shell(n_el=6, span=8.0, seed=s) for s in range(3)]
+    batch = sso.Batch([sso.Model(m) for m in meshes])
+    z = torch.tensor(np.stack([m["xyz"][:, 2] for m in meshes]), device="cuda",
+                     requires_grad=True)
+    t = torch.tensor(np.stack([m["quad_props"][:, 0] for m in meshes]), device="cuda",
+                     requires_grad=True)
+    u, C, V = BatchSSOFunction.apply(batch, z, t, sso.options(rtol=1e-10))
+    rng = np.random.default_rng(21)
+    gvec = torch.tensor(rng.normal(size=tuple(u.shape)) * 1e2, device="cuda")
+    (0.7 * C + (gvec * u).sum(dim=1) + 0.1 * V).sum().backward()
+    refs = _oracle_gradients(orc, meshes, w=0.7, gs=list(gvec.cpu().numpy()))
+    for i, (m, ref) in enumerate(zip(meshes, refs)):
+        vol = orc.volume(m)
+        assert rel(z.grad[i].cpu().numpy(), ref["dz"] + 0.1 * vol["dz"]) <= TOL_FP32_IR
+        assert rel(t.grad[i].cpu().numpy(), ref["dt"] + 0.1 * vol["dt"]) <= TOL_FP32_IR
+
+
+def test_autograd_with_fixed_thickness(sso, orc):
+    """t = None keeps the thicknesses: backward returns dz only."""
+    from paper_2407_20026_gb300.autograd import BatchSSOFunction, SSOFunction
+    m = small_shell(5)
+    ref = orc.gradient(m)
+    mdl = sso.Model(m)
+    z = torch.tensor(m["xyz"][:, 2], device="cuda", requires_grad=True)
+    u, C, V = SSOFunction.apply(mdl, z, None, sso.options(precision="fp64", rtol=1e-11))
+    C.backward()
+    assert rel(z.grad.cpu().numpy(), ref["dz"]) <= TOL_FP64
+    batch = sso.Batch([sso.Model(m)])
+    zb = torch.tensor(m["xyz"][None, :, 2], device="cuda", requires_grad=True)
+    u, C, V = BatchSSOFunction.apply(batch, zb, None, sso.options(precision="fp64", rtol=1e-11))
+    C.sum().backward()
+    assert rel(zb.grad[0].cpu().numpy(), ref["dz"]) <= TOL_FP64
