@@ -231,6 +231,14 @@ def slowest(seconds, world, dist=None, device=None):
     return float(t.item())
 
 
+def assembly_bytes(mdl):
+    """Algorithmic bytes of one model's assembly: its element blocks read once
+    (in assembly order), cptr, the block row and column of every block, the
+    support flags, and K64 + K32 written."""
+    nb, n = mdl.n_blocks, mdl.n_nodes
+    return mdl.n_elem_blocks * 288 + (nb + 1) * 4 + nb * 8 + 6 * n + nb * (288 + 144)
+
+
 def free_port():
     import socket
     with socket.socket() as sk:
@@ -709,8 +717,7 @@ def run_large(a):
                     abs(res_u["C"]),
                     "note": "no direct oracle solve at this size; the oracle's K bounds the "
                             "GPU solution's residual"}
-    n_eb = mdl.n_elem_blocks
-    asm_bytes = n_eb * (288 + 4) + (nb + 1) * 4 + nb * 8 + 6 * n + nb * (288 + 144)
+    asm_bytes = assembly_bytes(mdl)
     asm_gbs = asm_bytes / (su["assembly"] / 1e3) / 1e9 if su["assembly"] > 0 else None
     line = {
         "metric": METRIC, "value": 1000.0 / (solve_ms + grad_ms), "unit": "evals/s",
@@ -954,6 +961,19 @@ def main():
     traffic = kernel_traffic("pcg.cu", "pcg_a_%s" % ("f32" if fp32 else "f64"))
     traffic_bytes = traffic["dram_bytes_per_design_launch"] * B if traffic else None
 
+    # assembly: one launch for the whole batch, timed with events on the
+    # library's stream in the profiled step
+    asm_bytes = sum(assembly_bytes(m) for m in models)
+    asm_ms = setup["assembly"]
+    asm_gbs = asm_bytes / (asm_ms / 1e3) / 1e9 if asm_ms > 0 else None
+    asm_traffic = kernel_traffic("assembly.cu", "assemble_sorted")
+    roofline_assembly = {
+        "bound": "hbm", "kernel": "assemble_sorted (one launch, %d designs)" % B,
+        "achieved": asm_gbs, "peak": peak_gbs, "unit": "GB/s",
+        "frac": asm_gbs / peak_gbs if asm_gbs else None, "peak_kind": peak_kind,
+        "alg_bytes_per_launch": asm_bytes, "ms": asm_ms,
+        "traffic": asm_traffic["dram_bytes_per_design"] * B if asm_traffic else None}
+
     # end to end: designs from pinned host memory, results back to host
     e2e = None
     if not a.no_e2e:
@@ -1076,16 +1096,16 @@ def main():
                 "launches_timed": a_launches, "kernel_ms_total": ms_a,
                 "kernel_b_ms_total": ms_b,
             },
-            # elapsed per phase of the profiled step; the set-ups of the
-            # designs overlap on a stream pool, so their per-kernel device
-            # times are reported separately, summed over the designs
+            # elapsed per phase of the profiled step; each set-up stage is
+            # one launch for the whole batch
             "phase_ms_per_step": {"setup": setup["setup_wall"],
                                   "cg_kernel_a": ms_a, "cg_kernel_b_and_coarse": ms_b,
                                   "adjoint_contraction": setup["adjoint"],
-                                  "setup_device_ms_summed": {
+                                  "setup_stages": {
                                       "element_matrices": setup["elements"],
                                       "assembly": setup["assembly"],
                                       "preconditioner_and_loads": setup["precond"]}},
+            "roofline_assembly": roofline_assembly,
             "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "two_level": two_level,
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
         }

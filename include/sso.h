@@ -286,17 +286,16 @@ sso_status sso_batch_set_profiling(sso_batch* batch, int32_t enable);
 sso_status sso_batch_kernel_times(const sso_batch* batch, double* ms_a, double* ms_b,
                                   int64_t* launches);
 /* Set-up and adjoint timing while profiling is enabled (same switch and
- * reset).  The models' set-ups and contraction passes run concurrently on a
- * pool of up to 16 streams.  ms_elements, ms_assembly and ms_precond are
- * device milliseconds of each phase summed over every model set-up of
- * sso_batch_solve -- element matrices (Sec. 2.2), assembly of K (Eq. 1),
- * preconditioner + load vector -- and so count overlapping work once per
- * model; ms_setup_wall is the elapsed time of the whole set-up phase (first
- * set-up launched to last one finished), summed over solves.  ms_adjoint is
+ * reset).  sso_batch_solve sets up all its models with one launch per stage:
+ * element matrices (Sec. 2.2), assembly of K (Eq. 1), preconditioner + load
+ * vector.  ms_elements, ms_assembly and ms_precond are the device
+ * milliseconds of those launches (CUDA events on the batch's stream), summed
+ * over solves; ms_setup_wall is the elapsed time of the whole set-up phase
+ * (the two-level coarse spaces included), summed over solves.  ms_adjoint is
  * the elapsed time of every contraction pass of sso_batch_gradient (the
- * adjoint sum of Eq. 6 and the per-node gather, all models).  setups counts
- * model set-ups timed, gradients the gradient calls.  Any pointer may be
- * NULL. */
+ * adjoint sum of Eq. 6 and the per-node gather, all models, on a pool of up
+ * to 16 streams).  setups counts model set-ups timed, gradients the gradient
+ * calls.  Any pointer may be NULL. */
 sso_status sso_batch_setup_times(const sso_batch* batch, double* ms_elements,
                                  double* ms_assembly, double* ms_precond, double* ms_adjoint,
                                  double* ms_setup_wall, int64_t* setups, int64_t* gradients);

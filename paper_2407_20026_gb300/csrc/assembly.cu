@@ -1,12 +1,14 @@
 // Assembly of K (Eq. 1) from element blocks, supports (Eqs. 2-3 with b = 0,
 // by elimination), the (block-)Jacobi preconditioner and per-node gathers.
 //
-// Assembly is a gather: K block b is the sum of the element blocks listed in
-// csrc[cptr[b] .. cptr[b+1]), in that (increasing element-block) order.  The
-// list is built once per topology, so the sum order is fixed and the result is
-// bit-reproducible without atomics.  One thread per (block, entry): a warp
-// reads 32 consecutive doubles of one or two element blocks, so reads and the
-// K64/K32 writes are coalesced; the kernel is bound by HBM.
+// Assembly is a segmented sum over one contiguous stream: the element kernels
+// wrote every element block to its place in assembly order (sorted by K block,
+// then by element block id, once per topology), so K block b is the sum of
+// kes[cptr[b] .. cptr[b+1]) in that order -- fixed, hence bit-reproducible
+// without atomics.  One thread per (block, pair of entries) reads 16-byte
+// vectors of consecutive element blocks, so a warp's loads and its K64 / K32
+// stores are contiguous runs; the kernel is bound by HBM.  A batch of
+// structures is set up by one launch per stage (one structure per grid row).
 #include <math.h>
 
 #include "sso_internal.cuh"
@@ -14,36 +16,54 @@
 namespace sso {
 namespace {
 
-__global__ void __launch_bounds__(256) assemble_kernel(
-    int n_blocks, const int* __restrict__ cptr, const int* __restrict__ csrc,
-    const double* __restrict__ ke, const int* __restrict__ brow, const int* __restrict__ col,
-    const uint8_t* __restrict__ fixed, double* __restrict__ K64, float* __restrict__ K32) {
+// Pairs of entries per 6x6 block (36 doubles = 18 double2).
+constexpr int PAIRS = 18;
+
+__global__ void __launch_bounds__(256) assemble_sorted_kernel(const SetupJob* __restrict__ jobs) {
+  const SetupJob& J = jobs[blockIdx.y];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *J.err = 0;  // the preconditioner runs next
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n_blocks * 36) return;
-  const int b = (int)(idx / 36);
-  const int k = (int)(idx - (long long)b * 36);
-  const int r = k / 6, c = k - 6 * (k / 6);
-  double s = 0.0;
-  const int c1 = cptr[b + 1];
-  for (int i = cptr[b]; i < c1; ++i) s += ke[(size_t)csrc[i] * 36 + k];
-  const int ni = brow[b], nj = col[b];
-  if (fixed[6 * ni + r] || fixed[6 * nj + c]) s = (ni == nj && r == c) ? 1.0 : 0.0;
-  K64[idx] = s;
-  K32[idx] = (float)s;
+  if (idx >= (long long)J.n_blocks * PAIRS) return;
+  const int b = (int)(idx / PAIRS);
+  const int p = (int)(idx - (long long)b * PAIRS);
+  const int c0 = __ldg(J.cptr + b), c1 = __ldg(J.cptr + b + 1);
+  const double2* src = reinterpret_cast<const double2*>(J.kes) + p;
+  // the first four contributions are loaded together (a quad mesh has at
+  // most four per block), then summed in order
+  double2 v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    v[k] = c0 + k < c1 ? __ldcs(src + (size_t)(c0 + k) * PAIRS) : make_double2(0.0, 0.0);
+  double sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (c0 + k < c1) {
+      sx += v[k].x;
+      sy += v[k].y;
+    }
+  for (int i = c0 + 4; i < c1; ++i) {
+    const double2 w = __ldcs(src + (size_t)i * PAIRS);
+    sx += w.x;
+    sy += w.y;
+  }
+  // supports: fixed rows and columns become identity rows and columns
+  const int r = p / 3, c = 2 * (p - 3 * r);
+  const int ni = __ldg(J.brow + b), nj = __ldg(J.col + b);
+  const bool fr = J.fixed[6 * ni + r] != 0;
+  if (fr || J.fixed[6 * nj + c]) sx = (ni == nj && r == c) ? 1.0 : 0.0;
+  if (fr || J.fixed[6 * nj + c + 1]) sy = (ni == nj && r == c + 1) ? 1.0 : 0.0;
+  reinterpret_cast<double2*>(J.K64)[idx] = make_double2(sx, sy);
+  reinterpret_cast<float2*>(J.K32)[idx] = make_float2((float)sx, (float)sy);
 }
 
 // Block-Jacobi: Cholesky-invert the 6x6 diagonal block of every node (FP64).
 // Jacobi: invert the diagonal entries.  A non-positive pivot sets *err.
 // Layouts: M64 [n][6][6] (Jacobi: [n][6]); M32 packed [n][M32_PACK]
 // (Jacobi: [n][6]).
-__global__ void __launch_bounds__(128) precond_kernel(int n_nodes, int kind,
-                                                      const int* __restrict__ diag_idx,
-                                                      const double* __restrict__ K64,
-                                                      double* __restrict__ M64,
-                                                      float* __restrict__ M32,
-                                                      int* __restrict__ err) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= n_nodes) return;
+__device__ __forceinline__ void precond_node(int n, int kind, const int* __restrict__ diag_idx,
+                                             const double* __restrict__ K64,
+                                             double* __restrict__ M64, float* __restrict__ M32,
+                                             int* __restrict__ err) {
   const double* B = K64 + (size_t)diag_idx[n] * 36;
   if (kind == SSO_JACOBI) {
     for (int i = 0; i < 6; ++i) {
@@ -97,16 +117,23 @@ __global__ void __launch_bounds__(128) precond_kernel(int n_nodes, int kind,
   for (int k = 21; k < M32_PACK; ++k) M32[(size_t)n * M32_PACK + k] = 0.f;
 }
 
+__global__ void __launch_bounds__(128) precond_setup_kernel(const SetupJob* __restrict__ jobs,
+                                                            int kind) {
+  const SetupJob& J = jobs[blockIdx.y];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < J.n_nodes) precond_node(n, kind, J.diag, J.K64, J.M64, J.M32, J.err);
+}
+
 // Per node, in slot order: f = nodal load + area-load shares (uz only; quad
 // slots s >= slot_quad0 of fslot), zero on fixed DOFs; dz = sum of the per-slot
 // gradient values gslot[s].  Either output may be NULL.  One thread per node.
-__global__ void __launch_bounds__(128) node_gather_kernel(
-    int n_nodes, const int* __restrict__ nptr, const int* __restrict__ nsrc, int slot_quad0,
-    const double* __restrict__ fslot, const double* __restrict__ gslot,
-    const double* __restrict__ nodal_load, const uint8_t* __restrict__ fixed,
-    double* __restrict__ f, double* __restrict__ dz) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= n_nodes) return;
+__device__ __forceinline__ void node_gather(int n, const int* __restrict__ nptr,
+                                            const int* __restrict__ nsrc, int slot_quad0,
+                                            const double* __restrict__ fslot,
+                                            const double* __restrict__ gslot,
+                                            const double* __restrict__ nodal_load,
+                                            const uint8_t* __restrict__ fixed,
+                                            double* __restrict__ f, double* __restrict__ dz) {
   const int s0 = nptr[n], s1 = nptr[n + 1];
   if (f) {
     double fz = nodal_load[6 * n + 2];
@@ -126,6 +153,23 @@ __global__ void __launch_bounds__(128) node_gather_kernel(
   }
 }
 
+__global__ void __launch_bounds__(128) node_gather_kernel(
+    int n_nodes, const int* __restrict__ nptr, const int* __restrict__ nsrc, int slot_quad0,
+    const double* __restrict__ fslot, const double* __restrict__ gslot,
+    const double* __restrict__ nodal_load, const uint8_t* __restrict__ fixed,
+    double* __restrict__ f, double* __restrict__ dz) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < n_nodes) node_gather(n, nptr, nsrc, slot_quad0, fslot, gslot, nodal_load, fixed, f, dz);
+}
+
+__global__ void __launch_bounds__(128) loads_setup_kernel(const SetupJob* __restrict__ jobs) {
+  const SetupJob& J = jobs[blockIdx.y];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < J.n_nodes)
+    node_gather(n, J.nptr, J.nsrc, 2 * J.n_beams, J.fslot, nullptr, J.nodal_load, J.fixed, J.f,
+                nullptr);
+}
+
 __global__ void axpby_kernel(int n, double a, const double* __restrict__ x,
                              const double* __restrict__ y, const uint8_t* __restrict__ fixed,
                              double* __restrict__ out) {
@@ -137,21 +181,27 @@ __global__ void axpby_kernel(int n, double a, const double* __restrict__ x,
 
 }  // namespace
 
-cudaError_t launch_assemble(int n_blocks, const int* cptr, const int* csrc, const double* ke,
-                            const int* brow, const int* col, const uint8_t* fixed,
-                            double* K64, float* K32, cudaStream_t s) {
-  const long long n = (long long)n_blocks * 36;
-  if (n <= 0) return cudaSuccess;
-  assemble_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_blocks, cptr, csrc, ke, brow,
-                                                                col, fixed, K64, K32);
+cudaError_t launch_setup_assemble(const SetupJob* jobs, int n_jobs, int max_blocks,
+                                  cudaStream_t s) {
+  if (n_jobs <= 0 || max_blocks <= 0) return cudaSuccess;
+  if (n_jobs > 65535) return cudaErrorInvalidValue;
+  const long long n = (long long)max_blocks * PAIRS;
+  assemble_sorted_kernel<<<dim3((unsigned)((n + 255) / 256), n_jobs), 256, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_precond(int n_nodes, int kind, const int* diag_idx, const double* K64,
-                           double* M64, float* M32, int* err_flag, cudaStream_t s) {
-  if (n_nodes <= 0) return cudaSuccess;
-  precond_kernel<<<(n_nodes + 127) / 128, 128, 0, s>>>(n_nodes, kind, diag_idx, K64, M64, M32,
-                                                        err_flag);
+cudaError_t launch_setup_precond(const SetupJob* jobs, int n_jobs, int max_nodes, int kind,
+                                 cudaStream_t s) {
+  if (n_jobs <= 0 || max_nodes <= 0) return cudaSuccess;
+  if (n_jobs > 65535) return cudaErrorInvalidValue;
+  precond_setup_kernel<<<dim3((max_nodes + 127) / 128, n_jobs), 128, 0, s>>>(jobs, kind);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_loads(const SetupJob* jobs, int n_jobs, int max_nodes, cudaStream_t s) {
+  if (n_jobs <= 0 || max_nodes <= 0) return cudaSuccess;
+  if (n_jobs > 65535) return cudaErrorInvalidValue;
+  loads_setup_kernel<<<dim3((max_nodes + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -127,6 +127,8 @@ struct HostMesh {
 
 struct HostTopo {
   std::vector<int> row_ptr, col, brow, diag, cptr, csrc, nptr, nsrc;
+  // epos[eb]: position of element block eb in assembly order (inverse of csrc)
+  std::vector<int> epos;
   // two-level preconditioner: node aggregates and, per aggregate pair (g, h),
   // the K blocks (i, j) with i in g and j in h, in block order
   int n_agg = 0;
@@ -135,6 +137,18 @@ struct HostTopo {
   // one of the diagonal (a chain)
   std::vector<int> chain_up;
   bool is_chain = false;
+};
+
+// Largest per-model counts of a set of models (the set-up grids' x extents).
+struct SetupExtent {
+  int beams = 0, quads = 0, blocks = 0, nodes = 0;
+  template <class Model>
+  void add(const Model* M) {
+    beams = std::max(beams, M->n_beams);
+    quads = std::max(quads, M->n_quads);
+    blocks = std::max(blocks, M->n_blocks);
+    nodes = std::max(nodes, M->n_nodes);
+  }
 };
 
 }  // namespace
@@ -152,7 +166,7 @@ struct sso_model {
   size_t arena_bytes = 0;  // size of the arena (fixed at creation)
   bool own_arena = true;   // false: the arena belongs to a server's pool
   // topology
-  int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_brow, *d_diag, *d_cptr, *d_csrc,
+  int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_brow, *d_diag, *d_cptr, *d_epos,
       *d_nptr, *d_nsrc;
   uint8_t* d_fixed;
   // design
@@ -185,6 +199,8 @@ struct sso_model {
   double* d_chain_ws = nullptr;
   long long assembly_gen = 0, chain_gen = -1;
   int* d_err;
+  // the set-up stages' view of this model (device copy, written at creation)
+  SetupJob* d_job;
   bool assembled = false, solved = false;
   int assembled_precond = -1;
   sso_options last_opts;
@@ -235,6 +251,9 @@ struct sso_batch {
   int* d_csys = nullptr;
   int* d_ccount = nullptr;
   int grid_restrict = 0, grid_csolve = 0;
+  // the models' set-up jobs (one launch per set-up stage for the whole batch)
+  SetupJob* d_jobs = nullptr;
+  SetupExtent extent;
   cudaEvent_t ev = nullptr;
   // kernel timing (sso_batch_set_profiling): events around every A and B
   // launch inside the captured graph
@@ -423,6 +442,8 @@ void build_topology(const HostMesh& m, HostTopo& T) {
     std::vector<int> fill(T.cptr.begin(), T.cptr.end() - 1);
     for (int k = 0; k < n_eb; ++k) T.csrc[fill[target[k]]++] = k;
   }
+  T.epos.resize(n_eb);
+  for (int k = 0; k < n_eb; ++k) T.epos[T.csrc[k]] = k;
   // node incidence: slots 2e+a (beams), 2 n_beams + 4e + a (quads), by node, stable
   const int n_slots = 2 * m.n_beams + 4 * m.n_quads;
   std::vector<int> slot_node(n_slots);
@@ -570,7 +591,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_brow = c.take<int>(M->n_blocks);
   M->d_diag = c.take<int>(n);
   M->d_cptr = c.take<int>((size_t)M->n_blocks + 1);
-  M->d_csrc = c.take<int>(M->n_eb);
+  M->d_epos = c.take<int>(M->n_eb);
   M->d_nptr = c.take<int>(n + 1);
   M->d_nsrc = c.take<int>(M->n_slots);
   M->d_fixed = c.take<uint8_t>(ndof);
@@ -629,6 +650,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_cdot = c.take<double>(COARSE_ROW_BLOCKS);
   M->d_zb = c.take<double>(ndof);
   M->d_err = c.take<int>(1);
+  M->d_job = c.take<SetupJob>(1);
   return align_up(c.off, 256);
 }
 
@@ -666,39 +688,83 @@ sso_status leave(sso_model* M) {
   return SSO_OK;
 }
 
-// Element matrices, K, preconditioner and loads of one model.  ev (or NULL):
-// four events recorded before the element kernels, after them, after the
-// assembly and at the end.
-sso_status setup_model(sso_model* M, int precond, cudaStream_t s,
-                       const cudaEvent_t* ev = nullptr) {
+// The set-up stages' view of a model's arrays.
+SetupJob make_setup_job(const sso_model* M) {
+  SetupJob J;
+  J.xyz = M->d_xyz;
+  J.beam_conn = M->d_beam_conn;
+  J.beam_props = M->d_beam_props;
+  J.quad_conn = M->d_quad_conn;
+  J.quad_props = M->d_quad_props;
+  J.n_beams = M->n_beams;
+  J.n_quads = M->n_quads;
+  J.n_nodes = M->n_nodes;
+  J.n_blocks = M->n_blocks;
+  J.pressure = M->pressure;
+  J.gamma = M->gamma;
+  J.epos = M->d_epos;
+  J.kes = M->d_ke;
+  J.fslot = M->d_fslot;
+  J.cptr = M->d_cptr;
+  J.brow = M->d_brow;
+  J.col = M->d_col;
+  J.fixed = M->d_fixed;
+  J.K64 = M->d_K64;
+  J.K32 = M->d_K32;
+  J.err = M->d_err;
+  J.diag = M->d_diag;
+  J.M64 = M->d_M64;
+  J.M32 = M->d_M32;
+  J.nptr = M->d_nptr;
+  J.nsrc = M->d_nsrc;
+  J.nodal_load = M->d_nodal_load;
+  J.f = M->d_f;
+  return J;
+}
+
+// Element matrices, K, preconditioner and loads of the n models whose jobs
+// are jobs[0 .. n), one launch per stage.  ev (or NULL): four events recorded
+// before the element kernels, after them, after the assembly and at the end.
+sso_status setup_stages(const SetupJob* jobs, int n, const SetupExtent& x, int precond,
+                        cudaStream_t s, const cudaEvent_t* ev = nullptr) {
   if (ev) CK(cudaEventRecord(ev[0], s));
-  CL(launch_beam_stiffness(M->n_beams, M->d_xyz, M->d_beam_conn, M->d_beam_props, M->d_ke, s),
-     M->n_beams > 0);
-  CL(launch_quad_stiffness(M->n_quads, M->d_xyz, M->d_quad_conn, M->d_quad_props, M->pressure,
-                           M->gamma, M->d_ke + (size_t)4 * M->n_beams * 36,
-                           M->d_fslot + 2 * (size_t)M->n_beams, s),
-     M->n_quads > 0);
+  CL(launch_setup_beams(jobs, n, x.beams, s), x.beams > 0);
+  CL(launch_setup_quads(jobs, n, x.quads, s), x.quads > 0);
   if (ev) CK(cudaEventRecord(ev[1], s));
-  CL(launch_assemble(M->n_blocks, M->d_cptr, M->d_csrc, M->d_ke, M->d_brow, M->d_col,
-                     M->d_fixed, M->d_K64, M->d_K32, s),
-     1);
+  CL(launch_setup_assemble(jobs, n, x.blocks, s), 1);
   if (ev) CK(cudaEventRecord(ev[2], s));
-  CK(cudaMemsetAsync(M->d_err, 0, sizeof(int), s));
-  CL(launch_precond(M->n_nodes, precond, M->d_diag, M->d_K64, M->d_M64, M->d_M32, M->d_err, s),
+  CL(launch_setup_precond(jobs, n, x.nodes, precond == SSO_JACOBI ? SSO_JACOBI : SSO_BLOCK_JACOBI,
+                          s),
      1);
-  if (precond == SSO_TWO_LEVEL)
-    CL(launch_coarse_setup(M->n_nodes, M->n_agg, M->n_blocks, M->d_agg_ptr, M->d_agg_nodes,
-                           M->d_brow, M->d_col, M->d_cg_ptr, M->d_cg_src, M->d_xyz, M->d_fixed,
-                           M->d_K64, M->d_node_r64, M->d_node_rf, M->d_ke, M->d_Ac, M->d_gj,
-                           M->d_Aci, s),
-       coarse_setup_launches(M->n_agg));
-  CL(launch_node_gather(M->n_nodes, M->d_nptr, M->d_nsrc, 2 * M->n_beams, M->d_fslot, nullptr,
-                        M->d_nodal_load, M->d_fixed, M->d_f, nullptr, s),
-     1);
+  CL(launch_setup_loads(jobs, n, x.nodes, s), 1);
   if (ev) CK(cudaEventRecord(ev[3], s));
+  return SSO_OK;
+}
+
+// The two-level coarse space of one assembled model.
+sso_status setup_coarse(sso_model* M, cudaStream_t s) {
+  CL(launch_coarse_setup(M->n_nodes, M->n_agg, M->n_blocks, M->d_agg_ptr, M->d_agg_nodes,
+                         M->d_brow, M->d_col, M->d_cg_ptr, M->d_cg_src, M->d_xyz, M->d_fixed,
+                         M->d_K64, M->d_node_r64, M->d_node_rf, M->d_ke, M->d_Ac, M->d_gj,
+                         M->d_Aci, s),
+     coarse_setup_launches(M->n_agg));
+  return SSO_OK;
+}
+
+void mark_assembled(sso_model* M, int precond) {
   M->assembled = true;
   M->assembled_precond = precond;
   ++M->assembly_gen;
+}
+
+// Element matrices, K, preconditioner and loads of one model (its own job).
+sso_status setup_model(sso_model* M, int precond, cudaStream_t s) {
+  SetupExtent x;
+  x.add(M);
+  sso_status st = setup_stages(M->d_job, 1, x, precond, s);
+  if (st != SSO_OK) return st;
+  if (precond == SSO_TWO_LEVEL && (st = setup_coarse(M, s)) != SSO_OK) return st;
+  mark_assembled(M, precond);
   return SSO_OK;
 }
 
@@ -1231,7 +1297,7 @@ sso_status prepare_model(ModelPrep& P) {
   put(M->d_brow, T.brow.data(), T.brow.size() * 4);
   put(M->d_diag, T.diag.data(), T.diag.size() * 4);
   put(M->d_cptr, T.cptr.data(), T.cptr.size() * 4);
-  put(M->d_csrc, T.csrc.data(), T.csrc.size() * 4);
+  put(M->d_epos, T.epos.data(), T.epos.size() * 4);
   put(M->d_nptr, T.nptr.data(), T.nptr.size() * 4);
   put(M->d_nsrc, T.nsrc.data(), T.nsrc.size() * 4);
   put(M->d_fixed, hm.fixed.data(), hm.fixed.size());
@@ -1296,6 +1362,10 @@ sso_status create_model_device(ModelPrep& P, cudaStream_t user_stream, bool own_
   if (e == cudaSuccess)
     e = cudaMemsetAsync(static_cast<unsigned char*>(M->arena) + P.prefix, 0, P.bytes - P.prefix,
                         s);
+  if (e == cudaSuccess) {
+    e = launch_store_setup_job(M->d_job, make_setup_job(M), s);
+    g_launches += 1;
+  }
   if (e == cudaSuccess && own_stream) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "uploading the model"));
   *out = M;
@@ -1644,7 +1714,17 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   c.take<AggRef>(std::max<size_t>(aggs.size(), 1));
   c.take<int>(n);
   c.take<int>(2);
+  c.take<SetupJob>(n);
   const size_t bytes = align_up(c.off, 256);
+  std::vector<SetupJob> jobs(n);
+  for (int s = 0; s < n; ++s) {
+    jobs[s] = make_setup_job(models[s]);
+    B->extent.add(models[s]);
+  }
+  if (n > 65535) {
+    delete B;
+    return fail(SSO_ERR_INVALID, "a batch holds at most 65535 models");
+  }
   cudaError_t e = cudaMalloc(&B->arena, bytes);
   if (e != cudaSuccess) {
     delete B;
@@ -1660,6 +1740,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   B->d_aggs = d.take<AggRef>(std::max<size_t>(aggs.size(), 1));
   B->d_csys = d.take<int>(n);
   B->d_ccount = d.take<int>(2);
+  B->d_jobs = d.take<SetupJob>(n);
   B->grid_restrict = (B->n_aggs + 7) / 8;  // one warp per (system, aggregate)
   B->grid_csolve = n * COARSE_ROW_BLOCKS;  // one CTA per work item
   const int ccount[2] = {B->n_aggs, n};
@@ -1685,6 +1766,9 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
                         B->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(B->d_ccount, ccount, sizeof(ccount), cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_jobs, jobs.data(), sizeof(SetupJob) * n, cudaMemcpyHostToDevice,
+                        B->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
   if (e != cudaSuccess) {
     sso_batch_destroy(B);
@@ -1761,17 +1845,22 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
     CK(cudaStreamWaitEvent(B->stream, M->ev_in, 0));
   }
   const bool prof = B->profiling != 0;
-  const size_t ew = 4 * (size_t)B->n_sys + 2;  // set-up wall-time events
-  if (prof && (st = ensure_setup_events(B, ew + 2)) != SSO_OK) return st;
-  if (prof) CK(cudaEventRecord(B->sev[ew], B->stream));
-  if ((st = fork_aux(B)) != SSO_OK) return st;
-  for (int s = 0; s < B->n_sys; ++s) {
-    st = setup_model(B->models[s], opts->precond, B->aux[s % B->aux.size()],
-                     prof ? &B->sev[4 * s] : nullptr);
-    if (st != SSO_OK) return st;
+  // set-up: one launch per stage for the whole batch (events: before the
+  // element kernels, after them, after assembly, after the preconditioner and
+  // loads, after the two-level coarse set-ups)
+  if (prof && (st = ensure_setup_events(B, 5)) != SSO_OK) return st;
+  st = setup_stages(B->d_jobs, B->n_sys, B->extent, opts->precond, B->stream,
+                    prof ? B->sev.data() : nullptr);
+  if (st != SSO_OK) return st;
+  if (opts->precond == SSO_TWO_LEVEL) {
+    // coarse spaces per model, on a pool of streams (they are independent)
+    if ((st = fork_aux(B)) != SSO_OK) return st;
+    for (int s = 0; s < B->n_sys; ++s)
+      if ((st = setup_coarse(B->models[s], B->aux[s % B->aux.size()])) != SSO_OK) return st;
+    if ((st = join_aux(B)) != SSO_OK) return st;
   }
-  if ((st = join_aux(B)) != SSO_OK) return st;
-  if (prof) CK(cudaEventRecord(B->sev[ew + 1], B->stream));
+  if (prof) CK(cudaEventRecord(B->sev[4], B->stream));
+  for (int s = 0; s < B->n_sys; ++s) mark_assembled(B->models[s], opts->precond);
   std::vector<char> active(B->n_sys, 1);
   sso_status run = batch_run(B, opts, false, active, stats);
   if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
@@ -1788,13 +1877,11 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
                        B->stream));
   CK(cudaStreamSynchronize(B->stream));
   if (prof) {
-    for (int s = 0; s < B->n_sys; ++s) {
-      const cudaEvent_t* e = &B->sev[4 * s];
-      B->prof_ms_el += elapsed_ms(e[0], e[1]);
-      B->prof_ms_asm += elapsed_ms(e[1], e[2]);
-      B->prof_ms_pre += elapsed_ms(e[2], e[3]);
-    }
-    B->prof_ms_setup += elapsed_ms(B->sev[ew], B->sev[ew + 1]);
+    const cudaEvent_t* e = B->sev.data();
+    B->prof_ms_el += elapsed_ms(e[0], e[1]);
+    B->prof_ms_asm += elapsed_ms(e[1], e[2]);
+    B->prof_ms_pre += elapsed_ms(e[2], e[3]);
+    B->prof_ms_setup += elapsed_ms(e[0], e[4]);
     B->prof_setups += B->n_sys;
   }
   for (int s = 0; s < B->n_sys; ++s) {
@@ -1852,7 +1939,7 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
     if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
   }
   const bool prof = B->profiling != 0;
-  const size_t e0 = 4 * (size_t)B->n_sys;
+  const size_t e0 = 5;  // after the solve's set-up events
   if (prof) {
     if ((st = ensure_setup_events(B, e0 + 2)) != SSO_OK) return st;
     CK(cudaEventRecord(B->sev[e0], B->stream));

@@ -273,12 +273,12 @@ __device__ void quad_material(S t, double E, double nu, double kx, double ky,
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) quad_stiffness_kernel(
-    int nq, const double* __restrict__ xyz, const int* __restrict__ conn,
+// Element e's 16 node-pair blocks: block (a, b) goes to
+// ke + 36 * pos(16 e + 4 a + b), pos = epos (assembly order) or the identity.
+__device__ __forceinline__ void quad_stiffness_element(
+    int e, const double* __restrict__ xyz, const int* __restrict__ conn,
     const double* __restrict__ props, double pressure, double gamma, double* __restrict__ ke,
-    double* __restrict__ fslot) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nq) return;
+    const int* __restrict__ epos, double* __restrict__ fslot) {
   double X[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -315,7 +315,10 @@ __global__ void __launch_bounds__(128) quad_stiffness_kernel(
     }
   }
 
-  double* out = ke + (size_t)e * 16 * 36;
+  auto block_out = [&](int a, int b) {
+    const int eb = 16 * e + 4 * a + b;
+    return ke + (size_t)(epos ? epos[eb] : eb) * 36;
+  };
   for (int a = 0; a < 4; ++a) {
     for (int b = a; b < 4; ++b) {
       double K[6][6];
@@ -386,13 +389,13 @@ __global__ void __launch_bounds__(128) quad_stiffness_kernel(
               Kg[3 * p + i][3 * r + j] =
                   g.R[0][i] * T[0][j] + g.R[1][i] * T[1][j] + g.R[2][i] * T[2][j];
         }
-      double* oab = out + (a * 4 + b) * 36;
+      double* oab = block_out(a, b);
 #pragma unroll
       for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < 6; ++j) oab[i * 6 + j] = Kg[i][j];
       if (a != b) {
-        double* oba = out + (b * 4 + a) * 36;
+        double* oba = block_out(b, a);
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -400,6 +403,23 @@ __global__ void __launch_bounds__(128) quad_stiffness_kernel(
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(128) quad_stiffness_kernel(
+    int nq, const double* __restrict__ xyz, const int* __restrict__ conn,
+    const double* __restrict__ props, double pressure, double gamma, double* __restrict__ ke,
+    double* __restrict__ fslot) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nq) quad_stiffness_element(e, xyz, conn, props, pressure, gamma, ke, nullptr, fslot);
+}
+
+// Set-up stage of a batch: quads of job blockIdx.y, blocks in assembly order.
+__global__ void __launch_bounds__(128) quad_setup_kernel(const SetupJob* __restrict__ jobs) {
+  const SetupJob& J = jobs[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= J.n_quads) return;
+  quad_stiffness_element(e, J.xyz, J.quad_conn, J.quad_props, J.pressure, J.gamma, J.kes,
+                         J.epos + 4 * (size_t)J.n_beams, J.fslot + 2 * (size_t)J.n_beams);
 }
 
 // ---------------------------------------------------------------------------
@@ -456,11 +476,12 @@ __device__ void beam_local(double L, const double* p, double k[12][12]) {
   }
 }
 
-__global__ void __launch_bounds__(128) beam_stiffness_kernel(
-    int nb, const double* __restrict__ xyz, const int* __restrict__ conn,
-    const double* __restrict__ props, double* __restrict__ ke) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nb) return;
+// Beam e's 4 node-pair blocks: block (a, b) goes to ke + 36 * pos(4 e + 2 a + b).
+__device__ __forceinline__ void beam_stiffness_element(int e, const double* __restrict__ xyz,
+                                                       const int* __restrict__ conn,
+                                                       const double* __restrict__ props,
+                                                       double* __restrict__ ke,
+                                                       const int* __restrict__ epos) {
   const int ni = conn[2 * e], nj = conn[2 * e + 1];
   double xi[3], xj[3];
 #pragma unroll
@@ -475,9 +496,10 @@ __global__ void __launch_bounds__(128) beam_stiffness_kernel(
   for (int k = 0; k < 6; ++k) p[k] = props[6 * e + k];
   double k[12][12];
   beam_local(L, p, k);
-  double* out = ke + (size_t)e * 4 * 36;
   for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
+      const int eb = 4 * e + 2 * a + b;
+      double* out = ke + (size_t)(epos ? epos[eb] : eb) * 36;
       for (int p3 = 0; p3 < 2; ++p3)
         for (int r3 = 0; r3 < 2; ++r3) {
           const int i0 = 6 * a + 3 * p3, j0 = 6 * b + 3 * r3;
@@ -488,10 +510,26 @@ __global__ void __launch_bounds__(128) beam_stiffness_kernel(
                         k[i0 + i][j0 + 2] * R[2][j];
           for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
-              out[(a * 2 + b) * 36 + (3 * p3 + i) * 6 + 3 * r3 + j] =
+              out[(3 * p3 + i) * 6 + 3 * r3 + j] =
                   R[0][i] * T[0][j] + R[1][i] * T[1][j] + R[2][i] * T[2][j];
         }
+    }
 }
+
+__global__ void __launch_bounds__(128) beam_stiffness_kernel(
+    int nb, const double* __restrict__ xyz, const int* __restrict__ conn,
+    const double* __restrict__ props, double* __restrict__ ke) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nb) beam_stiffness_element(e, xyz, conn, props, ke, nullptr);
+}
+
+__global__ void __launch_bounds__(128) beam_setup_kernel(const SetupJob* __restrict__ jobs) {
+  const SetupJob& J = jobs[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < J.n_beams) beam_stiffness_element(e, J.xyz, J.beam_conn, J.beam_props, J.kes, J.epos);
+}
+
+__global__ void store_setup_job_kernel(SetupJob* dst, const SetupJob job) { *dst = job; }
 
 // ---------------------------------------------------------------------------
 // Adjoint contractions (Eq. 6).  For every element the scalar
@@ -743,6 +781,25 @@ cudaError_t launch_beam_stiffness(int n_beams, const double* xyz, const int* con
                                   const double* props, double* ke, cudaStream_t s) {
   if (n_beams <= 0) return cudaSuccess;
   beam_stiffness_kernel<<<(n_beams + 127) / 128, 128, 0, s>>>(n_beams, xyz, conn, props, ke);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_setup_job(SetupJob* dst, const SetupJob& job, cudaStream_t s) {
+  store_setup_job_kernel<<<1, 1, 0, s>>>(dst, job);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_beams(const SetupJob* jobs, int n_jobs, int max_beams, cudaStream_t s) {
+  if (n_jobs <= 0 || max_beams <= 0) return cudaSuccess;
+  if (n_jobs > 65535) return cudaErrorInvalidValue;
+  beam_setup_kernel<<<dim3((max_beams + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_quads(const SetupJob* jobs, int n_jobs, int max_quads, cudaStream_t s) {
+  if (n_jobs <= 0 || max_quads <= 0) return cudaSuccess;
+  if (n_jobs > 65535) return cudaErrorInvalidValue;
+  quad_setup_kernel<<<dim3((max_quads + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 

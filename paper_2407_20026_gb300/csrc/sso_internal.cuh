@@ -164,6 +164,53 @@ __host__ __device__ constexpr int sym6(int a, int c) {
 }
 
 // ---------------------------------------------------------------------------
+// Set-up of one structure: element matrices and area-load shares, assembly of
+// K64 and K32, the (block-)Jacobi preconditioner, the load vector.  The
+// element kernels write every 6x6 element block to its place in assembly
+// order (epos: element block -> position, the inverse of the sorted scatter
+// map), so the blocks summed into K block b are kes[cptr[b] .. cptr[b+1]),
+// contiguous, and assembly reads one stream.  Set-up kernels take an array of
+// jobs and run one job per grid row (blockIdx.y): one launch per stage sets
+// up a whole batch.
+struct SetupJob {
+  const double* xyz;
+  const int* beam_conn;
+  const double* beam_props;
+  const int* quad_conn;
+  const double* quad_props;
+  int n_beams, n_quads, n_nodes, n_blocks;
+  double pressure, gamma;
+  const int* epos;        // [4 n_beams + 16 n_quads]
+  double* kes;            // element blocks in assembly order [n_eb][36]
+  double* fslot;          // area-load share per (element, node) slot
+  const int* cptr;        // [n_blocks + 1]
+  const int* brow;        // block row of every block
+  const int* col;         // block column of every block
+  const uint8_t* fixed;   // [6 n_nodes]
+  double* K64;
+  float* K32;
+  int* err;               // set by a non-positive preconditioner pivot
+  const int* diag;        // diagonal block of every node
+  double* M64;
+  float* M32;
+  const int* nptr;        // node incidence (slots by node)
+  const int* nsrc;
+  const double* nodal_load;
+  double* f;
+};
+
+// Launchers (set-up stages; elements.cu and assembly.cu).  max_*: the largest
+// count over the jobs (the grid's x extent).  n_jobs <= 65535.
+cudaError_t launch_store_setup_job(SetupJob* dst, const SetupJob& job, cudaStream_t s);
+cudaError_t launch_setup_beams(const SetupJob* jobs, int n_jobs, int max_beams, cudaStream_t s);
+cudaError_t launch_setup_quads(const SetupJob* jobs, int n_jobs, int max_quads, cudaStream_t s);
+cudaError_t launch_setup_assemble(const SetupJob* jobs, int n_jobs, int max_blocks,
+                                  cudaStream_t s);
+cudaError_t launch_setup_precond(const SetupJob* jobs, int n_jobs, int max_nodes, int kind,
+                                 cudaStream_t s);
+cudaError_t launch_setup_loads(const SetupJob* jobs, int n_jobs, int max_nodes, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Launchers (elements.cu)
 cudaError_t launch_beam_stiffness(int n_beams, const double* xyz, const int* conn,
                                   const double* props, double* ke, cudaStream_t s);
@@ -187,9 +234,6 @@ cudaError_t launch_simp(int n_quads, const double* rho, const double* E0, double
                         double* props, cudaStream_t s);
 
 // Launchers (assembly.cu)
-cudaError_t launch_assemble(int n_blocks, const int* cptr, const int* csrc, const double* ke,
-                            const int* brow, const int* col, const uint8_t* fixed,
-                            double* K64, float* K32, cudaStream_t s);
 cudaError_t launch_precond(int n_nodes, int kind, const int* diag_idx, const double* K64,
                            double* M64, float* M32, int* err_flag, cudaStream_t s);
 cudaError_t launch_node_gather(int n_nodes, const int* nptr, const int* nsrc, int slot_quad0,

@@ -250,9 +250,9 @@ class Batch:
 
     def setup_times(self):
         """Device ms since profiling was enabled: dict with elements, assembly,
-        precond (+ loads) summed per model, setup_wall (elapsed time of the
-        concurrent set-ups), adjoint (elapsed contraction passes), setups,
-        gradients."""
+        precond (+ loads) -- each one launch for the whole batch per solve --,
+        setup_wall (the whole set-up, two-level coarse spaces included),
+        adjoint (elapsed contraction passes), setups, gradients."""
         v = [ctypes.c_double() for _ in range(5)]
         n = [ctypes.c_int64() for _ in range(2)]
         _lib.check(_lib.load().sso_batch_setup_times(self._h, *[ctypes.byref(x) for x in v],
