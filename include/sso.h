@@ -13,8 +13,9 @@
  *   - the supports V u = b with b = 0 (Eqs. 2-3), imposed by eliminating the
  *     fixed DOFs (identity rows/columns in K, zero load), which gives the same
  *     u as the Lagrange-multiplier system K_aug u_aug = f_aug;
- *   - the solve of K u = f by Jacobi / block-Jacobi preconditioned CG, in FP64
- *     or in FP32 inside FP64 iterative refinement;
+ *   - the solve of K u = f by Jacobi / block-Jacobi preconditioned CG, in FP64,
+ *     in FP32 inside FP64 iterative refinement, or (small systems, one CTA
+ *     each) in double-float arithmetic;
  *   - compliance C = f^T u and the adjoint sensitivity of
  *     J = w C + g^T u (Eqs. 5-6): K^T lambda = dJ/du,
  *     dJ/dp = dJ/dp|explicit - lambda^T (dK/dp u - df/dp), for p = the z
@@ -77,7 +78,17 @@ typedef struct {
   double gamma;               /* self-weight density (N/m^3); quad e carries gamma*t_e along -Z */
 } sso_mesh;
 
-typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1 } sso_precision;
+/* SSO_F32X2: the whole CG of each system in one CTA and one launch, in
+ * double-float arithmetic (every value an unevaluated sum of two FP32
+ * numbers, about 48 significant bits, on the FP32 pipes); K is read as its
+ * FP32 rounding plus the FP32 rounding of the remainder (K64 - K32).  For
+ * small systems (up to a few thousand DOF), whose solve is otherwise
+ * dominated by launch and synchronisation latency: one SM works per system,
+ * so a large system is slow.  Jacobi or block-Jacobi; batches and models
+ * (not the server).  Convergence is tested on the residual b - K u recomputed
+ * in double-float from both parts of K; max_sweeps caps the restarts from
+ * it, and a restart that lowers the residual less than 2x ends the solve. */
+typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1, SSO_F32X2 = 2 } sso_precision;
 /* SSO_TWO_LEVEL: block-Jacobi plus a coarse correction over the rigid-body
  * modes of node aggregates (z = M_b^-1 r + P A_c^-1 P^T r, A_c = P^T K P);
  * FP32_IR only; batches, models and the server.

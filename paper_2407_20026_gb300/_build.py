@@ -8,7 +8,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsso.so")
 SOURCES = ["elements.cu", "assembly.cu", "pcg.cu", "coarse.cu", "chain.cu", "spmv.cu", "spmv_noalloc.cu",
-           "capi.cu"]
+           "small.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

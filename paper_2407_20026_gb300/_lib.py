@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "SINGULAR", 4: "NOT_CONVERGE
 
 FP64 = 0
 FP32_IR = 1
+F32X2 = 2
 JACOBI = 0
 BLOCK_JACOBI = 1
 TWO_LEVEL = 2

@@ -5,10 +5,11 @@
 // wrote every element block to its place in assembly order (sorted by K block,
 // then by element block id, once per topology), so K block b is the sum of
 // kes[cptr[b] .. cptr[b+1]) in that order -- fixed, hence bit-reproducible
-// without atomics.  One thread per (block, pair of entries) reads 16-byte
-// vectors of consecutive element blocks, so a warp's loads and its K64 / K32
-// stores are contiguous runs; the kernel is bound by HBM.  A batch of
-// structures is set up by one launch per stage (one structure per grid row).
+// without atomics.  A chunk of consecutive K blocks therefore reads one
+// contiguous range, which a CTA brings into shared memory with a single bulk
+// copy; its K64 / K32 stores are contiguous runs too.  The kernel is bound by
+// HBM.  A batch of structures is set up by one launch per stage (one
+// structure per grid row).
 #include <math.h>
 
 #include "sso_internal.cuh"
@@ -18,42 +19,86 @@ namespace {
 
 // Pairs of entries per 6x6 block (36 doubles = 18 double2).
 constexpr int PAIRS = 18;
+// K blocks per CTA, and the shared-memory slab that receives their element
+// blocks in one bulk copy (a quad mesh's chunk holds ~1.8 contributions per
+// block, at most 4; a chunk whose range does not fit -- a hub node's
+// diagonal block -- is summed straight from global memory).
+constexpr int ASM_CHUNK = 64;
+constexpr int ASM_SLAB = 40 * 1024;
+constexpr int ASM_THREADS = 256;
 
-__global__ void __launch_bounds__(256) assemble_sorted_kernel(const SetupJob* __restrict__ jobs) {
+// One CTA per chunk of ASM_CHUNK consecutive K blocks of job blockIdx.y.  The
+// chunk's element blocks are the contiguous range kes[cptr[b0] .. cptr[b0 +
+// n)): thread 0 copies it into shared memory with one bulk copy (the copy
+// engine keeps many KB in flight per SM without registers), while the
+// threads stage the chunk's cptr, block rows and columns; then each thread
+// sums (block, pair) items from shared memory in cptr order and writes K64
+// and its FP32 rounding K32.  Supports turn fixed rows / columns into identity
+// rows / columns.  The wait for the copy is bounded: a CTA that gives up sets
+// *err = 2 (reported as a CUDA failure) and writes nothing.
+__global__ void __launch_bounds__(ASM_THREADS) assemble_bulk_kernel(
+    const SetupJob* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char asm_slab[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int s_cptr[ASM_CHUNK + 1], s_brow[ASM_CHUNK], s_col[ASM_CHUNK];
+  __shared__ int s_staged;
   const SetupJob& J = jobs[blockIdx.y];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *J.err = 0;  // the preconditioner runs next
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)J.n_blocks * PAIRS) return;
-  const int b = (int)(idx / PAIRS);
-  const int p = (int)(idx - (long long)b * PAIRS);
-  const int c0 = __ldg(J.cptr + b), c1 = __ldg(J.cptr + b + 1);
-  const double2* src = reinterpret_cast<const double2*>(J.kes) + p;
-  // the first four contributions are loaded together (a quad mesh has at
-  // most four per block), then summed in order
-  double2 v[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    v[k] = c0 + k < c1 ? __ldcs(src + (size_t)(c0 + k) * PAIRS) : make_double2(0.0, 0.0);
-  double sx = 0.0, sy = 0.0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (c0 + k < c1) {
-      sx += v[k].x;
-      sy += v[k].y;
+  const int b0 = blockIdx.x * ASM_CHUNK;
+  const int t = threadIdx.x;
+  if (blockIdx.x == 0 && t == 0) *J.err = 0;  // the preconditioner runs next
+  if (b0 >= J.n_blocks) return;  // uniform over the CTA
+  const int nb = min(ASM_CHUNK, J.n_blocks - b0);
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    const int c0 = __ldg(J.cptr + b0), c1 = __ldg(J.cptr + b0 + nb);
+    const uint32_t bytes = (uint32_t)(c1 - c0) * 288u;
+    const bool fits = (long long)(c1 - c0) * 288 <= ASM_SLAB;
+    s_staged = fits;
+    fence_proxy_async();
+    if (fits && bytes > 0) {
+      mbar_arrive_tx(&bar, bytes);
+      bulk_g2s(asm_slab, J.kes + (size_t)c0 * 36, bytes, &bar);
+    } else {
+      mbar_arrive(&bar);
     }
-  for (int i = c0 + 4; i < c1; ++i) {
-    const double2 w = __ldcs(src + (size_t)i * PAIRS);
-    sx += w.x;
-    sy += w.y;
   }
-  // supports: fixed rows and columns become identity rows and columns
-  const int r = p / 3, c = 2 * (p - 3 * r);
-  const int ni = __ldg(J.brow + b), nj = __ldg(J.col + b);
-  const bool fr = J.fixed[6 * ni + r] != 0;
-  if (fr || J.fixed[6 * nj + c]) sx = (ni == nj && r == c) ? 1.0 : 0.0;
-  if (fr || J.fixed[6 * nj + c + 1]) sy = (ni == nj && r == c + 1) ? 1.0 : 0.0;
-  reinterpret_cast<double2*>(J.K64)[idx] = make_double2(sx, sy);
-  reinterpret_cast<float2*>(J.K32)[idx] = make_float2((float)sx, (float)sy);
+  if (t <= nb) s_cptr[t] = __ldg(J.cptr + b0 + t);
+  if (t < nb) {
+    s_brow[t] = __ldg(J.brow + b0 + t);
+    s_col[t] = __ldg(J.col + b0 + t);
+  }
+  __syncthreads();
+  const bool staged = s_staged != 0;
+  if (!mbar_wait(&bar, 0)) {
+    if (t == 0) atomicExch(J.err, 2);
+    mbar_wait(&bar, 0);  // the copy may still land; give it one more bounded wait
+    return;
+  }
+  const int cbase = s_cptr[0];
+  const double2* slab = reinterpret_cast<const double2*>(asm_slab);
+  const double2* gsrc = reinterpret_cast<const double2*>(J.kes);
+  double2* K64 = reinterpret_cast<double2*>(J.K64) + (size_t)b0 * PAIRS;
+  float2* K32 = reinterpret_cast<float2*>(J.K32) + (size_t)b0 * PAIRS;
+  for (int item = t; item < nb * PAIRS; item += ASM_THREADS) {
+    const int lb = item / PAIRS;
+    const int p = item - lb * PAIRS;
+    const int c0 = s_cptr[lb], c1 = s_cptr[lb + 1];
+    double sx = 0.0, sy = 0.0;
+    for (int c = c0; c < c1; ++c) {
+      const double2 v = staged ? slab[(size_t)(c - cbase) * PAIRS + p]
+                               : __ldcs(gsrc + (size_t)c * PAIRS + p);
+      sx += v.x;
+      sy += v.y;
+    }
+    const int r = p / 3, cc = 2 * (p - 3 * r);
+    const int ni = s_brow[lb], nj = s_col[lb];
+    const bool fr = J.fixed[6 * ni + r] != 0;
+    if (fr || J.fixed[6 * nj + cc]) sx = (ni == nj && r == cc) ? 1.0 : 0.0;
+    if (fr || J.fixed[6 * nj + cc + 1]) sy = (ni == nj && r == cc + 1) ? 1.0 : 0.0;
+    K64[item] = make_double2(sx, sy);
+    K32[item] = make_float2((float)sx, (float)sy);
+  }
 }
 
 // Block-Jacobi: Cholesky-invert the 6x6 diagonal block of every node (FP64).
@@ -69,7 +114,7 @@ __device__ __forceinline__ void precond_node(int n, int kind, const int* __restr
     for (int i = 0; i < 6; ++i) {
       const double d = B[7 * i];
       const double inv = d > 0.0 ? 1.0 / d : 0.0;
-      if (!(d > 0.0)) atomicExch(err, 1);
+      if (!(d > 0.0)) atomicMax(err, 1);
       M64[6 * n + i] = inv;
       M32[6 * n + i] = (float)inv;
     }
@@ -93,7 +138,7 @@ __device__ __forceinline__ void precond_node(int n, int kind, const int* __restr
       L[i][j] = t / L[j][j];
     }
   }
-  if (!ok) atomicExch(err, 1);
+  if (!ok) atomicMax(err, 1);
   // inverse of L (lower), then M = L^-T L^-1
   double Li[6][6];
   for (int j = 0; j < 6; ++j) {
@@ -185,8 +230,15 @@ cudaError_t launch_setup_assemble(const SetupJob* jobs, int n_jobs, int max_bloc
                                   cudaStream_t s) {
   if (n_jobs <= 0 || max_blocks <= 0) return cudaSuccess;
   if (n_jobs > 65535) return cudaErrorInvalidValue;
-  const long long n = (long long)max_blocks * PAIRS;
-  assemble_sorted_kernel<<<dim3((unsigned)((n + 255) / 256), n_jobs), 256, 0, s>>>(jobs);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(assemble_bulk_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, ASM_SLAB);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const unsigned chunks = (unsigned)((max_blocks + ASM_CHUNK - 1) / ASM_CHUNK);
+  assemble_bulk_kernel<<<dim3(chunks, n_jobs), ASM_THREADS, ASM_SLAB, s>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -166,7 +167,8 @@ struct sso_model {
   size_t arena_bytes = 0;  // size of the arena (fixed at creation)
   bool own_arena = true;   // false: the arena belongs to a server's pool
   // topology
-  int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_brow, *d_diag, *d_cptr, *d_epos,
+  int *d_beam_conn, *d_quad_conn, *d_row_ptr, *d_col, *d_hslot, *d_brow, *d_diag, *d_cptr,
+      *d_epos,
       *d_nptr, *d_nsrc;
   uint8_t* d_fixed;
   // design
@@ -253,6 +255,9 @@ struct sso_batch {
   int grid_restrict = 0, grid_csolve = 0;
   // the models' set-up jobs (one launch per set-up stage for the whole batch)
   SetupJob* d_jobs = nullptr;
+  // SSO_F32X2: the systems being solved (one CTA each)
+  int* d_list = nullptr;
+  std::vector<int> h_list;
   SetupExtent extent;
   cudaEvent_t ev = nullptr;
   // kernel timing (sso_batch_set_profiling): events around every A and B
@@ -588,6 +593,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_quad_conn = c.take<int>(4 * (size_t)M->n_quads);
   M->d_row_ptr = c.take<int>(n + 1);
   M->d_col = c.take<int>(M->n_blocks);
+  M->d_hslot = c.take<int>(M->n_blocks);
   M->d_brow = c.take<int>(M->n_blocks);
   M->d_diag = c.take<int>(n);
   M->d_cptr = c.take<int>((size_t)M->n_blocks + 1);
@@ -656,8 +662,10 @@ size_t layout_model(sso_model* M, void* base) {
 
 sso_status check_options(const sso_options* o) {
   if (!o) return fail(SSO_ERR_INVALID, "options is NULL");
-  if (o->precision != SSO_FP64 && o->precision != SSO_FP32_IR)
-    return fail(SSO_ERR_INVALID, "precision must be SSO_FP64 or SSO_FP32_IR");
+  if (o->precision != SSO_FP64 && o->precision != SSO_FP32_IR && o->precision != SSO_F32X2)
+    return fail(SSO_ERR_INVALID, "precision must be SSO_FP64, SSO_FP32_IR or SSO_F32X2");
+  if (o->precision == SSO_F32X2 && o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI)
+    return fail(SSO_ERR_INVALID, "SSO_F32X2 needs SSO_JACOBI or SSO_BLOCK_JACOBI");
   if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI && o->precond != SSO_TWO_LEVEL &&
       o->precond != SSO_CHAIN)
     return fail(SSO_ERR_INVALID,
@@ -1014,7 +1022,20 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   B->h_flag[1] = 0;
   CK(cudaMemcpyAsync(B->d_n_active, B->h_flag, 2 * sizeof(int), cudaMemcpyHostToDevice,
                      B->stream));
-  if (n_act > 0) {
+  if (n_act > 0 && o->precision == SSO_F32X2) {
+    // every active system's whole CG in one CTA of one launch
+    B->h_list.clear();
+    int groups = 1;
+    for (int s = 0; s < B->n_sys; ++s)
+      if (active[s]) {
+        B->h_list.push_back(s);
+        groups = std::max(groups, (B->models[s]->n_nodes + NODES_PER_WARP - 1) / NODES_PER_WARP);
+      }
+    CK(cudaMemcpyAsync(B->d_list, B->h_list.data(), B->h_list.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, B->stream));
+    const int threads = 32 * std::min(32, groups);
+    CL(launch_small_cg(B->d_sys, B->d_list, (int)B->h_list.size(), threads, B->stream), 2);
+  } else if (n_act > 0) {
     const bool two_level = o->precond == SSO_TWO_LEVEL;
     sso_status st = batch_graph(B, fp64, o->iters_per_launch, two_level);
     if (st != SSO_OK) return st;
@@ -1283,6 +1304,18 @@ sso_status prepare_model(ModelPrep& P) {
   sso_default_options(&M->last_opts);
   P.tiles.reserve(M->n_tiles);
   for (int t = 0; t < M->n_tiles; ++t) P.tiles.push_back(make_tile(M, -1, t));
+  // every block's column slot in its tile's staged halo (the runs laid end
+  // to end; the same rule as the consumers' slot of their own node)
+  std::vector<int> hslot(T.col.size(), 0);
+  for (const TileDesc& d : P.tiles) {
+    if (!d.stage) continue;
+    const int v1 = d.nv[1] ? d.vlo[1] : INT_MAX, v2 = d.nv[2] ? d.vlo[2] : INT_MAX;
+    const int sh0 = -d.vlo[0], sh1 = d.nv[0] - d.vlo[1], sh2 = d.nv[0] + d.nv[1] - d.vlo[2];
+    for (int j = d.j0; j < d.j0 + d.nblk; ++j) {
+      const int c = T.col[j];
+      hslot[j] = c + (c >= v2 ? sh2 : (c >= v1 ? sh1 : sh0));
+    }
+  }
   // arena offsets (base 0) and the image of the arrays that start it
   P.bytes = layout_model(M, nullptr);
   P.prefix = (size_t)reinterpret_cast<uintptr_t>(M->d_ke);
@@ -1294,6 +1327,7 @@ sso_status prepare_model(ModelPrep& P) {
   put(M->d_quad_conn, hm.quad_conn.data(), hm.quad_conn.size() * 4);
   put(M->d_row_ptr, T.row_ptr.data(), T.row_ptr.size() * 4);
   put(M->d_col, T.col.data(), T.col.size() * 4);
+  put(M->d_hslot, hslot.data(), hslot.size() * 4);
   put(M->d_brow, T.brow.data(), T.brow.size() * 4);
   put(M->d_diag, T.diag.data(), T.diag.size() * 4);
   put(M->d_cptr, T.cptr.data(), T.cptr.size() * 4);
@@ -1662,6 +1696,8 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     D.precond = SSO_BLOCK_JACOBI;
     D.row_ptr = M->d_row_ptr;
     D.col = M->d_col;
+  D.hslot = M->d_hslot;
+    D.hslot = M->d_hslot;
     D.K32 = M->d_K32;
     D.K64 = M->d_K64;
     D.M32 = M->d_M32;
@@ -1691,6 +1727,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     D.y = M->d_cy;
     D.cdot = M->d_cdot;
     D.zb = M->d_zb;
+    D.klo = reinterpret_cast<float*>(M->d_ke);
     for (int k = 0; k < M->n_tiles; ++k) tiles.push_back(make_tile(M, s, k));
   }
   B->n_tiles = (int)tiles.size();
@@ -1715,6 +1752,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   c.take<int>(n);
   c.take<int>(2);
   c.take<SetupJob>(n);
+  c.take<int>(n);
   const size_t bytes = align_up(c.off, 256);
   std::vector<SetupJob> jobs(n);
   for (int s = 0; s < n; ++s) {
@@ -1741,6 +1779,7 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
   B->d_csys = d.take<int>(n);
   B->d_ccount = d.take<int>(2);
   B->d_jobs = d.take<SetupJob>(n);
+  B->d_list = d.take<int>(n);
   B->grid_restrict = (B->n_aggs + 7) / 8;  // one warp per (system, aggregate)
   B->grid_csolve = n * COARSE_ROW_BLOCKS;  // one CTA per work item
   const int ccount[2] = {B->n_aggs, n};
@@ -1888,7 +1927,10 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
     sso_model* M = B->models[s];
     M->solved = true;
     M->last_opts = *opts;
-    if (errs[s]) {
+    if (errs[s] >= 2) {
+      if (stats) stats[s].status = SSO_ERR_CUDA;
+      run = fail(SSO_ERR_CUDA, "assembly gave up waiting for a bulk copy (device fault?)");
+    } else if (errs[s]) {
       if (stats) stats[s].status = SSO_ERR_SINGULAR;
       if (run == SSO_OK) run = fail(SSO_ERR_SINGULAR, "a diagonal block of K is not positive "
                                                       "definite (unsupported mechanism?)");
@@ -2324,6 +2366,7 @@ void fill_sysdesc(SysDesc& D, sso_model* M, int precond) {
   D.precond = precond;
   D.row_ptr = M->d_row_ptr;
   D.col = M->d_col;
+  D.hslot = M->d_hslot;
   D.K32 = M->d_K32;
   D.K64 = M->d_K64;
   D.M32 = M->d_M32;
@@ -2353,6 +2396,7 @@ void fill_sysdesc(SysDesc& D, sso_model* M, int precond) {
   D.y = M->d_cy;
   D.cdot = M->d_cdot;
   D.zb = M->d_zb;
+  D.klo = reinterpret_cast<float*>(M->d_ke);
 }
 
 void init_scalars(SysScalars& S, const sso_options& o) {
@@ -2378,6 +2422,8 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
   if (st != SSO_OK) return st;
   if (opts->precond == SSO_CHAIN)
     return fail(SSO_ERR_INVALID, "the server runs the CG preconditioners only (not SSO_CHAIN)");
+  if (opts->precision == SSO_F32X2)
+    return fail(SSO_ERR_INVALID, "the server runs SSO_FP64 or SSO_FP32_IR (not SSO_F32X2)");
   if (max_systems <= 0 || max_tiles <= 0 || hbm_budget_bytes == 0)
     return fail(SSO_ERR_INVALID, "need max_systems > 0, max_tiles > 0, budget > 0");
   sso_server* S = new sso_server();
@@ -2658,7 +2704,7 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
       const SysScalars& sc = B->h_sc[slot];
       int err = 0;
       CK(cudaMemcpy(&err, R->M->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-      R->stats.status = err ? SSO_ERR_SINGULAR : sc.status;
+      R->stats.status = err >= 2 ? SSO_ERR_CUDA : err ? SSO_ERR_SINGULAR : sc.status;
       R->stats.iterations = sc.iters;
       R->stats.sweeps = sc.sweeps;
       R->stats.rel_residual = sc.ff > 0.0 ? std::sqrt(sc.rr64 / sc.ff) : 0.0;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_invert_kernel(
   double a[36], ai[36];
   ld36(A + (size_t)i * 36, a);
   if (!spd_inv6(a, ai)) {
-    atomicExch(err, 1);
+    atomicMax(err, 1);
 #pragma unroll
     for (int q = 0; q < 36; ++q) ai[q] = 0.0;
   }
@@ -221,7 +221,7 @@ __global__ void chain_last_kernel(const double* __restrict__ A, const double* __
   double a[36], ai[36];
   ld36(A, a);
   if (!spd_inv6(a, ai)) {
-    atomicExch(err, 1);
+    atomicMax(err, 1);
     for (int q = 0; q < 6; ++q) x[q] = 0.0;
     return;
   }

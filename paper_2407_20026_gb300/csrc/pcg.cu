@@ -65,41 +65,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Double-float sums of FP32 products: an unevaluated sum hi + lo of two
-// floats, formed only with error-free transformations (the exact product
-// a b = p + fma(a, b, -p); Knuth's two-sum; a fast two-sum to renormalise),
-// so a dot product of FP32 vectors is accumulated to about 48 significant
-// bits on the FP32 pipes.  The FP32 CG kernels sum a warp's terms this way
-// and convert once to FP64, where every later sum (tiles, chunks) happens:
-// on this GPU an FP64 instruction costs a warp about 64 FP32 ones.
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ DF df_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float v = __fsub_rn(s, a.hi);
-  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  const float hi = __fadd_rn(s, e);
-  return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
-}
-// Fixed-shape tree over the warp; the sum is in lane 0.
-__device__ __forceinline__ DF df_warp_sum(DF x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    DF y;
-    y.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
-    y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
-    x = df_add(x, y);
-  }
-  return x;
-}
-__device__ __forceinline__ double df_double(DF x) { return (double)x.hi + (double)x.lo; }
-
 // Programmatic dependent launch: a CG kernel lets the next kernel of the
 // stream begin launching as soon as all of its own CTAs run (its grids are one
 // wave, so waiting CTAs never hold back its own), and waits for the previous
@@ -655,62 +620,6 @@ __global__ void __launch_bounds__(NT, 4) pcg_b_kernel(const TileDesc* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// mbarrier and bulk-copy (1-D TMA) helpers.  Every wait is bounded.
-constexpr long long kWaitPolls = 1LL << 22;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// Announces `bytes` more of asynchronous copies in the current phase without
-// arriving (the phase then also waits for a later arrival).
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  for (long long i = 0; i < kWaitPolls; ++i)
-    if (mbar_test(bar, parity)) return true;
-  return false;
-}
-
-// ---------------------------------------------------------------------------
 // Kernel B for the FP32 CG.  A warp owns a tile (TILE nodes) at a time and
 // works from its own two-stage slice of shared memory.  While it computes one
 // tile, lane 0 has already issued the bulk copies (cp.async.bulk) of the
@@ -1236,6 +1145,7 @@ struct StageInfo {
   // halo runs in the stage: column c sits at slot c + shift[k] (nodes) for the
   // last run k whose first node is <= c (first nodes of unused runs: INT_MAX)
   int v1, v2, sh0, sh1, sh2;
+  int nhalo;  // halo nodes in the stage (mode 1)
 };
 
 __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
@@ -1285,7 +1195,8 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       fence_proxy_async();
       mbar_expect_tx(&full[pre], kb + cb + 2 * vb + rb);
       bulk_g2s(st, S->K32 + (size_t)t.j0 * 36, kb, &full[pre]);
-      bulk_g2s(st + ST_OFF_C, S->col + t.cb, cb, &full[pre]);
+      // a tile staged whole reads its columns as halo slots
+      bulk_g2s(st + ST_OFF_C, (t.stage ? S->hslot : S->col) + t.cb, cb, &full[pre]);
       bulk_g2s(st + ST_OFF_R, S->row_ptr + t.rb, rb, &full[pre]);
     }
     pdl_wait();
@@ -1296,7 +1207,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
     struct {
       const float *z, *K32;
       float *p0, *p1, *q;
-      const int *col, *row_ptr;
+      const int *col, *hslot, *row_ptr;
       double* part_a;
       int tile0;
     } P = {};
@@ -1322,6 +1233,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         P.p1 = (float*)S->p1;
         P.q = (float*)S->q;
         P.col = S->col;
+        P.hslot = S->hslot;
         P.row_ptr = S->row_ptr;
         P.part_a = S->part_a;
         P.tile0 = S->tile0;
@@ -1347,6 +1259,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.sh0 = -td.vlo[0];
       inf.sh1 = td.nv[0] - td.vlo[1];
       inf.sh2 = td.nv[0] + td.nv[1] - td.vlo[2];
+      inf.nhalo = td.nv[0] + td.nv[1] + td.nv[2];
       ++issued;
       if (k < pre) {
         // K, columns and row_ptr already on their way; the halo (copied
@@ -1383,7 +1296,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
         fence_proxy_async();
         mbar_arrive_tx(&full[s], kb + cb + 2 * vb + rb);
         bulk_g2s(st, P.K32 + (size_t)td.j0 * 36, kb, &full[s]);
-        bulk_g2s(st + ST_OFF_C, P.col + td.cb, cb, &full[s]);
+        bulk_g2s(st + ST_OFF_C, (td.stage ? P.hslot : P.col) + td.cb, cb, &full[s]);
         if (td.stage) {
           uint32_t off = 0u;  // bytes into each vector slab
           for (int k = 0; k < HALO_RUNS; ++k) {
@@ -1429,6 +1342,18 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.state = read_state(sys[inf.sys].sc).state;
       inf.run_end = tile + 1 >= end || tiles[tile + 1].sys != inf.sys;
     }
+    // A staged CG tile: form w = z + beta p once per halo entry, in place of
+    // z in the stage (every row reading a column then loads w alone).  The
+    // barrier is taken for every tile by every consumer warp, dry or not.
+    if (!dry && inf.state == ST_PCG && inf.mode == 1) {
+      unsigned char* st = ring + s * ST_STAGE;
+      float* Ws = reinterpret_cast<float*>(st + ST_OFF_Z);
+      const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P);
+      const int nh = 6 * inf.nhalo;
+      const float beta = inf.beta;
+      for (int e = t; e < nh; e += NT) Ws[e] = fmaf(beta, Ps[e], Ws[e]);
+    }
+    consumer_sync();
     const SysDesc& S = sys[inf.sys];
     SysScalars* sc = S.sc;
     const int real_state = inf.state;
@@ -1443,30 +1368,25 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       float* pnew = inf.pnew;
       const float beta = inf.beta;
       if (act) {
-        float acc = 0.f, zi, pi_old;
+        float acc = 0.f, zi = 0.f, pi_old = 0.f, wi = 0.f;
         if (inf.mode == 1) {
           const unsigned char* st = ring + s * ST_STAGE;
           const int* Rs = reinterpret_cast<const int*>(st + ST_OFF_R) - inf.rb;
           const int j0 = Rs[node], j1 = Rs[node + 1];
           const float* Ks = reinterpret_cast<const float*>(st) + (size_t)(j0 - inf.j0) * 36 + rr * 6;
-          const int* Cs = reinterpret_cast<const int*>(st + ST_OFF_C) - inf.cb;
-          const float* Zs = reinterpret_cast<const float*>(st + ST_OFF_Z);
-          const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P);
+          const int* Hs = reinterpret_cast<const int*>(st + ST_OFF_C) - inf.cb;
+          const float* Ws = reinterpret_cast<const float*>(st + ST_OFF_Z);
           const int v1 = inf.v1, v2 = inf.v2, sh0 = inf.sh0, sh1 = inf.sh1, sh2 = inf.sh2;
-          auto slot = [&](int c) { return 6 * (c + (c >= v2 ? sh2 : (c >= v1 ? sh1 : sh0))); };
           for (int j = j0; j < j1; ++j) {
-            const int o = slot(Cs[j]);
-            float kv[6], zv[6], pv[6];
+            float kv[6], wv[6];
             ld6s(Ks, kv);
-            ld6s(Zs + o, zv);
-            ld6s(Ps + o, pv);
+            ld6s(Ws + 6 * Hs[j], wv);
             Ks += 36;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc = fmaf(kv[q], fmaf(beta, pv[q], zv[q]), acc);
+            for (int q = 0; q < 6; ++q) acc = fmaf(kv[q], wv[q], acc);
           }
-          const int oi = slot(node) + rr;
-          zi = Zs[oi];
-          pi_old = Ps[oi];
+          const int oi = 6 * (node + (node >= v2 ? sh2 : (node >= v1 ? sh1 : sh0))) + rr;
+          wi = Ws[oi];
         } else if (inf.mode == 2) {
           // K rows, columns and row_ptr from the stage; z and p gathered from
           // global memory, three columns in flight at a time
@@ -1507,7 +1427,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
           zi = z[i];
           pi_old = pold[i];
         }
-        const float pi = fmaf(beta, pi_old, zi);
+        const float pi = inf.mode == 1 ? wi : fmaf(beta, pi_old, zi);
         pnew[i] = pi;
         inf.q[i] = acc;
         dpart = df_prod(pi, acc);

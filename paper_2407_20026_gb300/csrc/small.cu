@@ -1,0 +1,318 @@
+// Double-float CG in one CTA per system (precision SSO_F32X2): the whole
+// preconditioned CG of K u = b (Eq. 1 under the supports of Eqs. 2-3) in a
+// single launch, for small systems whose solve time is otherwise launch and
+// host-synchronisation latency (the 600-DOF grid-shell: ~100 iterations).
+//
+// Arithmetic.  GB300 issues an FP64 instruction at about 1/64 of the FP32
+// rate, and one SM does all of a system's work here, so every vector and
+// every product is kept as an unevaluated sum hi + lo of two floats (about 48
+// significant bits) and computed on the FP32 pipes with error-free
+// transformations: K = K32 + Klo with Klo = K64 - K32 rounded to FP32 (exact
+// to ~2^-48 relative), row products accumulated as compensated dot products
+// (a running two-sum plus an FP32 error term, the "Dot2" scheme of Ogita,
+// Rump and Oishi, 2005, with the cross terms of the low parts added), vector
+// updates by double-float multiply and add.  The scalars alpha, beta and the
+// convergence test are formed in FP64 from the double-float block sums.  The
+// preconditioner (Jacobi or block-Jacobi, FP32 inverse blocks) is applied to
+// the double-float residual with double-float products.
+//
+// Layout of the work: warps own groups of 5 nodes, one lane per scalar row
+// (30 lanes, two idle), as in the batched CG kernels; every reduction is a
+// fixed-shape warp tree, then the warps' partials summed in warp order by
+// every warp alike, so each system's iterates are the same alone or in a
+// batch.  Vectors live in the system's scratch vectors as float2 (hi, lo);
+// the matrix is read through the read-only cache, so a small K stays in the
+// SM's L1.
+//
+// Convergence: when the recursive residual satisfies ||r|| <= rtol ||b||, the
+// residual b - K x is recomputed (double-float, from K64's two parts); above
+// rtol the CG restarts from it (a "sweep", at most max_sweeps), below it the
+// system is done.  Exits: converged (SSO_OK), p^T K p <= 0 or non-finite
+// (SSO_ERR_SINGULAR), max_iter or max_sweeps reached (SSO_ERR_NOT_CONVERGED).
+#include "sso_internal.cuh"
+
+namespace sso {
+namespace {
+
+constexpr int MAX_WARPS = 32;
+
+__device__ __forceinline__ DF df_split(double v) {
+  const float hi = __double2float_rn(v);
+  return {hi, __double2float_rn(v - (double)hi)};
+}
+// a * b for double-float a, b (the lo * lo term, below 2^-48 |a b|, dropped)
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float hi = __fadd_rn(p, e);
+  return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF ld_df(const float2* p) {
+  const float2 v = *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st_df(float2* p, DF v) { *p = make_float2(v.hi, v.lo); }
+
+// Compensated accumulation of products: s carries the running sum, c the
+// FP32 sum of every rounding error (two-product and two-sum) and cross term.
+struct Acc {
+  float s = 0.f, c = 0.f;
+};
+__device__ __forceinline__ void acc_prod(Acc& A, DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  const float t = __fadd_rn(A.s, p);
+  const float z = __fsub_rn(t, A.s);
+  const float se = __fadd_rn(__fsub_rn(A.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  A.s = t;
+  A.c = __fadd_rn(A.c, __fadd_rn(pe, se));
+}
+__device__ __forceinline__ DF acc_value(const Acc& A) {
+  const float hi = __fadd_rn(A.s, A.c);
+  return {hi, __fsub_rn(A.c, __fsub_rn(hi, A.s))};
+}
+
+// Sum over the CTA of each lane's (a, b) in a fixed order; every thread gets
+// both totals.  buf: 2 * MAX_WARPS DF of shared memory, not touched again
+// before the next __syncthreads of the caller's loop.
+__device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, double& sa, double& sb) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  a = df_warp_sum(a);
+  b = df_warp_sum(b);
+  if (lane == 0) {
+    buf[w] = a;
+    buf[MAX_WARPS + w] = b;
+  }
+  __syncthreads();
+  DF x = lane < nw ? buf[lane] : DF{0.f, 0.f};
+  DF y = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
+  x = df_warp_sum(x);
+  y = df_warp_sum(y);
+  sa = __shfl_sync(0xffffffffu, df_double(x), 0);
+  sb = __shfl_sync(0xffffffffu, df_double(y), 0);
+}
+
+struct Small {
+  const int* row_ptr;
+  const int* col;
+  const float* KH;
+  const float* KL;
+  const float* M;
+  bool block;
+  int n;
+};
+
+// (K v)[6 node + r] for a double-float vector v
+__device__ __forceinline__ DF row_product(const Small& G, const float2* v, int node, int r) {
+  Acc A;
+  const int j1 = __ldg(G.row_ptr + node + 1);
+  for (int j = __ldg(G.row_ptr + node); j < j1; ++j) {
+    const int c0 = 6 * __ldg(G.col + j);
+    const float* kh = G.KH + (size_t)j * 36 + 6 * r;
+    const float* kl = G.KL + (size_t)j * 36 + 6 * r;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc_prod(A, DF{__ldg(kh + c), __ldg(kl + c)}, ld_df(v + c0 + c));
+  }
+  return acc_value(A);
+}
+
+// z = M^-1 r for the lane's row; every lane of the warp calls it (shuffles).
+// rv: this lane's residual entry; node / r: its row (valid or not).
+__device__ __forceinline__ DF apply_precond(const Small& G, DF rv, int node, int r, bool ok) {
+  const int lane = threadIdx.x & 31;
+  const int base = lane - r;  // first lane of the node
+  Acc A;
+  if (G.block) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      DF rc;
+      rc.hi = __shfl_sync(0xffffffffu, rv.hi, (base + c) & 31);
+      rc.lo = __shfl_sync(0xffffffffu, rv.lo, (base + c) & 31);
+      const float m = ok ? __ldg(G.M + (size_t)node * M32_PACK + sym6(r, c)) : 0.f;
+      acc_prod(A, DF{m, 0.f}, rc);
+    }
+  } else {
+    const float m = ok ? __ldg(G.M + 6 * (size_t)node + r) : 0.f;
+    acc_prod(A, DF{m, 0.f}, rv);
+  }
+  return acc_value(A);
+}
+
+__global__ void __launch_bounds__(1024) split_k_kernel(const SysDesc* __restrict__ sys,
+                                                       const int* __restrict__ list) {
+  const SysDesc& S = sys[list[blockIdx.y]];
+  const long long n = (long long)S.row_ptr[S.n_nodes] * 36;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    S.klo[i] = __double2float_rn(S.K64[i] - (double)S.K32[i]);
+}
+
+__global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restrict__ sys,
+                                                        const int* __restrict__ list) {
+  // two sets of warp partials, used alternately by consecutive block sums
+  __shared__ DF red_a[2 * MAX_WARPS], red_b[2 * MAX_WARPS];
+  const SysDesc& S = sys[list[blockIdx.x]];
+  SysScalars* sc = S.sc;
+  const int n = S.n_nodes;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int groups = (n + NODES_PER_WARP - 1) / NODES_PER_WARP;
+  const Small G{S.row_ptr, S.col, S.K32, S.klo, S.M32, S.precond != SSO_JACOBI, n};
+  float2* X = reinterpret_cast<float2*>(S.dx);
+  float2* R = reinterpret_cast<float2*>(S.r);
+  float2* Z = reinterpret_cast<float2*>(S.z);
+  float2* P = reinterpret_cast<float2*>(S.p0);
+  float2* Q = reinterpret_cast<float2*>(S.q);
+  const bool warm = sc->state == ST_RESID;
+  const double rtol2 = sc->rtol2;
+  const int max_iter = sc->max_iter, max_sweeps = sc->max_sweeps;
+  const int r6 = lane % 6;
+  const DF zero{0.f, 0.f};
+  // rows of group g: node 5 g + lane / 6, row lane % 6 (lanes 30, 31 idle);
+  // the loop over groups is uniform over a warp
+#define SMALL_ROWS(BODY)                                                  \
+  for (int g = w; g < groups; g += nw) {                                  \
+    const int node = NODES_PER_WARP * g + lane / 6;                       \
+    const bool ok = lane < 6 * NODES_PER_WARP && node < n;               \
+    const int i = 6 * node + r6;                                          \
+    BODY                                                                  \
+  }
+
+  // x0 (warm start: the current solution) and ||b||^2
+  DF ff_p = zero;
+  SMALL_ROWS({
+    if (ok) {
+      const DF bi = df_split(S.b[i]);
+      st_df(X + i, warm ? df_split(S.x[i]) : zero);
+      ff_p = df_add(ff_p, df_mul(bi, bi));
+    }
+  })
+  double ff, dummy;
+  block_sum2(ff_p, zero, red_a, ff, dummy);
+  __syncthreads();  // X complete before K x
+
+  // Every decision below is taken from block sums that all threads hold
+  // alike, so the control flow (and every __syncthreads) is uniform.
+  int iters = 0, sweeps = 0, status = SSO_ERR_NOT_CONVERGED;
+  double rr64 = 0.0, rr64_prev = 0.0;
+  for (;;) {
+    // r = b - K x (double-float), z = M^-1 r, p = z
+    DF rr_p = zero, rz_p = zero;
+    SMALL_ROWS({
+      DF rv = zero;
+      if (ok) rv = df_add(df_split(S.b[i]), df_neg(row_product(G, X, node, r6)));
+      const DF zv = apply_precond(G, rv, node, r6, ok);
+      if (ok) {
+        st_df(R + i, rv);
+        st_df(Z + i, zv);
+        st_df(P + i, zv);
+        rr_p = df_add(rr_p, df_mul(rv, rv));
+        rz_p = df_add(rz_p, df_mul(rv, zv));
+      }
+    })
+    double rr, rz;
+    block_sum2(rr_p, rz_p, red_b, rr, rz);
+    rr64 = rr;
+    if (!isfinite(rr)) {
+      status = SSO_ERR_SINGULAR;
+      break;
+    }
+    if (rr <= rtol2 * ff) {
+      status = SSO_OK;
+      break;
+    }
+    // out of iterations or sweeps, or the last sweep lowered the residual
+    // less than 2x (rtol below what K and this arithmetic resolve)
+    if (iters >= max_iter || sweeps >= max_sweeps || (iters > 0 && !(rr < 0.25 * rr64_prev)))
+      break;
+    if (iters > 0) ++sweeps;
+    rr64_prev = rr;
+    __syncthreads();  // P complete before K p
+    while (iters < max_iter) {
+      // q = K p, p^T q
+      DF pq_p = zero;
+      SMALL_ROWS({
+        if (ok) {
+          const DF qv = row_product(G, P, node, r6);
+          st_df(Q + i, qv);
+          pq_p = df_add(pq_p, df_mul(ld_df(P + i), qv));
+        }
+      })
+      double pq;
+      block_sum2(pq_p, zero, red_a, pq, dummy);
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        status = SSO_ERR_SINGULAR;
+        break;
+      }
+      const DF alpha = df_split(rz / pq);
+      // x += alpha p, r -= alpha q, z = M^-1 r, r^T z, r^T r
+      DF rz_p2 = zero, rr_p2 = zero;
+      SMALL_ROWS({
+        DF rv = zero;
+        if (ok) {
+          const DF pv = ld_df(P + i);
+          st_df(X + i, df_add(ld_df(X + i), df_mul(alpha, pv)));
+          rv = df_add(ld_df(R + i), df_neg(df_mul(alpha, ld_df(Q + i))));
+          st_df(R + i, rv);
+        }
+        const DF zv = apply_precond(G, rv, node, r6, ok);
+        if (ok) {
+          st_df(Z + i, zv);
+          rz_p2 = df_add(rz_p2, df_mul(rv, zv));
+          rr_p2 = df_add(rr_p2, df_mul(rv, rv));
+        }
+      })
+      double rzn, rrn;
+      block_sum2(rz_p2, rr_p2, red_b, rzn, rrn);
+      ++iters;
+      if (!isfinite(rrn) || !isfinite(rzn)) {
+        status = SSO_ERR_SINGULAR;
+        break;
+      }
+      if (rrn <= rtol2 * ff) break;  // the recursive residual: check the true one
+      const DF beta = df_split(rzn / rz);
+      rz = rzn;
+      SMALL_ROWS({
+        if (ok) st_df(P + i, df_add(ld_df(Z + i), df_mul(beta, ld_df(P + i))));
+      })
+      __syncthreads();  // P complete before the next K p
+    }
+    if (status == SSO_ERR_SINGULAR) break;
+    __syncthreads();  // X complete before the residual pass
+  }
+#undef SMALL_ROWS
+  __syncthreads();
+  // the solution in FP64
+  for (int k = threadIdx.x; k < 6 * n; k += blockDim.x) {
+    const float2 v = X[k];
+    S.x[k] = (double)v.x + (double)v.y;
+  }
+  if (threadIdx.x == 0) {
+    sc->iters = iters;
+    sc->sweeps = sweeps;
+    sc->rr64 = rr64;
+    sc->ff = ff;
+    sc->status = status;
+    sc->state = ST_DONE;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int threads,
+                            cudaStream_t s) {
+  if (n_list <= 0) return cudaSuccess;
+  if (threads < 32 || threads > 1024 || threads % 32 || n_list > 65535)
+    return cudaErrorInvalidValue;
+  split_k_kernel<<<dim3(8, n_list), 1024, 0, s>>>(sys, list);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  small_cg_kernel<<<n_list, threads, 0, s>>>(sys, list);
+  return cudaGetLastError();
+}
+
+}  // namespace sso

@@ -99,6 +99,9 @@ struct SysDesc {
   int precond;      // sso_precond
   const int* row_ptr;
   const int* col;
+  // per block: the slot (in nodes) of its column in the staged halo of its
+  // row's tile (tiles with stage = 1; fixed by the mesh, built on the host)
+  const int* hslot;
   const float* K32;
   const double* K64;
   const float* M32;  // block-Jacobi: packed upper triangle, M32_PACK per node; Jacobi: 6 per node
@@ -134,8 +137,107 @@ struct SysDesc {
   float* y;               // [6 n_agg] A_c^-1 w
   double* cdot;           // [COARSE_ROW_BLOCKS] w^T y per row block of the coarse solve
   void* zb;               // [6 n_nodes] z_b (FP32)
+  // double-float CG (precision SSO_F32X2, small.cu): the low parts of K,
+  // K64 - K32 rounded to FP32, [n_blocks * 36] (the element-block scratch)
+  float* klo;
   SysScalars* sc;
 };
+
+#ifdef __CUDACC__
+// Double-float sums of FP32 products: an unevaluated sum hi + lo of two
+// floats, formed only with error-free transformations (the exact product
+// a b = p + fma(a, b, -p); Knuth's two-sum; a fast two-sum to renormalise),
+// so a dot product of FP32 vectors is accumulated to about 48 significant
+// bits on the FP32 pipes.  The FP32 CG kernels sum a warp's terms this way
+// and convert once to FP64, where every later sum (tiles, chunks) happens:
+// on this GPU an FP64 instruction costs a warp about 64 FP32 ones.
+// (Also the arithmetic of the one-CTA double-float CG, small.cu.)
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, e);
+  return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+// Fixed-shape tree over the warp; the sum is in lane 0.
+__device__ __forceinline__ DF df_warp_sum(DF x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF y;
+    y.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
+    y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
+    x = df_add(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ double df_double(DF x) { return (double)x.hi + (double)x.lo; }
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-copy (1-D TMA) helpers (CG kernels, assembly).  Every
+// wait is bounded.
+constexpr long long kWaitPolls = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Announces `bytes` more of asynchronous copies in the current phase without
+// arriving (the phase then also waits for a later arrival).
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitPolls; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+#endif
 
 // ---------------------------------------------------------------------------
 // Tiles per reduction chunk.  A chunk's kernel-A partials (CHUNK * WARPS)
@@ -258,6 +360,11 @@ constexpr int STAGE_SLAB_C = 1280;       // column indices (bytes)
 constexpr int STAGE_SLAB_V = 6144;       // one vector halo (bytes)
 constexpr int STAGE_SLAB_R = 256;        // row_ptr run (bytes)
 cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t s);
+
+// Launchers (small.cu): the whole double-float CG of each listed system in
+// one CTA (systems sys[list[0 .. n_list)]); threads a multiple of 32, <= 1024.
+cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int threads,
+                            cudaStream_t s);
 // The coarse correction of the two-level preconditioner, after kernel B:
 // restriction (one warp per (system, aggregate) of `aggs`), coarse solve and
 // scalar update (COARSE_ROW_BLOCKS work items per system of `csys`),

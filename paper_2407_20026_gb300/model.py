@@ -39,7 +39,8 @@ def _stream_ptr(stream):
 def options(**kw):
     """sso_options with the library defaults, overridden by keyword.
 
-    precision: "fp32_ir" | "fp64"; precond: "block_jacobi" | "jacobi" | "two_level" | "chain"; and the
+    precision: "fp32_ir" | "fp64" | "f32x2" (double-float, one CTA per system:
+    small systems); precond: "block_jacobi" | "jacobi" | "two_level" | "chain"; and the
     numeric fields of ``sso_options``.
     """
     lib = _lib.load()
@@ -47,7 +48,7 @@ def options(**kw):
     lib.sso_default_options(ctypes.byref(o))
     for k, v in kw.items():
         if k == "precision":
-            v = {"fp64": _lib.FP64, "fp32_ir": _lib.FP32_IR}.get(v, v)
+            v = {"fp64": _lib.FP64, "fp32_ir": _lib.FP32_IR, "f32x2": _lib.F32X2}.get(v, v)
         elif k == "precond":
             v = {"jacobi": _lib.JACOBI, "block_jacobi": _lib.BLOCK_JACOBI,
                  "two_level": _lib.TWO_LEVEL, "chain": _lib.CHAIN}.get(v, v)

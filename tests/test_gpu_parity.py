@@ -516,3 +516,83 @@ def test_autograd_with_fixed_thickness(sso, orc):
     u, C, V = BatchSSOFunction.apply(batch, zb, None, sso.options(precision="fp64", rtol=1e-11))
     C.sum().backward()
     assert rel(zb.grad[0].cpu().numpy(), ref["dz"]) <= TOL_FP64
+
+
+# ---------------------------------------------------------------------------
+# Double-float CG in one CTA per system (precision "f32x2", small systems)
+
+F32X2_MODELS = ["gridshell10", "gridshell13", "shell5", "mixed", "shell9_clamped", "hub"]
+
+
+@pytest.mark.parametrize("precond", ["block_jacobi", "jacobi"])
+@pytest.mark.parametrize("name", F32X2_MODELS)
+def test_f32x2_solve_and_gradient(sso, orc, name, precond):
+    """The one-CTA double-float CG reaches the FP64 tolerance against the
+    oracle (u, C, dz, dt), with supports held at exactly zero."""
+    m = MODELS[name]()
+    ref = orc.gradient(m, w=1.0)
+    mdl = sso.Model(m)
+    st = mdl.solve(precision="f32x2", precond=precond, rtol=1e-11)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-11, st
+    mdl.gradient(1.0)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= TOL_FP64
+    assert abs(r["C"] - ref["C"]) <= TOL_FP64 * abs(ref["C"])
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP64
+    if m["quad_conn"].shape[0]:
+        assert rel(r["dt"], ref["dt"]) <= TOL_FP64
+    assert np.all(r["u"][m["fixed"].ravel().astype(bool)] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["gridshell10", "mixed"])
+def test_f32x2_general_objective_adjoint(sso, orc, name):
+    """J = w C + g^T u with the adjoint solve (Eq. 5) in the double-float CG."""
+    m = MODELS[name]()
+    rng = np.random.default_rng(17)
+    g = rng.normal(size=6 * m["xyz"].shape[0]) * 1e3
+    ref = orc.gradient(m, w=0.5, g=g)
+    mdl = sso.Model(m)
+    assert mdl.solve(precision="f32x2", rtol=1e-11)["status"] == 0
+    assert mdl.gradient(0.5, g)["status"] == 0
+    r = mdl.result()
+    free = ~m["fixed"].ravel().astype(bool)
+    assert rel(r["lam"][free], ref["lam"][free]) <= TOL_FP64
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP64
+
+
+def test_f32x2_batch_equals_alone_bitwise(sso):
+    """One CTA per system with fixed-order sums: a system's result is the same
+    bit for bit alone and in a batch of systems of different sizes."""
+    ms = [MODELS[k]() for k in ("gridshell13", "shell5", "mixed", "gridshell10")]
+    alone = []
+    for m in ms:
+        mdl = sso.Model(m)
+        assert mdl.solve(precision="f32x2", rtol=1e-10)["status"] == 0
+        mdl.gradient(1.0)
+        alone.append(mdl.result())
+    models = [sso.Model(m) for m in ms]
+    batch = sso.Batch(models)
+    stats = batch.solve(precision="f32x2", rtol=1e-10)
+    assert all(s["status"] == 0 for s in stats)
+    batch.gradient()
+    for mdl, a in zip(models, alone):
+        r = mdl.result()
+        for k in ("u", "dz", "dt"):
+            assert np.array_equal(r[k], a[k]), k
+        assert r["C"] == a["C"]
+
+
+def test_f32x2_caps_and_options(sso):
+    """Iteration cap -> SSO_ERR_NOT_CONVERGED with the residual reported;
+    two-level / chain preconditioners and the server refuse f32x2."""
+    from paper_2407_20026_gb300 import _lib
+    from paper_2407_20026_gb300.serve import Server
+    mdl = sso.Model(MODELS["gridshell13"]())
+    st = mdl.solve(precision="f32x2", rtol=1e-12, max_iter=5, raise_on_error=False)
+    assert st["status"] == _lib.ERR_NOT_CONVERGED and st["iterations"] == 5
+    assert 0.0 < st["rel_residual"] < 1.0
+    for pc in ("two_level", "chain"):
+        with pytest.raises(sso.SSOError):
+            mdl.solve(precision="f32x2", precond=pc)
+    with pytest.raises(sso.SSOError):
+        Server(sso.options(precision="f32x2"))
