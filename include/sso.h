@@ -86,8 +86,9 @@ typedef struct {
  * dominated by launch and synchronisation latency: one SM works per system,
  * so a large system is slow.  Jacobi or block-Jacobi; batches and models
  * (not the server).  Convergence is tested on the residual b - K u recomputed
- * in double-float from both parts of K; max_sweeps caps the restarts from
- * it, and a restart that lowers the residual less than 2x ends the solve. */
+ * in FP64 from the FP64 K; the CG restarts from it while it is above rtol
+ * (max_sweeps caps the restarts, and a restart that lowers the residual less
+ * than 2x ends the solve). */
 typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1, SSO_F32X2 = 2 } sso_precision;
 /* SSO_TWO_LEVEL: block-Jacobi plus a coarse correction over the rigid-body
  * modes of node aggregates (z = M_b^-1 r + P A_c^-1 P^T r, A_c = P^T K P);

@@ -25,9 +25,9 @@
 // SM's L1.
 //
 // Convergence: when the recursive residual satisfies ||r|| <= rtol ||b||, the
-// residual b - K x is recomputed (double-float, from K64's two parts); above
-// rtol the CG restarts from it (a "sweep", at most max_sweeps), below it the
-// system is done.  Exits: converged (SSO_OK), p^T K p <= 0 or non-finite
+// residual b - K64 x is recomputed in FP64 (the refinement residual: FP64 only
+// there, a few microseconds per sweep on one SM); above rtol the CG restarts
+// from it (a "sweep", at most max_sweeps), below it the system is done.  Exits: converged (SSO_OK), p^T K p <= 0 or non-finite
 // (SSO_ERR_SINGULAR), max_iter or max_sweeps reached (SSO_ERR_NOT_CONVERGED).
 #include "sso_internal.cuh"
 
@@ -78,13 +78,16 @@ __device__ __forceinline__ DF acc_value(const Acc& A) {
 }
 
 // Sum over the CTA of each lane's (a, b) in a fixed order; every thread gets
-// both totals.  buf: 2 * MAX_WARPS DF of shared memory, not touched again
-// before the next __syncthreads of the caller's loop.
-__device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, double& sa, double& sb) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+// both totals.  Warps >= nw hold no rows: the tree over 32 warp slots sees
+// zeros there whatever the CTA's size, so a system's sums do not depend on
+// the launch's block size.  buf: 2 * MAX_WARPS DF of shared memory, not
+// touched again before the next __syncthreads of the caller's loop.
+__device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, double& sa,
+                                           double& sb) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   a = df_warp_sum(a);
   b = df_warp_sum(b);
-  if (lane == 0) {
+  if (lane == 0 && w < nw) {
     buf[w] = a;
     buf[MAX_WARPS + w] = b;
   }
@@ -143,6 +146,19 @@ __device__ __forceinline__ DF apply_precond(const Small& G, DF rv, int node, int
   return acc_value(A);
 }
 
+// (b - K64 x)[i] for row i = 6 node + r in FP64 (x the FP64 solution)
+__device__ __forceinline__ double residual64(const SysDesc& S, int node, int r, int i) {
+  double acc = S.b[i];
+  const int j1 = __ldg(S.row_ptr + node + 1);
+  for (int j = __ldg(S.row_ptr + node); j < j1; ++j) {
+    const int c0 = 6 * __ldg(S.col + j);
+    const double* k = S.K64 + (size_t)j * 36 + 6 * r;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc = fma(-__ldg(k + c), S.x[c0 + c], acc);
+  }
+  return acc;
+}
+
 __global__ void __launch_bounds__(1024) split_k_kernel(const SysDesc* __restrict__ sys,
                                                        const int* __restrict__ list) {
   const SysDesc& S = sys[list[blockIdx.y]];
@@ -159,8 +175,12 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   const SysDesc& S = sys[list[blockIdx.x]];
   SysScalars* sc = S.sc;
   const int n = S.n_nodes;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int groups = (n + NODES_PER_WARP - 1) / NODES_PER_WARP;
+  // warps that own rows: min(32, groups) whatever the launch's block size (a
+  // batch launches for its largest system), so the order of every sum is the
+  // system's own
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = min(min((int)(blockDim.x >> 5), MAX_WARPS), groups);
   const Small G{S.row_ptr, S.col, S.K32, S.klo, S.M32, S.precond != SSO_JACOBI, n};
   float2* X = reinterpret_cast<float2*>(S.dx);
   float2* R = reinterpret_cast<float2*>(S.r);
@@ -175,7 +195,7 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   // rows of group g: node 5 g + lane / 6, row lane % 6 (lanes 30, 31 idle);
   // the loop over groups is uniform over a warp
 #define SMALL_ROWS(BODY)                                                  \
-  for (int g = w; g < groups; g += nw) {                                  \
+  for (int g = w; w < nw && g < groups; g += nw) {                        \
     const int node = NODES_PER_WARP * g + lane / 6;                       \
     const bool ok = lane < 6 * NODES_PER_WARP && node < n;               \
     const int i = 6 * node + r6;                                          \
@@ -192,7 +212,7 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
     }
   })
   double ff, dummy;
-  block_sum2(ff_p, zero, red_a, ff, dummy);
+  block_sum2(ff_p, zero, red_a, nw, ff, dummy);
   __syncthreads();  // X complete before K x
 
   // Every decision below is taken from block sums that all threads hold
@@ -200,11 +220,17 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   int iters = 0, sweeps = 0, status = SSO_ERR_NOT_CONVERGED;
   double rr64 = 0.0, rr64_prev = 0.0;
   for (;;) {
-    // r = b - K x (double-float), z = M^-1 r, p = z
+    // the refinement residual r = b - K64 x in FP64 (x = hi + lo), then
+    // z = M^-1 r and p = z in double-float
+    for (int k = threadIdx.x; k < 6 * n; k += blockDim.x) {
+      const float2 v = X[k];
+      S.x[k] = (double)v.x + (double)v.y;
+    }
+    __syncthreads();
     DF rr_p = zero, rz_p = zero;
     SMALL_ROWS({
       DF rv = zero;
-      if (ok) rv = df_add(df_split(S.b[i]), df_neg(row_product(G, X, node, r6)));
+      if (ok) rv = df_split(residual64(S, node, r6, i));
       const DF zv = apply_precond(G, rv, node, r6, ok);
       if (ok) {
         st_df(R + i, rv);
@@ -215,7 +241,7 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
       }
     })
     double rr, rz;
-    block_sum2(rr_p, rz_p, red_b, rr, rz);
+    block_sum2(rr_p, rz_p, red_b, nw, rr, rz);
     rr64 = rr;
     if (!isfinite(rr)) {
       status = SSO_ERR_SINGULAR;
@@ -243,7 +269,7 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
         }
       })
       double pq;
-      block_sum2(pq_p, zero, red_a, pq, dummy);
+      block_sum2(pq_p, zero, red_a, nw, pq, dummy);
       if (!(pq > 0.0) || !isfinite(pq)) {
         status = SSO_ERR_SINGULAR;
         break;
@@ -267,7 +293,7 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
         }
       })
       double rzn, rrn;
-      block_sum2(rz_p2, rr_p2, red_b, rzn, rrn);
+      block_sum2(rz_p2, rr_p2, red_b, nw, rzn, rrn);
       ++iters;
       if (!isfinite(rrn) || !isfinite(rzn)) {
         status = SSO_ERR_SINGULAR;
