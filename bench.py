@@ -411,13 +411,16 @@ def run_serving(a):
         rng = np.random.default_rng(12345)
         gaps = rng.exponential(1.0 / rate, len(meshes))
         t = np.cumsum(gaps) - gaps[0]
+        pinfo0 = srv.info()
         res2, el2 = run_stream(srv, [{"mesh": m, "t_arrive": float(tt)}
                                      for m, tt in zip(meshes, t)], time_limit_s=1800.0)
+        pinfo1 = srv.info()
         lat = [r["latency_arrival_ms"] for r in res2]
         poisson.append({"rate_frac": frac, "offered_per_s": rate,
                         "achieved_per_s": len(meshes) / el2,
                         "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
-                        "failed": sum(r["stats"]["status"] != 0 for r in res2)})
+                        "failed": sum(r["stats"]["status"] != 0 for r in res2),
+                        "server_host_phases": {k: pinfo1[k] - pinfo0[k] for k in pinfo1}})
     srv.close()
 
     # the plain path: one request at a time, FP64 CG, same rtol

@@ -590,7 +590,9 @@ def test_f32x2_caps_and_options(sso):
     mdl = sso.Model(MODELS["gridshell13"]())
     st = mdl.solve(precision="f32x2", rtol=1e-12, max_iter=5, raise_on_error=False)
     assert st["status"] == _lib.ERR_NOT_CONVERGED and st["iterations"] == 5
-    assert 0.0 < st["rel_residual"] < 1.0
+    # CG lowers the energy norm of the error, not the residual norm: after 5
+    # iterations the residual is only required to be reported (finite, > 0)
+    assert np.isfinite(st["rel_residual"]) and st["rel_residual"] > 0.0
     for pc in ("two_level", "chain"):
         with pytest.raises(sso.SSOError):
             mdl.solve(precision="f32x2", precond=pc)
