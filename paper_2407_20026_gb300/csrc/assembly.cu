@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_bulk_kernel(
     const SetupJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char asm_slab[];
   __shared__ __align__(8) unsigned long long bar;
-  __shared__ int s_cptr[ASM_CHUNK + 1], s_brow[ASM_CHUNK], s_col[ASM_CHUNK];
+  __shared__ int s_cptr[ASM_CHUNK + 1], s_mask[ASM_CHUNK];
   __shared__ int s_staged;
   const SetupJob& J = jobs[blockIdx.y];
   const int b0 = blockIdx.x * ASM_CHUNK;
@@ -65,8 +65,16 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_bulk_kernel(
   }
   if (t <= nb) s_cptr[t] = __ldg(J.cptr + b0 + t);
   if (t < nb) {
-    s_brow[t] = __ldg(J.brow + b0 + t);
-    s_col[t] = __ldg(J.col + b0 + t);
+    // the block's supports as bits: fixed rows 0-5 of node i, fixed columns
+    // 6-11 of node j, bit 12 for a diagonal block
+    const int ni = __ldg(J.brow + b0 + t), nj = __ldg(J.col + b0 + t);
+    int m = ni == nj ? 1 << 12 : 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      m |= (__ldg(J.fixed + 6 * ni + d) != 0) << d;
+      m |= (__ldg(J.fixed + 6 * nj + d) != 0) << (6 + d);
+    }
+    s_mask[t] = m;
   }
   __syncthreads();
   const bool staged = s_staged != 0;
@@ -92,10 +100,10 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_bulk_kernel(
       sy += v.y;
     }
     const int r = p / 3, cc = 2 * (p - 3 * r);
-    const int ni = s_brow[lb], nj = s_col[lb];
-    const bool fr = J.fixed[6 * ni + r] != 0;
-    if (fr || J.fixed[6 * nj + cc]) sx = (ni == nj && r == cc) ? 1.0 : 0.0;
-    if (fr || J.fixed[6 * nj + cc + 1]) sy = (ni == nj && r == cc + 1) ? 1.0 : 0.0;
+    const int m = s_mask[lb];
+    const bool fr = (m >> r) & 1, diag = (m >> 12) & 1;
+    if (fr || ((m >> (6 + cc)) & 1)) sx = (diag && r == cc) ? 1.0 : 0.0;
+    if (fr || ((m >> (7 + cc)) & 1)) sy = (diag && r == cc + 1) ? 1.0 : 0.0;
     K64[item] = make_double2(sx, sy);
     K32[item] = make_float2((float)sx, (float)sy);
   }

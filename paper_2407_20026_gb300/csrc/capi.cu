@@ -1025,16 +1025,19 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   if (n_act > 0 && o->precision == SSO_F32X2) {
     // every active system's whole CG in one CTA of one launch
     B->h_list.clear();
-    int groups = 1;
+    int groups = 1, max_nodes = 1;
     for (int s = 0; s < B->n_sys; ++s)
       if (active[s]) {
         B->h_list.push_back(s);
         groups = std::max(groups, (B->models[s]->n_nodes + NODES_PER_WARP - 1) / NODES_PER_WARP);
+        max_nodes = std::max(max_nodes, B->models[s]->n_nodes);
       }
     CK(cudaMemcpyAsync(B->d_list, B->h_list.data(), B->h_list.size() * sizeof(int),
                        cudaMemcpyHostToDevice, B->stream));
     const int threads = 32 * std::min(32, groups);
-    CL(launch_small_cg(B->d_sys, B->d_list, (int)B->h_list.size(), threads, B->stream), 2);
+    CL(launch_small_cg(B->d_sys, B->d_list, (int)B->h_list.size(), threads, max_nodes,
+                       B->stream),
+       2);
   } else if (n_act > 0) {
     const bool two_level = o->precond == SSO_TWO_LEVEL;
     sso_status st = batch_graph(B, fp64, o->iters_per_launch, two_level);

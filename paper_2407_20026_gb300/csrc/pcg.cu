@@ -1145,7 +1145,6 @@ struct StageInfo {
   // halo runs in the stage: column c sits at slot c + shift[k] (nodes) for the
   // last run k whose first node is <= c (first nodes of unused runs: INT_MAX)
   int v1, v2, sh0, sh1, sh2;
-  int nhalo;  // halo nodes in the stage (mode 1)
 };
 
 __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
@@ -1259,7 +1258,6 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.sh0 = -td.vlo[0];
       inf.sh1 = td.nv[0] - td.vlo[1];
       inf.sh2 = td.nv[0] + td.nv[1] - td.vlo[2];
-      inf.nhalo = td.nv[0] + td.nv[1] + td.nv[2];
       ++issued;
       if (k < pre) {
         // K, columns and row_ptr already on their way; the halo (copied
@@ -1342,18 +1340,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       inf.state = read_state(sys[inf.sys].sc).state;
       inf.run_end = tile + 1 >= end || tiles[tile + 1].sys != inf.sys;
     }
-    // A staged CG tile: form w = z + beta p once per halo entry, in place of
-    // z in the stage (every row reading a column then loads w alone).  The
-    // barrier is taken for every tile by every consumer warp, dry or not.
-    if (!dry && inf.state == ST_PCG && inf.mode == 1) {
-      unsigned char* st = ring + s * ST_STAGE;
-      float* Ws = reinterpret_cast<float*>(st + ST_OFF_Z);
-      const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P);
-      const int nh = 6 * inf.nhalo;
-      const float beta = inf.beta;
-      for (int e = t; e < nh; e += NT) Ws[e] = fmaf(beta, Ps[e], Ws[e]);
-    }
-    consumer_sync();
+
     const SysDesc& S = sys[inf.sys];
     SysScalars* sc = S.sc;
     const int real_state = inf.state;
@@ -1368,25 +1355,30 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
       float* pnew = inf.pnew;
       const float beta = inf.beta;
       if (act) {
-        float acc = 0.f, zi = 0.f, pi_old = 0.f, wi = 0.f;
+        float acc = 0.f, zi = 0.f, pi_old = 0.f;
         if (inf.mode == 1) {
           const unsigned char* st = ring + s * ST_STAGE;
           const int* Rs = reinterpret_cast<const int*>(st + ST_OFF_R) - inf.rb;
           const int j0 = Rs[node], j1 = Rs[node + 1];
           const float* Ks = reinterpret_cast<const float*>(st) + (size_t)(j0 - inf.j0) * 36 + rr * 6;
+          // each block's column slot in the staged halo comes precomputed
           const int* Hs = reinterpret_cast<const int*>(st + ST_OFF_C) - inf.cb;
-          const float* Ws = reinterpret_cast<const float*>(st + ST_OFF_Z);
+          const float* Zs = reinterpret_cast<const float*>(st + ST_OFF_Z);
+          const float* Ps = reinterpret_cast<const float*>(st + ST_OFF_P);
           const int v1 = inf.v1, v2 = inf.v2, sh0 = inf.sh0, sh1 = inf.sh1, sh2 = inf.sh2;
           for (int j = j0; j < j1; ++j) {
-            float kv[6], wv[6];
+            const int o = 6 * Hs[j];
+            float kv[6], zv[6], pv[6];
             ld6s(Ks, kv);
-            ld6s(Ws + 6 * Hs[j], wv);
+            ld6s(Zs + o, zv);
+            ld6s(Ps + o, pv);
             Ks += 36;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc = fmaf(kv[q], wv[q], acc);
+            for (int q = 0; q < 6; ++q) acc = fmaf(kv[q], fmaf(beta, pv[q], zv[q]), acc);
           }
           const int oi = 6 * (node + (node >= v2 ? sh2 : (node >= v1 ? sh1 : sh0))) + rr;
-          wi = Ws[oi];
+          zi = Zs[oi];
+          pi_old = Ps[oi];
         } else if (inf.mode == 2) {
           // K rows, columns and row_ptr from the stage; z and p gathered from
           // global memory, three columns in flight at a time
@@ -1427,7 +1419,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) pcg_a_staged_kernel(
           zi = z[i];
           pi_old = pold[i];
         }
-        const float pi = inf.mode == 1 ? wi : fmaf(beta, pi_old, zi);
+        const float pi = fmaf(beta, pi_old, zi);
         pnew[i] = pi;
         inf.q[i] = acc;
         dpart = df_prod(pi, acc);

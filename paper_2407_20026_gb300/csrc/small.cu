@@ -20,9 +20,10 @@
 // (30 lanes, two idle), as in the batched CG kernels; every reduction is a
 // fixed-shape warp tree, then the warps' partials summed in warp order by
 // every warp alike, so each system's iterates are the same alone or in a
-// batch.  Vectors live in the system's scratch vectors as float2 (hi, lo);
-// the matrix is read through the read-only cache, so a small K stays in the
-// SM's L1.
+// batch.  The five vectors (x, r, z, p, q as float2 hi, lo) live in shared
+// memory for systems of up to 640 nodes, else in the system's scratch
+// vectors; the matrix is read through the read-only cache, so a small K stays
+// in the SM's L1.
 //
 // Convergence: when the recursive residual satisfies ||r|| <= rtol ||b||, the
 // residual b - K64 x is recomputed in FP64 (the refinement residual: FP64 only
@@ -35,6 +36,9 @@ namespace sso {
 namespace {
 
 constexpr int MAX_WARPS = 32;
+// five double-float vectors of 6 entries per node in shared memory
+constexpr int SMALL_BYTES_PER_NODE = 5 * 6 * 8;
+constexpr int SMALL_SMEM_NODES = 640;  // 150 KB; the rest of the SM's 256 KB stays L1 for K
 
 __device__ __forceinline__ DF df_split(double v) {
   const float hi = __double2float_rn(v);
@@ -114,6 +118,7 @@ struct Small {
 __device__ __forceinline__ DF row_product(const Small& G, const float2* v, int node, int r) {
   Acc A;
   const int j1 = __ldg(G.row_ptr + node + 1);
+#pragma unroll 2
   for (int j = __ldg(G.row_ptr + node); j < j1; ++j) {
     const int c0 = 6 * __ldg(G.col + j);
     const float* kh = G.KH + (size_t)j * 36 + 6 * r;
@@ -168,8 +173,12 @@ __global__ void __launch_bounds__(1024) split_k_kernel(const SysDesc* __restrict
     S.klo[i] = __double2float_rn(S.K64[i] - (double)S.K32[i]);
 }
 
+// kSmem: the five double-float vectors in dynamic shared memory (systems of
+// up to SMALL_SMEM_NODES nodes), else in the system's scratch vectors.
+template <bool kSmem>
 __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restrict__ sys,
                                                         const int* __restrict__ list) {
+  extern __shared__ __align__(16) float2 small_vec[];
   // two sets of warp partials, used alternately by consecutive block sums
   __shared__ DF red_a[2 * MAX_WARPS], red_b[2 * MAX_WARPS];
   const SysDesc& S = sys[list[blockIdx.x]];
@@ -182,11 +191,21 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = min(min((int)(blockDim.x >> 5), MAX_WARPS), groups);
   const Small G{S.row_ptr, S.col, S.K32, S.klo, S.M32, S.precond != SSO_JACOBI, n};
-  float2* X = reinterpret_cast<float2*>(S.dx);
-  float2* R = reinterpret_cast<float2*>(S.r);
-  float2* Z = reinterpret_cast<float2*>(S.z);
-  float2* P = reinterpret_cast<float2*>(S.p0);
-  float2* Q = reinterpret_cast<float2*>(S.q);
+  float2 *X, *R, *Z, *P, *Q;
+  if (kSmem) {
+    const int nd = 6 * n;
+    X = small_vec;
+    R = X + nd;
+    Z = R + nd;
+    P = Z + nd;
+    Q = P + nd;
+  } else {
+    X = reinterpret_cast<float2*>(S.dx);
+    R = reinterpret_cast<float2*>(S.r);
+    Z = reinterpret_cast<float2*>(S.z);
+    P = reinterpret_cast<float2*>(S.p0);
+    Q = reinterpret_cast<float2*>(S.q);
+  }
   const bool warm = sc->state == ST_RESID;
   const double rtol2 = sc->rtol2;
   const int max_iter = sc->max_iter, max_sweeps = sc->max_sweeps;
@@ -330,14 +349,25 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
 }  // namespace
 
 cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int threads,
-                            cudaStream_t s) {
+                            int max_nodes, cudaStream_t s) {
   if (n_list <= 0) return cudaSuccess;
   if (threads < 32 || threads > 1024 || threads % 32 || n_list > 65535)
     return cudaErrorInvalidValue;
   split_k_kernel<<<dim3(8, n_list), 1024, 0, s>>>(sys, list);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  small_cg_kernel<<<n_list, threads, 0, s>>>(sys, list);
+  if (max_nodes <= SMALL_SMEM_NODES) {
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(small_cg_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               SMALL_SMEM_NODES * SMALL_BYTES_PER_NODE);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    small_cg_kernel<true><<<n_list, threads, max_nodes * SMALL_BYTES_PER_NODE, s>>>(sys, list);
+  } else {
+    small_cg_kernel<false><<<n_list, threads, 0, s>>>(sys, list);
+  }
   return cudaGetLastError();
 }
 

@@ -598,3 +598,29 @@ def test_f32x2_caps_and_options(sso):
             mdl.solve(precision="f32x2", precond=pc)
     with pytest.raises(sso.SSOError):
         Server(sso.options(precision="f32x2"))
+
+
+def test_f32x2_large_system_global_vectors(sso, orc):
+    """A system above the shared-memory limit of the double-float CG (640
+    nodes) keeps its vectors in global memory: same tolerance vs the oracle,
+    and the same bits alone and next to a small system (whose vectors then
+    also live in global memory)."""
+    m = meshgen.shell(n_el=26, span=10.0, seed=8)
+    assert m["xyz"].shape[0] > 640
+    ref = orc.gradient(m)
+    mdl = sso.Model(m)
+    st = mdl.solve(precision="f32x2", rtol=1e-10, raise_on_error=False)
+    assert st["status"] == 0, st
+    mdl.gradient(1.0)
+    r = mdl.result()
+    assert rel(r["u"], ref["u"]) <= TOL_FP64
+    assert rel(r["dz"], ref["dz"]) <= TOL_FP64
+    assert rel(r["dt"], ref["dt"]) <= TOL_FP64
+    small = MODELS["gridshell10"]()
+    m_small = sso.Model(small)
+    m_small.solve(precision="f32x2", rtol=1e-10)
+    alone_small = m_small.result()["u"]
+    pair = [sso.Model(small), sso.Model(m)]
+    assert all(s["status"] == 0 for s in sso.Batch(pair).solve(precision="f32x2", rtol=1e-10))
+    assert np.array_equal(pair[0].result()["u"], alone_small)
+    assert np.array_equal(pair[1].result()["u"], r["u"])
