@@ -36,7 +36,7 @@ constexpr int ASM_THREADS = 256;
 // and its FP32 rounding K32.  Supports turn fixed rows / columns into identity
 // rows / columns.  The wait for the copy is bounded: a CTA that gives up sets
 // *err = 2 (reported as a CUDA failure) and writes nothing.
-__global__ void __launch_bounds__(ASM_THREADS) assemble_bulk_kernel(
+__global__ void __launch_bounds__(ASM_THREADS, 5) assemble_bulk_kernel(
     const SetupJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char asm_slab[];
   __shared__ __align__(8) unsigned long long bar;
@@ -242,6 +242,11 @@ cudaError_t launch_setup_assemble(const SetupJob* jobs, int n_jobs, int max_bloc
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(assemble_bulk_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, ASM_SLAB);
+    // all of the SM's shared memory for the slabs: five CTAs per SM
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(assemble_bulk_kernel,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr = true;
   }
