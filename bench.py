@@ -233,10 +233,10 @@ def slowest(seconds, world, dist=None, device=None):
 
 def assembly_bytes(mdl):
     """Algorithmic bytes of one model's assembly: its element blocks read once
-    (in assembly order), cptr, the block row and column of every block, the
-    support flags, and K64 + K32 written."""
-    nb, n = mdl.n_blocks, mdl.n_nodes
-    return mdl.n_elem_blocks * 288 + (nb + 1) * 4 + nb * 8 + 6 * n + nb * (288 + 144)
+    (in assembly order), cptr and the 2-byte support mask of every block, and
+    K64 + K32 written."""
+    nb = mdl.n_blocks
+    return mdl.n_elem_blocks * 288 + (nb + 1) * 4 + nb * 2 + nb * (288 + 144)
 
 
 def free_port():

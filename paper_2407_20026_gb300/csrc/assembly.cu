@@ -64,18 +64,7 @@ __global__ void __launch_bounds__(ASM_THREADS, 5) assemble_bulk_kernel(
     }
   }
   if (t <= nb) s_cptr[t] = __ldg(J.cptr + b0 + t);
-  if (t < nb) {
-    // the block's supports as bits: fixed rows 0-5 of node i, fixed columns
-    // 6-11 of node j, bit 12 for a diagonal block
-    const int ni = __ldg(J.brow + b0 + t), nj = __ldg(J.col + b0 + t);
-    int m = ni == nj ? 1 << 12 : 0;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      m |= (__ldg(J.fixed + 6 * ni + d) != 0) << d;
-      m |= (__ldg(J.fixed + 6 * nj + d) != 0) << (6 + d);
-    }
-    s_mask[t] = m;
-  }
+  if (t < nb) s_mask[t] = __ldg(J.bmask + b0 + t);
   __syncthreads();
   const bool staged = s_staged != 0;
   if (!mbar_wait(&bar, 0)) {
@@ -170,6 +159,7 @@ __device__ __forceinline__ void precond_node(int n, int kind, const int* __restr
   for (int k = 21; k < M32_PACK; ++k) M32[(size_t)n * M32_PACK + k] = 0.f;
 }
 
+// 32-thread CTAs: FP64-bound per node, spread over SMs for small models
 __global__ void __launch_bounds__(128) precond_setup_kernel(const SetupJob* __restrict__ jobs,
                                                             int kind) {
   const SetupJob& J = jobs[blockIdx.y];
@@ -259,7 +249,7 @@ cudaError_t launch_setup_precond(const SetupJob* jobs, int n_jobs, int max_nodes
                                  cudaStream_t s) {
   if (n_jobs <= 0 || max_nodes <= 0) return cudaSuccess;
   if (n_jobs > 65535) return cudaErrorInvalidValue;
-  precond_setup_kernel<<<dim3((max_nodes + 127) / 128, n_jobs), 128, 0, s>>>(jobs, kind);
+  precond_setup_kernel<<<dim3((max_nodes + 31) / 32, n_jobs), 32, 0, s>>>(jobs, kind);
   return cudaGetLastError();
 }
 

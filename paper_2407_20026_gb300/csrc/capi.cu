@@ -203,6 +203,7 @@ struct sso_model {
   int* d_err;
   // the set-up stages' view of this model (device copy, written at creation)
   SetupJob* d_job;
+  uint16_t* d_bmask;  // per block: supports of its row and column nodes
   bool assembled = false, solved = false;
   int assembled_precond = -1;
   sso_options last_opts;
@@ -597,6 +598,7 @@ size_t layout_model(sso_model* M, void* base) {
   M->d_brow = c.take<int>(M->n_blocks);
   M->d_diag = c.take<int>(n);
   M->d_cptr = c.take<int>((size_t)M->n_blocks + 1);
+  M->d_bmask = c.take<uint16_t>(M->n_blocks);
   M->d_epos = c.take<int>(M->n_eb);
   M->d_nptr = c.take<int>(n + 1);
   M->d_nsrc = c.take<int>(M->n_slots);
@@ -714,8 +716,7 @@ SetupJob make_setup_job(const sso_model* M) {
   J.kes = M->d_ke;
   J.fslot = M->d_fslot;
   J.cptr = M->d_cptr;
-  J.brow = M->d_brow;
-  J.col = M->d_col;
+  J.bmask = M->d_bmask;
   J.fixed = M->d_fixed;
   J.K64 = M->d_K64;
   J.K32 = M->d_K32;
@@ -1334,6 +1335,19 @@ sso_status prepare_model(ModelPrep& P) {
   put(M->d_brow, T.brow.data(), T.brow.size() * 4);
   put(M->d_diag, T.diag.data(), T.diag.size() * 4);
   put(M->d_cptr, T.cptr.data(), T.cptr.size() * 4);
+  {
+    std::vector<uint16_t> bm(T.col.size());
+    for (size_t b = 0; b < T.col.size(); ++b) {
+      const int ni = T.brow[b], nj = T.col[b];
+      int m = ni == nj ? 1 << 12 : 0;
+      for (int d = 0; d < 6; ++d) {
+        m |= (hm.fixed[6 * (size_t)ni + d] != 0) << d;
+        m |= (hm.fixed[6 * (size_t)nj + d] != 0) << (6 + d);
+      }
+      bm[b] = (uint16_t)m;
+    }
+    put(M->d_bmask, bm.data(), bm.size() * 2);
+  }
   put(M->d_epos, T.epos.data(), T.epos.size() * 4);
   put(M->d_nptr, T.nptr.data(), T.nptr.size() * 4);
   put(M->d_nsrc, T.nsrc.data(), T.nsrc.size() * 4);
@@ -2583,8 +2597,23 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
       ta = now;
     };
     {
+      // The request's host half is built by a worker thread after submission.
+      // Wait for it only while there is nothing else to do: with a graph in
+      // flight, until the graph completes (then harvest, and admit at the
+      // next step); with systems set up and waiting to join, not at all; with
+      // the GPU idle and nothing pending, as long as it takes.
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_done.wait(lk, [R] { return R->prep_done; });
+      if (launched) {
+        while (!R->prep_done && cudaEventQuery(B->ev) == cudaErrorNotReady)
+          S->cv_done.wait_for(lk, std::chrono::microseconds(50));
+      } else if (S->running.empty() && S->pending.empty()) {
+        S->cv_done.wait(lk, [R] { return R->prep_done; });
+      }
+      if (!R->prep_done) {
+        lk.unlock();
+        lap2(S->ms_admit_prep);
+        break;
+      }
     }
     lap2(S->ms_admit_prep);
     if (R->prep_status != SSO_OK) {  // invalid request: its result is the error

@@ -18,15 +18,23 @@
 //  * Area load q = pressure + gamma t along -Z, consistent nodal values
 //    f_a = -q sum_g N_a(g) detJ(g).
 //
-// Mapping: one thread per element.  The FP64 work per quad is ~10^4 flops,
-// run once per design evaluation; the solve (thousands of CG iterations)
-// dominates every workload, so these kernels favour clarity over throughput.
+// Mapping: one thread per element.  A quad costs about 6,000 FP64 operations,
+// once per design evaluation, and keeps GB300's FP64 pipe ~86 % busy; the
+// solve (thousands of CG iterations) dominates every workload.
 #include <math.h>
 
 #include "sso_internal.cuh"
 
 namespace sso {
 namespace {
+
+// Element kernels run one element per thread and are bound by the FP64 pipe
+// (about 2 FP64 operations per clock per SM on GB300), so they are launched as
+// 32-thread CTAs: a small model's few elements spread over many SMs instead
+// of sharing the FP64 pipe of one (the 261 beams of the 10 x 10 grid-shell:
+// 42 us in 128-thread CTAs).  A large batch keeps the same occupancy (the
+// quad kernels' registers allow 8 such CTAs per SM).
+constexpr int EL_THREADS = 32;
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual number with N tangents (adjoint kernels).
@@ -767,7 +775,7 @@ cudaError_t launch_quad_volume(int n_quads, const double* xyz, const int* conn,
                                const double* props, double* vslot, double* dt, double* vol,
                                cudaStream_t s) {
   if (n_quads <= 0) return cudaSuccess;
-  quad_volume_kernel<<<(n_quads + 127) / 128, 128, 0, s>>>(n_quads, xyz, conn, props, vslot,
+  quad_volume_kernel<<<(n_quads + EL_THREADS - 1) / EL_THREADS, EL_THREADS, 0, s>>>(n_quads, xyz, conn, props, vslot,
                                                             dt, vol);
   return cudaGetLastError();
 }
@@ -780,7 +788,7 @@ cudaError_t launch_ordered_sum(int n, const double* v, double* out, cudaStream_t
 cudaError_t launch_beam_stiffness(int n_beams, const double* xyz, const int* conn,
                                   const double* props, double* ke, cudaStream_t s) {
   if (n_beams <= 0) return cudaSuccess;
-  beam_stiffness_kernel<<<(n_beams + 127) / 128, 128, 0, s>>>(n_beams, xyz, conn, props, ke);
+  beam_stiffness_kernel<<<(n_beams + EL_THREADS - 1) / EL_THREADS, EL_THREADS, 0, s>>>(n_beams, xyz, conn, props, ke);
   return cudaGetLastError();
 }
 
@@ -792,14 +800,14 @@ cudaError_t launch_store_setup_job(SetupJob* dst, const SetupJob& job, cudaStrea
 cudaError_t launch_setup_beams(const SetupJob* jobs, int n_jobs, int max_beams, cudaStream_t s) {
   if (n_jobs <= 0 || max_beams <= 0) return cudaSuccess;
   if (n_jobs > 65535) return cudaErrorInvalidValue;
-  beam_setup_kernel<<<dim3((max_beams + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
+  beam_setup_kernel<<<dim3((max_beams + EL_THREADS - 1) / EL_THREADS, n_jobs), EL_THREADS, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_setup_quads(const SetupJob* jobs, int n_jobs, int max_quads, cudaStream_t s) {
   if (n_jobs <= 0 || max_quads <= 0) return cudaSuccess;
   if (n_jobs > 65535) return cudaErrorInvalidValue;
-  quad_setup_kernel<<<dim3((max_quads + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
+  quad_setup_kernel<<<dim3((max_quads + EL_THREADS - 1) / EL_THREADS, n_jobs), EL_THREADS, 0, s>>>(jobs);
   return cudaGetLastError();
 }
 
@@ -807,7 +815,7 @@ cudaError_t launch_quad_stiffness(int n_quads, const double* xyz, const int* con
                                   const double* props, double pressure, double gamma,
                                   double* ke, double* fslot, cudaStream_t s) {
   if (n_quads <= 0) return cudaSuccess;
-  quad_stiffness_kernel<<<(n_quads + 127) / 128, 128, 0, s>>>(n_quads, xyz, conn, props,
+  quad_stiffness_kernel<<<(n_quads + EL_THREADS - 1) / EL_THREADS, EL_THREADS, 0, s>>>(n_quads, xyz, conn, props,
                                                                pressure, gamma, ke, fslot);
   return cudaGetLastError();
 }
@@ -816,7 +824,7 @@ cudaError_t launch_beam_adjoint(int n_beams, const double* xyz, const int* conn,
                                 const double* props, const double* u, const double* lam,
                                 double lam_scale, double* gslot, cudaStream_t s) {
   if (n_beams <= 0) return cudaSuccess;
-  beam_adjoint_kernel<<<(n_beams + 127) / 128, 128, 0, s>>>(n_beams, xyz, conn, props, u, lam,
+  beam_adjoint_kernel<<<(n_beams + EL_THREADS - 1) / EL_THREADS, EL_THREADS, 0, s>>>(n_beams, xyz, conn, props, u, lam,
                                                              lam_scale, gslot);
   return cudaGetLastError();
 }
@@ -827,7 +835,7 @@ cudaError_t launch_quad_adjoint(int n_quads, const double* xyz, const int* conn,
                                 double w, double* gslot, double* dt, cudaStream_t s,
                                 const double* rho, double penal, double* drho) {
   if (n_quads <= 0) return cudaSuccess;
-  quad_adjoint_kernel<<<(n_quads + 127) / 128, 128, 0, s>>>(
+  quad_adjoint_kernel<<<(n_quads + EL_THREADS - 1) / EL_THREADS, EL_THREADS, 0, s>>>(
       n_quads, xyz, conn, props, pressure, gamma, u, lam, lam_scale, w, gslot, dt, rho, penal,
       drho);
   return cudaGetLastError();

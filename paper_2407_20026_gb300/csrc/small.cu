@@ -12,7 +12,9 @@
 // (a running two-sum plus an FP32 error term, the "Dot2" scheme of Ogita,
 // Rump and Oishi, 2005, with the cross terms of the low parts added), vector
 // updates by double-float multiply and add.  The scalars alpha, beta and the
-// convergence test are formed in FP64 from the double-float block sums.  The
+// convergence tests are double-float too (quotients refined once by their
+// remainder): every thread forms them, and an FP64 instruction per thread
+// would cost more than the matrix product of the iteration.  The
 // preconditioner (Jacobi or block-Jacobi, FP32 inverse blocks) is applied to
 // the double-float residual with double-float products.
 //
@@ -86,8 +88,7 @@ __device__ __forceinline__ DF acc_value(const Acc& A) {
 // zeros there whatever the CTA's size, so a system's sums do not depend on
 // the launch's block size.  buf: 2 * MAX_WARPS DF of shared memory, not
 // touched again before the next __syncthreads of the caller's loop.
-__device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, double& sa,
-                                           double& sb) {
+__device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, DF& sa, DF& sb) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   a = df_warp_sum(a);
   b = df_warp_sum(b);
@@ -100,9 +101,27 @@ __device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, double& 
   DF y = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
   x = df_warp_sum(x);
   y = df_warp_sum(y);
-  sa = __shfl_sync(0xffffffffu, df_double(x), 0);
-  sb = __shfl_sync(0xffffffffu, df_double(y), 0);
+  sa.hi = __shfl_sync(0xffffffffu, x.hi, 0);
+  sa.lo = __shfl_sync(0xffffffffu, x.lo, 0);
+  sb.hi = __shfl_sync(0xffffffffu, y.hi, 0);
+  sb.lo = __shfl_sync(0xffffffffu, y.lo, 0);
 }
+
+// a / b in double-float: an FP32 quotient, corrected once by the double-float
+// remainder a - q b (about 44 significant bits).  Every thread computes the
+// CG scalars this way, on the FP32 pipes.
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const DF r = df_add(a, df_neg(df_mul(DF{q1, 0.f}, b)));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  const float hi = __fadd_rn(q1, q2);
+  return {hi, __fsub_rn(q2, __fsub_rn(hi, q1))};
+}
+// a <= b for normalised double-float values
+__device__ __forceinline__ bool df_le(DF a, DF b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+__device__ __forceinline__ bool df_finite(DF a) { return isfinite(a.hi) && isfinite(a.lo); }
 
 struct Small {
   const int* row_ptr;
@@ -230,14 +249,18 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
       ff_p = df_add(ff_p, df_mul(bi, bi));
     }
   })
-  double ff, dummy;
+  DF ff, dummy;
   block_sum2(ff_p, zero, red_a, nw, ff, dummy);
+  // convergence threshold rtol^2 ||b||^2 (the only FP64 scalar arithmetic, once)
+  const DF thr = df_split(rtol2 * df_double(ff));
   __syncthreads();  // X complete before K x
 
   // Every decision below is taken from block sums that all threads hold
-  // alike, so the control flow (and every __syncthreads) is uniform.
+  // alike, so the control flow (and every __syncthreads) is uniform.  The
+  // scalars are double-float: an FP64 instruction per thread of the CTA
+  // would cost more than the iteration's matrix product.
   int iters = 0, sweeps = 0, status = SSO_ERR_NOT_CONVERGED;
-  double rr64 = 0.0, rr64_prev = 0.0;
+  DF rr64 = zero, rr64_prev = zero;
   for (;;) {
     // the refinement residual r = b - K64 x in FP64 (x = hi + lo), then
     // z = M^-1 r and p = z in double-float
@@ -259,20 +282,21 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
         rz_p = df_add(rz_p, df_mul(rv, zv));
       }
     })
-    double rr, rz;
+    DF rr, rz;
     block_sum2(rr_p, rz_p, red_b, nw, rr, rz);
     rr64 = rr;
-    if (!isfinite(rr)) {
+    if (!df_finite(rr)) {
       status = SSO_ERR_SINGULAR;
       break;
     }
-    if (rr <= rtol2 * ff) {
+    if (df_le(rr, thr)) {
       status = SSO_OK;
       break;
     }
     // out of iterations or sweeps, or the last sweep lowered the residual
     // less than 2x (rtol below what K and this arithmetic resolve)
-    if (iters >= max_iter || sweeps >= max_sweeps || (iters > 0 && !(rr < 0.25 * rr64_prev)))
+    if (iters >= max_iter || sweeps >= max_sweeps ||
+        (iters > 0 && df_le(DF{0.25f * rr64_prev.hi, 0.25f * rr64_prev.lo}, rr)))
       break;
     if (iters > 0) ++sweeps;
     rr64_prev = rr;
@@ -287,13 +311,13 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
           pq_p = df_add(pq_p, df_mul(ld_df(P + i), qv));
         }
       })
-      double pq;
+      DF pq;
       block_sum2(pq_p, zero, red_a, nw, pq, dummy);
-      if (!(pq > 0.0) || !isfinite(pq)) {
+      if (!(pq.hi > 0.f) || !df_finite(pq)) {
         status = SSO_ERR_SINGULAR;
         break;
       }
-      const DF alpha = df_split(rz / pq);
+      const DF alpha = df_div(rz, pq);
       // x += alpha p, r -= alpha q, z = M^-1 r, r^T z, r^T r
       DF rz_p2 = zero, rr_p2 = zero;
       SMALL_ROWS({
@@ -311,15 +335,15 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
           rr_p2 = df_add(rr_p2, df_mul(rv, rv));
         }
       })
-      double rzn, rrn;
+      DF rzn, rrn;
       block_sum2(rz_p2, rr_p2, red_b, nw, rzn, rrn);
       ++iters;
-      if (!isfinite(rrn) || !isfinite(rzn)) {
+      if (!df_finite(rrn) || !df_finite(rzn)) {
         status = SSO_ERR_SINGULAR;
         break;
       }
-      if (rrn <= rtol2 * ff) break;  // the recursive residual: check the true one
-      const DF beta = df_split(rzn / rz);
+      if (df_le(rrn, thr)) break;  // the recursive residual: check the true one
+      const DF beta = df_div(rzn, rz);
       rz = rzn;
       SMALL_ROWS({
         if (ok) st_df(P + i, df_add(ld_df(Z + i), df_mul(beta, ld_df(P + i))));
@@ -339,8 +363,8 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   if (threadIdx.x == 0) {
     sc->iters = iters;
     sc->sweeps = sweeps;
-    sc->rr64 = rr64;
-    sc->ff = ff;
+    sc->rr64 = df_double(rr64);
+    sc->ff = df_double(ff);
     sc->status = status;
     sc->state = ST_DONE;
   }

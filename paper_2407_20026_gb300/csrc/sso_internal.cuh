@@ -286,8 +286,9 @@ struct SetupJob {
   double* kes;            // element blocks in assembly order [n_eb][36]
   double* fslot;          // area-load share per (element, node) slot
   const int* cptr;        // [n_blocks + 1]
-  const int* brow;        // block row of every block
-  const int* col;         // block column of every block
+  // supports of every block: bits 0-5 fixed rows of its row node, 6-11 fixed
+  // columns of its column node, 12 a diagonal block (fixed by the mesh)
+  const uint16_t* bmask;
   const uint8_t* fixed;   // [6 n_nodes]
   double* K64;
   float* K32;
