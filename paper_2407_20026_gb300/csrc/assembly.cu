@@ -81,12 +81,19 @@ __global__ void __launch_bounds__(ASM_THREADS, 5) assemble_bulk_kernel(
     const int lb = item / PAIRS;
     const int p = item - lb * PAIRS;
     const int c0 = s_cptr[lb], c1 = s_cptr[lb + 1];
+    // the sum starts from the first contribution (no 0 + v: GB300's FP64 pipe
+    // issues about 2 operations per clock per SM, and is this kernel's limit)
     double sx = 0.0, sy = 0.0;
     for (int c = c0; c < c1; ++c) {
       const double2 v = staged ? slab[(size_t)(c - cbase) * PAIRS + p]
                                : __ldcs(gsrc + (size_t)c * PAIRS + p);
-      sx += v.x;
-      sy += v.y;
+      if (c == c0) {
+        sx = v.x;
+        sy = v.y;
+      } else {
+        sx += v.x;
+        sy += v.y;
+      }
     }
     const int r = p / 3, cc = 2 * (p - 3 * r);
     const int m = s_mask[lb];
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(ASM_THREADS, 5) assemble_bulk_kernel(
     if (fr || ((m >> (6 + cc)) & 1)) sx = (diag && r == cc) ? 1.0 : 0.0;
     if (fr || ((m >> (7 + cc)) & 1)) sy = (diag && r == cc + 1) ? 1.0 : 0.0;
     K64[item] = make_double2(sx, sy);
-    K32[item] = make_float2((float)sx, (float)sy);
+    K32[item] = make_float2(f64_to_f32_rn(sx), f64_to_f32_rn(sy));
   }
 }
 

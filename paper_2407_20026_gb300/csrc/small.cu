@@ -377,7 +377,7 @@ cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int
   if (n_list <= 0) return cudaSuccess;
   if (threads < 32 || threads > 1024 || threads % 32 || n_list > 65535)
     return cudaErrorInvalidValue;
-  split_k_kernel<<<dim3(8, n_list), 1024, 0, s>>>(sys, list);
+  split_k_kernel<<<dim3(64, n_list), 256, 0, s>>>(sys, list);  // FP64: spread over SMs
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (max_nodes <= SMALL_SMEM_NODES) {

@@ -180,6 +180,29 @@ __device__ __forceinline__ DF df_warp_sum(DF x) {
 }
 __device__ __forceinline__ double df_double(DF x) { return (double)x.hi + (double)x.lo; }
 
+// double -> float rounded to nearest even, with integer operations when the
+// result is a normal float (every stiffness entry here), else the hardware
+// conversion.  GB300 runs double -> float conversions on its FP64 pipe (about
+// 2 per clock per SM), which limited assembly; these are ~12 integer ops.
+// The 52-bit mantissa keeps its top 23 bits; the 29 dropped bits round up
+// above half and at half when the kept part is odd; a carry out of the
+// mantissa moves into the exponent (and to infinity past the largest float),
+// as rounding does.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int E = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;  // float biased exponent
+  if (E >= 1 && E <= 254) {
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    unsigned r = (hi & 0x80000000u) | ((unsigned)E << 23) | m;
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(r);
+  }
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi);  // signed zero
+  return __double2float_rn(x);
+}
+
 // ---------------------------------------------------------------------------
 // mbarrier and bulk-copy (1-D TMA) helpers (CG kernels, assembly).  Every
 // wait is bounded.
