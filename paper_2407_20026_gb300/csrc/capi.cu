@@ -80,6 +80,16 @@ bool debug_sync() {
 
 // True when p is device (or managed) memory.  A pointer CUDA does not know,
 // or a machine without a usable device, means host memory.
+// Host memory the GPU cannot reach directly (not pinned, not managed).
+bool is_pageable_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeUnregistered;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -204,6 +214,9 @@ struct sso_model {
   // the set-up stages' view of this model (device copy, written at creation)
   SetupJob* d_job;
   uint16_t* d_bmask;  // per block: supports of its row and column nodes
+  // pinned staging of results bound for pageable host memory (sso_model_get)
+  double* h_stage = nullptr;
+  size_t h_stage_n = 0;
   bool assembled = false, solved = false;
   int assembled_precond = -1;
   sso_options last_opts;
@@ -1519,6 +1532,7 @@ void sso_model_destroy(sso_model* M) {
   if (M->stream) cudaStreamSynchronize(M->stream);
   if (M->arena && M->own_arena) cudaFree(M->arena);
   if (M->d_chain_ws) cudaFree(M->d_chain_ws);
+  if (M->h_stage) cudaFreeHost(M->h_stage);
   if (M->ev_in) cudaEventDestroy(M->ev_in);
   if (M->ev_out) cudaEventDestroy(M->ev_out);
   if (M->stream) cudaStreamDestroy(M->stream);
@@ -1560,13 +1574,47 @@ sso_status sso_model_get(sso_model* M, double* u, double* C, double* dz, double*
   sso_status st = enter(M);
   if (st != SSO_OK) return st;
   const size_t ndof = 6 * (size_t)M->n_nodes;
-  if (u) CK(cudaMemcpyAsync(u, M->d_u, ndof * 8, cudaMemcpyDefault, M->stream));
-  if (C) CK(cudaMemcpyAsync(C, M->d_C, 8, cudaMemcpyDefault, M->stream));
-  if (dz) CK(cudaMemcpyAsync(dz, M->d_dz, M->n_nodes * 8, cudaMemcpyDefault, M->stream));
-  if (dt && M->n_quads > 0)
-    CK(cudaMemcpyAsync(dt, M->d_dt, M->n_quads * 8, cudaMemcpyDefault, M->stream));
-  if (lam) CK(cudaMemcpyAsync(lam, M->d_lam, ndof * 8, cudaMemcpyDefault, M->stream));
+  struct Out {
+    double* dst;
+    const double* src;
+    size_t n;
+  } outs[5] = {{u, M->d_u, ndof},
+               {C, M->d_C, 1},
+               {dz, M->d_dz, (size_t)M->n_nodes},
+               {dt, M->d_dt, M->n_quads > 0 ? (size_t)M->n_quads : 0},
+               {lam, M->d_lam, ndof}};
+  // Outputs in pageable host memory go through one pinned staging buffer, so
+  // their copies run together and the call waits once (a copy into pageable
+  // memory would each wait for the stream); device and pinned outputs are
+  // copied straight.
+  size_t staged = 0;
+  bool pageable[5] = {};
+  for (int k = 0; k < 5; ++k)
+    if (outs[k].dst && outs[k].n && is_pageable_host(outs[k].dst)) {
+      pageable[k] = true;
+      staged += outs[k].n;
+    }
+  if (staged > M->h_stage_n) {
+    if (M->h_stage) cudaFreeHost(M->h_stage);
+    M->h_stage = nullptr;
+    M->h_stage_n = 0;
+    CK(cudaMallocHost(&M->h_stage, staged * sizeof(double)));
+    M->h_stage_n = staged;
+  }
+  size_t off = 0;
+  for (int k = 0; k < 5; ++k) {
+    if (!outs[k].dst || !outs[k].n) continue;
+    double* to = pageable[k] ? M->h_stage + off : outs[k].dst;
+    CK(cudaMemcpyAsync(to, outs[k].src, outs[k].n * 8, cudaMemcpyDefault, M->stream));
+    if (pageable[k]) off += outs[k].n;
+  }
   CK(cudaStreamSynchronize(M->stream));
+  off = 0;
+  for (int k = 0; k < 5; ++k)
+    if (pageable[k]) {
+      std::memcpy(outs[k].dst, M->h_stage + off, outs[k].n * 8);
+      off += outs[k].n;
+    }
   return leave(M);
 }
 
@@ -2003,10 +2051,12 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
     if ((st = ensure_setup_events(B, e0 + 2)) != SSO_OK) return st;
     CK(cudaEventRecord(B->sev[e0], B->stream));
   }
-  if ((st = fork_aux(B)) != SSO_OK) return st;
+  // models' contractions on a pool of streams (one model: its own stream)
+  const bool pool = B->n_sys > 1;
+  if (pool && (st = fork_aux(B)) != SSO_OK) return st;
   for (int s = 0; s < B->n_sys; ++s) {
     sso_model* M = B->models[s];
-    cudaStream_t as = B->aux[s % B->aux.size()];
+    cudaStream_t as = pool ? B->aux[s % B->aux.size()] : B->stream;
     const double ws = w ? w[s] : 1.0;
     const bool has_g = active[s] != 0;
     const double* lam = has_g ? M->d_lam : M->d_u;
@@ -2032,7 +2082,7 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
       stats[s].ms = 0.0;
     }
   }
-  if ((st = join_aux(B)) != SSO_OK) return st;
+  if (pool && (st = join_aux(B)) != SSO_OK) return st;
   if (prof) CK(cudaEventRecord(B->sev[e0 + 1], B->stream));
   CK(cudaStreamSynchronize(B->stream));
   if (prof) {

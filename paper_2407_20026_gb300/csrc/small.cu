@@ -86,8 +86,8 @@ __device__ __forceinline__ DF acc_value(const Acc& A) {
 // Sum over the CTA of each lane's (a, b) in a fixed order; every thread gets
 // both totals.  Warps >= nw hold no rows: the tree over 32 warp slots sees
 // zeros there whatever the CTA's size, so a system's sums do not depend on
-// the launch's block size.  buf: 2 * MAX_WARPS DF of shared memory, not
-// touched again before the next __syncthreads of the caller's loop.
+// the launch's block size.  buf: 2 * MAX_WARPS + 2 DF of shared memory, not
+// written again before the next __syncthreads of the caller's loop.
 __device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, DF& sa, DF& sb) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   a = df_warp_sum(a);
@@ -97,14 +97,21 @@ __device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, DF& sa, 
     buf[MAX_WARPS + w] = b;
   }
   __syncthreads();
-  DF x = lane < nw ? buf[lane] : DF{0.f, 0.f};
-  DF y = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
-  x = df_warp_sum(x);
-  y = df_warp_sum(y);
-  sa.hi = __shfl_sync(0xffffffffu, x.hi, 0);
-  sa.lo = __shfl_sync(0xffffffffu, x.lo, 0);
-  sb.hi = __shfl_sync(0xffffffffu, y.hi, 0);
-  sb.lo = __shfl_sync(0xffffffffu, y.lo, 0);
+  // warp 0 sums the warps' partials (a fixed 32-slot tree) and leaves the
+  // totals in buf[2 MAX_WARPS ..]; everyone reads them after the barrier
+  if (w == 0) {
+    DF x = lane < nw ? buf[lane] : DF{0.f, 0.f};
+    DF y = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
+    x = df_warp_sum(x);
+    y = df_warp_sum(y);
+    if (lane == 0) {
+      buf[2 * MAX_WARPS] = x;
+      buf[2 * MAX_WARPS + 1] = y;
+    }
+  }
+  __syncthreads();
+  sa = buf[2 * MAX_WARPS];
+  sb = buf[2 * MAX_WARPS + 1];
 }
 
 // a / b in double-float: an FP32 quotient, corrected once by the double-float
@@ -140,10 +147,15 @@ __device__ __forceinline__ DF row_product(const Small& G, const float2* v, int n
 #pragma unroll 2
   for (int j = __ldg(G.row_ptr + node); j < j1; ++j) {
     const int c0 = 6 * __ldg(G.col + j);
-    const float* kh = G.KH + (size_t)j * 36 + 6 * r;
-    const float* kl = G.KL + (size_t)j * 36 + 6 * r;
+    // the row's 6 entries of both parts as 8-byte loads (24-byte rows)
+    const float2* kh = reinterpret_cast<const float2*>(G.KH + (size_t)j * 36 + 6 * r);
+    const float2* kl = reinterpret_cast<const float2*>(G.KL + (size_t)j * 36 + 6 * r);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) acc_prod(A, DF{__ldg(kh + c), __ldg(kl + c)}, ld_df(v + c0 + c));
+    for (int c = 0; c < 3; ++c) {
+      const float2 h = __ldg(kh + c), l = __ldg(kl + c);
+      acc_prod(A, DF{h.x, l.x}, ld_df(v + c0 + 2 * c));
+      acc_prod(A, DF{h.y, l.y}, ld_df(v + c0 + 2 * c + 1));
+    }
   }
   return acc_value(A);
 }
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
                                                         const int* __restrict__ list) {
   extern __shared__ __align__(16) float2 small_vec[];
   // two sets of warp partials, used alternately by consecutive block sums
-  __shared__ DF red_a[2 * MAX_WARPS], red_b[2 * MAX_WARPS];
+  __shared__ DF red_a[2 * MAX_WARPS + 2], red_b[2 * MAX_WARPS + 2];
   const SysDesc& S = sys[list[blockIdx.x]];
   SysScalars* sc = S.sc;
   const int n = S.n_nodes;
