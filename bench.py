@@ -983,9 +983,9 @@ def main():
     asm_bytes = sum(assembly_bytes(m) for m in models)
     asm_ms = setup["assembly"]
     asm_gbs = asm_bytes / (asm_ms / 1e3) / 1e9 if asm_ms > 0 else None
-    asm_traffic = kernel_traffic("assembly.cu", "assemble_sorted")
+    asm_traffic = kernel_traffic("assembly.cu", "assemble_bulk")
     roofline_assembly = {
-        "bound": "hbm", "kernel": "assemble_sorted (one launch, %d designs)" % B,
+        "bound": "hbm", "kernel": "assemble_bulk (one launch, %d designs)" % B,
         "achieved": asm_gbs, "peak": peak_gbs, "unit": "GB/s",
         "frac": asm_gbs / peak_gbs if asm_gbs else None, "peak_kind": peak_kind,
         "alg_bytes_per_launch": asm_bytes, "ms": asm_ms,
