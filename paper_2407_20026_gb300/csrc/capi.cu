@@ -128,11 +128,35 @@ struct Carver {
   }
 };
 
+// A vector whose resize leaves new elements uninitialised: the mesh arrays
+// are overwritten by the caller's data right after, and zero-filling them
+// first doubled the host time of queuing a large stream of requests.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) {}
+  template <class U>
+  void construct(U* p) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using RawVec = std::vector<T, NoInitAlloc<T>>;
+
 struct HostMesh {
   int n_nodes = 0, n_beams = 0, n_quads = 0;
-  std::vector<double> xyz, beam_props, quad_props, nodal_load;
-  std::vector<int> beam_conn, quad_conn;
-  std::vector<uint8_t> fixed;
+  RawVec<double> xyz, beam_props, quad_props, nodal_load;
+  RawVec<int> beam_conn, quad_conn;
+  RawVec<uint8_t> fixed;
   double pressure = 0.0, gamma = 0.0;
 };
 
