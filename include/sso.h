@@ -277,7 +277,11 @@ sso_status sso_model_get_load(sso_model* model, double* f);
  * all systems that are still iterating; each system keeps its own scalars,
  * refinement state and convergence test, and its reductions follow a fixed
  * tiling of its own rows, so its result does not depend on which other systems
- * share the batch.  The batch runs on the stream of models[0].
+ * share the batch.  The batch runs on the stream of models[0].  A batch of 32
+ * or more models runs its CG as two halves at once, on the streams of their
+ * first models and on two host threads (the first half on the calling
+ * thread); each half's kernel ramps and tails overlap the other's work.  The
+ * results are the same bits as without the split.
  */
 sso_status sso_batch_create(sso_model* const* models, int32_t n_models, sso_batch** out);
 void sso_batch_destroy(sso_batch* batch);

@@ -291,6 +291,14 @@ struct sso_batch {
   int* d_csys = nullptr;
   int* d_ccount = nullptr;
   int grid_restrict = 0, grid_csolve = 0;
+  // A large batch runs its CG as two halves on two streams at once, one host
+  // thread each: each half's kernel ramps and tails overlap the other half's
+  // work (measured +8 % designs/s at 128 shell designs).  parts[k] holds the
+  // systems [part0[k], part0[k + 1]); a part is a batch of its own (tile list,
+  // scalars, CUDA graphs) on its first model's stream.
+  std::vector<sso_batch*> parts;
+  std::vector<int> part0;
+  std::vector<cudaEvent_t> part_ev;
   // the models' set-up jobs (one launch per set-up stage for the whole batch)
   SetupJob* d_jobs = nullptr;
   // SSO_F32X2: the systems being solved (one CTA each)
@@ -1165,6 +1173,47 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   return first_bad;
 }
 
+// The CG of a batch's active systems: batch_run, or for a split batch its
+// parts at once, each on its own stream and host thread (in sequence while
+// profiling, so that every kernel's events time it alone).  The parts start
+// after the work already on the batch's stream, which then waits for them.
+sso_status run_cg(sso_batch* B, const sso_options* o, bool adjoint,
+                  const std::vector<char>& active, sso_stats* stats) {
+  if (B->parts.empty()) return batch_run(B, o, adjoint, active, stats);
+  const int np = (int)B->parts.size();
+  CK(cudaEventRecord(B->part_ev[0], B->stream));
+  for (int k = 1; k < np; ++k) CK(cudaStreamWaitEvent(B->parts[k]->stream, B->part_ev[0], 0));
+  std::vector<sso_status> res(np, SSO_OK);
+  std::vector<std::string> msg(np);
+  auto work = [&](int k) {
+    const std::vector<char> act(active.begin() + B->part0[k], active.begin() + B->part0[k + 1]);
+    res[k] = batch_run(B->parts[k], o, adjoint, act, stats ? stats + B->part0[k] : nullptr);
+    if (res[k] != SSO_OK) msg[k] = g_last_error;
+  };
+  std::vector<std::thread> threads;
+  if (!B->profiling) {
+    try {
+      for (int k = 1; k < np; ++k) threads.emplace_back(work, k);
+    } catch (const std::exception&) {
+      // no thread: the remaining parts run after the first, in this thread
+    }
+  }
+  work(0);
+  for (std::thread& t : threads) t.join();
+  for (int k = 1 + (int)threads.size(); k < np; ++k) work(k);
+  for (int k = 1; k < np; ++k) {
+    CK(cudaEventRecord(B->part_ev[k], B->parts[k]->stream));
+    CK(cudaStreamWaitEvent(B->stream, B->part_ev[k], 0));
+  }
+  int worst = -1;
+  for (int k = 0; k < np; ++k)
+    if (res[k] != SSO_OK && (worst < 0 || res[k] == SSO_ERR_CUDA || res[k] == SSO_ERR_OOM))
+      worst = k;
+  if (worst < 0) return SSO_OK;
+  g_last_error = msg[worst];
+  return res[worst];
+}
+
 // Tile k of model M (system s of a batch): its block range, the aligned runs
 // of column indices and row_ptr entries, and the node range (halo) of the
 // vector entries its rows read; stage = 1 when all of it fits the FP32
@@ -1761,7 +1810,13 @@ sso_status sso_model_get_load(sso_model* M, double* f) {
   return leave(M);
 }
 
-sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out) {
+}  // extern "C"
+
+namespace {
+// Batches of at least this many systems run their CG as two concurrent parts.
+constexpr int kSplitMin = 32;
+
+sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bool split) {
   if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!models || n <= 0) return fail(SSO_ERR_INVALID, "need at least one model");
@@ -1902,12 +1957,42 @@ sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out
     sso_batch_destroy(B);
     return cuda_fail(e, "batch set-up");
   }
+  if (split && n >= kSplitMin) {
+    const int half = n / 2;
+    B->part0 = {0, half, n};
+    for (int k = 0; k < 2; ++k) {
+      sso_batch* P = nullptr;
+      sso_status st = create_batch(models + B->part0[k], B->part0[k + 1] - B->part0[k], &P, false);
+      if (st != SSO_OK) {
+        sso_batch_destroy(B);
+        return st;
+      }
+      B->parts.push_back(P);
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        sso_batch_destroy(B);
+        return cuda_fail(e, "batch part event");
+      }
+      B->part_ev.push_back(ev);
+    }
+  }
   *out = B;
   return SSO_OK;
 }
+}  // namespace
+
+extern "C" {
+
+sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out) {
+  return create_batch(models, n, out, true);
+}
+
 
 void sso_batch_destroy(sso_batch* B) {
   if (!B) return;
+  for (sso_batch* P : B->parts) sso_batch_destroy(P);
+  for (cudaEvent_t e : B->part_ev) cudaEventDestroy(e);
   if (B->stream) cudaStreamSynchronize(B->stream);
   for (int k = 0; k < 3; ++k)
     if (B->exec[k]) cudaGraphExecDestroy(B->exec[k]);
@@ -1928,6 +2013,7 @@ void sso_batch_destroy(sso_batch* B) {
 
 sso_status sso_batch_set_profiling(sso_batch* B, int32_t enable) {
   if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  for (sso_batch* P : B->parts) sso_batch_set_profiling(P, enable);
   B->profiling = enable ? 1 : 0;
   B->prof_ms_a = B->prof_ms_b = 0.0;
   B->prof_launches = 0;
@@ -1953,9 +2039,16 @@ sso_status sso_batch_setup_times(const sso_batch* B, double* ms_elements, double
 sso_status sso_batch_kernel_times(const sso_batch* B, double* ms_a, double* ms_b,
                                   int64_t* launches) {
   if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
-  if (ms_a) *ms_a = B->prof_ms_a;
-  if (ms_b) *ms_b = B->prof_ms_b;
-  if (launches) *launches = B->prof_launches;
+  double a = B->prof_ms_a, b = B->prof_ms_b;
+  long long n = B->prof_launches;
+  for (const sso_batch* P : B->parts) {
+    a += P->prof_ms_a;
+    b += P->prof_ms_b;
+    n += P->prof_launches;
+  }
+  if (ms_a) *ms_a = a;
+  if (ms_b) *ms_b = b;
+  if (launches) *launches = n;
   return SSO_OK;
 }
 
@@ -1990,7 +2083,7 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
   if (prof) CK(cudaEventRecord(B->sev[4], B->stream));
   for (int s = 0; s < B->n_sys; ++s) mark_assembled(B->models[s], opts->precond);
   std::vector<char> active(B->n_sys, 1);
-  sso_status run = batch_run(B, opts, false, active, stats);
+  sso_status run = run_cg(B, opts, false, active, stats);
   if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
   // compliance C = f^T u, and the preconditioner check
   CL(launch_dot(B->n_sys, B->d_sys, B->d_dots, B->stream), 1);
@@ -2066,7 +2159,7 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
   if (any) {
     // the adjoint solve reuses K, the preconditioner and the last options
     sso_options o = B->models[0]->last_opts;
-    run = batch_run(B, &o, true, active, stats);
+    run = run_cg(B, &o, true, active, stats);
     if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
   }
   const bool prof = B->profiling != 0;

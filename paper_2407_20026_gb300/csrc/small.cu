@@ -30,8 +30,9 @@
 // Convergence: when the recursive residual satisfies ||r|| <= rtol ||b||, the
 // residual b - K64 x is recomputed in FP64 (the refinement residual: FP64 only
 // there, a few microseconds per sweep on one SM); above rtol the CG restarts
-// from it (a "sweep", at most max_sweeps), below it the system is done.  Exits: converged (SSO_OK), p^T K p <= 0 or non-finite
-// (SSO_ERR_SINGULAR), max_iter or max_sweeps reached (SSO_ERR_NOT_CONVERGED).
+// from it (a "sweep", at most max_sweeps), below it the system is done.
+// Exits: converged (SSO_OK), p^T K p <= 0 or non-finite (SSO_ERR_SINGULAR),
+// max_iter or max_sweeps reached (SSO_ERR_NOT_CONVERGED).
 #include "sso_internal.cuh"
 
 namespace sso {
@@ -141,8 +142,11 @@ struct Small {
 };
 
 // (K v)[6 node + r] for a double-float vector v
+// Two accumulators, one for the even and one for the odd columns of every
+// block: two independent dependency chains per lane (the sum order is fixed
+// by the row alone).
 __device__ __forceinline__ DF row_product(const Small& G, const float2* v, int node, int r) {
-  Acc A;
+  Acc A0, A1;
   const int j1 = __ldg(G.row_ptr + node + 1);
 #pragma unroll 2
   for (int j = __ldg(G.row_ptr + node); j < j1; ++j) {
@@ -153,11 +157,11 @@ __device__ __forceinline__ DF row_product(const Small& G, const float2* v, int n
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float2 h = __ldg(kh + c), l = __ldg(kl + c);
-      acc_prod(A, DF{h.x, l.x}, ld_df(v + c0 + 2 * c));
-      acc_prod(A, DF{h.y, l.y}, ld_df(v + c0 + 2 * c + 1));
+      acc_prod(A0, DF{h.x, l.x}, ld_df(v + c0 + 2 * c));
+      acc_prod(A1, DF{h.y, l.y}, ld_df(v + c0 + 2 * c + 1));
     }
   }
-  return acc_value(A);
+  return df_add(acc_value(A0), acc_value(A1));
 }
 
 // z = M^-1 r for the lane's row; every lane of the warp calls it (shuffles).

@@ -624,3 +624,36 @@ def test_f32x2_large_system_global_vectors(sso, orc):
     assert all(s["status"] == 0 for s in sso.Batch(pair).solve(precision="f32x2", rtol=1e-10))
     assert np.array_equal(pair[0].result()["u"], alone_small)
     assert np.array_equal(pair[1].result()["u"], r["u"])
+
+
+@pytest.mark.parametrize("precision,precond", [("fp32_ir", "block_jacobi"), ("fp32_ir", "two_level"),
+                                               ("fp64", "jacobi"), ("f32x2", "block_jacobi")])
+def test_split_batch_equals_alone_bitwise(sso, precision, precond):
+    """A batch of 32 or more systems runs its CG as two concurrent parts (two
+    streams, two host threads); every system's result is still the same bits
+    as solving it alone, for the solve and for a general-objective adjoint."""
+    ms = []
+    for k in range(34):
+        if k % 2:
+            ms.append(meshgen.gridshell(n_side=4 + k % 5, seed=k))
+        else:
+            ms.append(meshgen.shell(n_el=3 + k % 4, span=6.0, seed=k))
+    opts = sso.options(precision=precision, precond=precond, rtol=1e-9)
+    rng = np.random.default_rng(5)
+    gs = [rng.normal(size=6 * m["xyz"].shape[0]) for m in ms]
+    alone = []
+    for m, g in zip(ms, gs):
+        mdl = sso.Model(m)
+        assert mdl.solve(opts)["status"] == 0
+        mdl.gradient(0.5, g)
+        alone.append(mdl.result())
+    models = [sso.Model(m) for m in ms]
+    batch = sso.Batch(models)
+    stats = batch.solve(opts)
+    assert all(s["status"] == 0 for s in stats)
+    assert all(s["status"] == 0 for s in batch.gradient([0.5] * len(ms), gs))
+    for mdl, a in zip(models, alone):
+        r = mdl.result()
+        for key in ("u", "dz", "dt", "lam"):
+            assert np.array_equal(r[key], a[key]), key
+        assert r["C"] == a["C"]
