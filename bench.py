@@ -973,6 +973,8 @@ def main():
     bytes_pcg = nblk * (36 * wsz + 4) + (n_nodes + 1) * 4 + 4 * (6 * n_nodes * wsz)
     bytes_resid = nblk * (36 * 8 + 4) + (n_nodes + 1) * 4 + 3 * (6 * n_nodes * 8)
     alg_bytes = p_iters * bytes_pcg + p_sweeps * bytes_resid
+    step_bytes = (iters_total * (bytes_pcg + 264 * n_nodes) + sweeps_total * bytes_resid)
+    step_gbs = step_bytes / (total_ms / 1000.0) / 1e9  # this GPU
     achieved = alg_bytes / (ms_a / 1000.0) / 1e9 if ms_a > 0 else None
     a_launches = timed_pairs
     traffic = kernel_traffic("pcg.cu", "pcg_a_%s" % ("f32" if fp32 else "f64"))
@@ -1112,6 +1114,16 @@ def main():
                 "alg_bytes_per_cg_launch": B * bytes_pcg,
                 "launches_timed": a_launches, "kernel_ms_total": ms_a,
                 "kernel_b_ms_total": ms_b,
+                "kernel_times_from": "profiled step: events around every CG launch, the "
+                                     "batch run whole (the timed steps run it as two "
+                                     "concurrent halves)" if B >= 32 else "profiled step",
+                # the timed steps as a whole: the algorithmic bytes of both CG
+                # kernels over the steps' elapsed time (everything else counted
+                # as time), against the same peak
+                "step_hbm": {
+                    "achieved": step_gbs, "frac": step_gbs / peak_gbs,
+                    "bytes": step_bytes, "note": "kernel A (SpMV, FP64 residual passes) and "
+                                                 "kernel B (264 B per node) per CG iteration"},
             },
             # elapsed per phase of the profiled step; each set-up stage is
             # one launch for the whole batch

@@ -1174,12 +1174,13 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
 }
 
 // The CG of a batch's active systems: batch_run, or for a split batch its
-// parts at once, each on its own stream and host thread (in sequence while
-// profiling, so that every kernel's events time it alone).  The parts start
-// after the work already on the batch's stream, which then waits for them.
+// parts at once, each on its own stream and host thread.  While profiling, the
+// batch runs whole (one graph over every system), so that the events around
+// each kernel time it alone at the batch's full size.  The parts start after
+// the work already on the batch's stream, which then waits for them.
 sso_status run_cg(sso_batch* B, const sso_options* o, bool adjoint,
                   const std::vector<char>& active, sso_stats* stats) {
-  if (B->parts.empty()) return batch_run(B, o, adjoint, active, stats);
+  if (B->parts.empty() || B->profiling) return batch_run(B, o, adjoint, active, stats);
   const int np = (int)B->parts.size();
   CK(cudaEventRecord(B->part_ev[0], B->stream));
   for (int k = 1; k < np; ++k) CK(cudaStreamWaitEvent(B->parts[k]->stream, B->part_ev[0], 0));
@@ -1191,12 +1192,10 @@ sso_status run_cg(sso_batch* B, const sso_options* o, bool adjoint,
     if (res[k] != SSO_OK) msg[k] = g_last_error;
   };
   std::vector<std::thread> threads;
-  if (!B->profiling) {
-    try {
-      for (int k = 1; k < np; ++k) threads.emplace_back(work, k);
-    } catch (const std::exception&) {
-      // no thread: the remaining parts run after the first, in this thread
-    }
+  try {
+    for (int k = 1; k < np; ++k) threads.emplace_back(work, k);
+  } catch (const std::exception&) {
+    // no thread: the remaining parts run after the first, in this thread
   }
   work(0);
   for (std::thread& t : threads) t.join();
