@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batch", type=int, default=128, help="designs per step")
+    p.add_argument("--batch", type=int, default=256, help="designs per step")
     p.add_argument("--n-el", type=int, default=64)
     p.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
     p.add_argument("--precond", default="block_jacobi",

@@ -18,12 +18,18 @@
 // preconditioner (Jacobi or block-Jacobi, FP32 inverse blocks) is applied to
 // the double-float residual with double-float products.
 //
+// Recurrences: the Chronopoulos-Gear form of preconditioned CG (1989), which
+// carries s = K p by s = w + beta s with w = K u, u = M^-1 r, so that one
+// matrix product and ONE reduction point (r^T u, w^T u and r^T r together)
+// make an iteration; in one CTA a reduction costs two barriers and a warp
+// tree per warp, as much as a third of the iteration.
+//
 // Layout of the work: warps own groups of 5 nodes, one lane per scalar row
 // (30 lanes, two idle), as in the batched CG kernels; every reduction is a
-// fixed-shape warp tree, then the warps' partials summed in warp order by
-// every warp alike, so each system's iterates are the same alone or in a
-// batch.  The five vectors (x, r, z, p, q as float2 hi, lo) live in shared
-// memory for systems of up to 640 nodes, else in the system's scratch
+// fixed-shape warp tree, then the partials of the warps that own rows summed
+// in warp order by warp 0, so each system's iterates are the same alone or in
+// a batch.  The six vectors (x, r, u, w, p, s as float2 hi, lo) live in shared
+// memory for systems of up to 512 nodes, else in the system's scratch
 // vectors; the matrix is read through the read-only cache, so a small K stays
 // in the SM's L1.
 //
@@ -39,9 +45,12 @@ namespace sso {
 namespace {
 
 constexpr int MAX_WARPS = 32;
-// five double-float vectors of 6 entries per node in shared memory
-constexpr int SMALL_BYTES_PER_NODE = 5 * 6 * 8;
-constexpr int SMALL_SMEM_NODES = 640;  // 150 KB; the rest of the SM's 256 KB stays L1 for K
+// a CTA of at most 20 warps (640 threads: 100 nodes at a time), which leaves
+// each thread ~100 registers; larger systems loop over their node groups
+constexpr int SMALL_MAX_THREADS = 640;
+// six double-float vectors of 6 entries per node in shared memory
+constexpr int SMALL_BYTES_PER_NODE = 6 * 6 * 8;
+constexpr int SMALL_SMEM_NODES = 512;  // 144 KB; the rest of the SM's 256 KB stays L1 for K
 
 __device__ __forceinline__ DF df_split(double v) {
   const float hi = __double2float_rn(v);
@@ -113,6 +122,38 @@ __device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, DF& sa, 
   __syncthreads();
   sa = buf[2 * MAX_WARPS];
   sb = buf[2 * MAX_WARPS + 1];
+}
+
+// The same for three values (one reduction point per CG iteration).
+__device__ __forceinline__ void block_sum3(DF a, DF b, DF c, DF* buf, int nw, DF& sa, DF& sb,
+                                           DF& sc) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  a = df_warp_sum(a);
+  b = df_warp_sum(b);
+  c = df_warp_sum(c);
+  if (lane == 0 && w < nw) {
+    buf[w] = a;
+    buf[MAX_WARPS + w] = b;
+    buf[2 * MAX_WARPS + w] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    DF x = lane < nw ? buf[lane] : DF{0.f, 0.f};
+    DF y = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
+    DF z = lane < nw ? buf[2 * MAX_WARPS + lane] : DF{0.f, 0.f};
+    x = df_warp_sum(x);
+    y = df_warp_sum(y);
+    z = df_warp_sum(z);
+    if (lane == 0) {
+      buf[3 * MAX_WARPS] = x;
+      buf[3 * MAX_WARPS + 1] = y;
+      buf[3 * MAX_WARPS + 2] = z;
+    }
+  }
+  __syncthreads();
+  sa = buf[3 * MAX_WARPS];
+  sb = buf[3 * MAX_WARPS + 1];
+  sc = buf[3 * MAX_WARPS + 2];
 }
 
 // a / b in double-float: an FP32 quotient, corrected once by the double-float
@@ -208,14 +249,13 @@ __global__ void __launch_bounds__(1024) split_k_kernel(const SysDesc* __restrict
     S.klo[i] = __double2float_rn(S.K64[i] - (double)S.K32[i]);
 }
 
-// kSmem: the five double-float vectors in dynamic shared memory (systems of
+// kSmem: the six double-float vectors in dynamic shared memory (systems of
 // up to SMALL_SMEM_NODES nodes), else in the system's scratch vectors.
 template <bool kSmem>
-__global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restrict__ sys,
+__global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDesc* __restrict__ sys,
                                                         const int* __restrict__ list) {
   extern __shared__ __align__(16) float2 small_vec[];
-  // two sets of warp partials, used alternately by consecutive block sums
-  __shared__ DF red_a[2 * MAX_WARPS + 2], red_b[2 * MAX_WARPS + 2];
+  __shared__ DF red[3 * MAX_WARPS + 3];  // warp partials and totals of the block sums
   const SysDesc& S = sys[list[blockIdx.x]];
   SysScalars* sc = S.sc;
   const int n = S.n_nodes;
@@ -226,20 +266,23 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = min(min((int)(blockDim.x >> 5), MAX_WARPS), groups);
   const Small G{S.row_ptr, S.col, S.K32, S.klo, S.M32, S.precond != SSO_JACOBI, n};
-  float2 *X, *R, *Z, *P, *Q;
+  // x, r, u = M^-1 r, w = K u, p, s = K p (double-float)
+  float2 *X, *R, *U, *W, *P, *Sv;
   if (kSmem) {
     const int nd = 6 * n;
     X = small_vec;
     R = X + nd;
-    Z = R + nd;
-    P = Z + nd;
-    Q = P + nd;
+    U = R + nd;
+    W = U + nd;
+    P = W + nd;
+    Sv = P + nd;
   } else {
     X = reinterpret_cast<float2*>(S.dx);
     R = reinterpret_cast<float2*>(S.r);
-    Z = reinterpret_cast<float2*>(S.z);
+    U = reinterpret_cast<float2*>(S.z);
+    W = reinterpret_cast<float2*>(S.q);
     P = reinterpret_cast<float2*>(S.p0);
-    Q = reinterpret_cast<float2*>(S.q);
+    Sv = reinterpret_cast<float2*>(S.p1);
   }
   const bool warm = sc->state == ST_RESID;
   const double rtol2 = sc->rtol2;
@@ -265,11 +308,10 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
       ff_p = df_add(ff_p, df_mul(bi, bi));
     }
   })
-  DF ff, dummy;
-  block_sum2(ff_p, zero, red_a, nw, ff, dummy);
+  DF ff, dummy, dummy2;
+  block_sum3(ff_p, zero, zero, red, nw, ff, dummy, dummy2);
   // convergence threshold rtol^2 ||b||^2 (the only FP64 scalar arithmetic, once)
   const DF thr = df_split(rtol2 * df_double(ff));
-  __syncthreads();  // X complete before K x
 
   // Every decision below is taken from block sums that all threads hold
   // alike, so the control flow (and every __syncthreads) is uniform.  The
@@ -279,29 +321,39 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
   DF rr64 = zero, rr64_prev = zero;
   for (;;) {
     // the refinement residual r = b - K64 x in FP64 (x = hi + lo), then
-    // z = M^-1 r and p = z in double-float
+    // u = M^-1 r, w = K u and p = s = 0 in double-float
     for (int k = threadIdx.x; k < 6 * n; k += blockDim.x) {
       const float2 v = X[k];
       S.x[k] = (double)v.x + (double)v.y;
     }
     __syncthreads();
-    DF rr_p = zero, rz_p = zero;
+    DF rr_p = zero, ga_p = zero;
     SMALL_ROWS({
       DF rv = zero;
       if (ok) rv = df_split(residual64(S, node, r6, i));
-      const DF zv = apply_precond(G, rv, node, r6, ok);
+      const DF uv = apply_precond(G, rv, node, r6, ok);
       if (ok) {
         st_df(R + i, rv);
-        st_df(Z + i, zv);
-        st_df(P + i, zv);
+        st_df(U + i, uv);
+        st_df(P + i, zero);
+        st_df(Sv + i, zero);
         rr_p = df_add(rr_p, df_mul(rv, rv));
-        rz_p = df_add(rz_p, df_mul(rv, zv));
+        ga_p = df_add(ga_p, df_mul(rv, uv));
       }
     })
-    DF rr, rz;
-    block_sum2(rr_p, rz_p, red_b, nw, rr, rz);
+    __syncthreads();  // U complete before K u
+    DF de_p = zero;
+    SMALL_ROWS({
+      if (ok) {
+        const DF wv = row_product(G, U, node, r6);
+        st_df(W + i, wv);
+        de_p = df_add(de_p, df_mul(wv, ld_df(U + i)));
+      }
+    })
+    DF gamma, delta, rr;
+    block_sum3(ga_p, de_p, rr_p, red, nw, gamma, delta, rr);
     rr64 = rr;
-    if (!df_finite(rr)) {
+    if (!df_finite(rr) || !df_finite(delta)) {
       status = SSO_ERR_SINGULAR;
       break;
     }
@@ -316,55 +368,62 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
       break;
     if (iters > 0) ++sweeps;
     rr64_prev = rr;
-    __syncthreads();  // P complete before K p
+    if (!(delta.hi > 0.f)) {
+      status = SSO_ERR_SINGULAR;
+      break;
+    }
+    // Chronopoulos-Gear recurrences: one reduction point per iteration
+    // (gamma = r^T u, delta = w^T u and r^T r together), s = K p carried by
+    // s = w + beta s instead of a second product
+    DF alpha = df_div(gamma, delta), beta = zero;
     while (iters < max_iter) {
-      // q = K p, p^T q
-      DF pq_p = zero;
-      SMALL_ROWS({
-        if (ok) {
-          const DF qv = row_product(G, P, node, r6);
-          st_df(Q + i, qv);
-          pq_p = df_add(pq_p, df_mul(ld_df(P + i), qv));
-        }
-      })
-      DF pq;
-      block_sum2(pq_p, zero, red_a, nw, pq, dummy);
-      if (!(pq.hi > 0.f) || !df_finite(pq)) {
-        status = SSO_ERR_SINGULAR;
-        break;
-      }
-      const DF alpha = df_div(rz, pq);
-      // x += alpha p, r -= alpha q, z = M^-1 r, r^T z, r^T r
-      DF rz_p2 = zero, rr_p2 = zero;
+      // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r
+      DF ga_n = zero, rr_n = zero;
       SMALL_ROWS({
         DF rv = zero;
         if (ok) {
-          const DF pv = ld_df(P + i);
+          const DF pv = df_add(ld_df(U + i), df_mul(beta, ld_df(P + i)));
+          const DF sv = df_add(ld_df(W + i), df_mul(beta, ld_df(Sv + i)));
+          st_df(P + i, pv);
+          st_df(Sv + i, sv);
           st_df(X + i, df_add(ld_df(X + i), df_mul(alpha, pv)));
-          rv = df_add(ld_df(R + i), df_neg(df_mul(alpha, ld_df(Q + i))));
+          rv = df_add(ld_df(R + i), df_neg(df_mul(alpha, sv)));
           st_df(R + i, rv);
         }
-        const DF zv = apply_precond(G, rv, node, r6, ok);
+        const DF uv = apply_precond(G, rv, node, r6, ok);
         if (ok) {
-          st_df(Z + i, zv);
-          rz_p2 = df_add(rz_p2, df_mul(rv, zv));
-          rr_p2 = df_add(rr_p2, df_mul(rv, rv));
+          st_df(U + i, uv);
+          ga_n = df_add(ga_n, df_mul(rv, uv));
+          rr_n = df_add(rr_n, df_mul(rv, rv));
         }
       })
-      DF rzn, rrn;
-      block_sum2(rz_p2, rr_p2, red_b, nw, rzn, rrn);
+      __syncthreads();  // U complete before K u
+      DF de_n = zero;
+      SMALL_ROWS({
+        if (ok) {
+          const DF wv = row_product(G, U, node, r6);
+          st_df(W + i, wv);
+          de_n = df_add(de_n, df_mul(wv, ld_df(U + i)));
+        }
+      })
+      DF gn, dn, rrn;
+      block_sum3(ga_n, de_n, rr_n, red, nw, gn, dn, rrn);
       ++iters;
-      if (!df_finite(rrn) || !df_finite(rzn)) {
+      if (!df_finite(rrn) || !df_finite(gn) || !df_finite(dn)) {
         status = SSO_ERR_SINGULAR;
         break;
       }
       if (df_le(rrn, thr)) break;  // the recursive residual: check the true one
-      const DF beta = df_div(rzn, rz);
-      rz = rzn;
-      SMALL_ROWS({
-        if (ok) st_df(P + i, df_add(ld_df(Z + i), df_mul(beta, ld_df(P + i))));
-      })
-      __syncthreads();  // P complete before the next K p
+      // beta = gamma_n / gamma, alpha = gamma_n / (delta_n - beta gamma_n / alpha)
+      const DF bn = df_div(gn, gamma);
+      const DF den = df_add(dn, df_neg(df_div(df_mul(bn, gn), alpha)));
+      if (!(den.hi > 0.f)) {  // p^T K p <= 0: K is not positive definite
+        status = SSO_ERR_SINGULAR;
+        break;
+      }
+      alpha = df_div(gn, den);
+      beta = bn;
+      gamma = gn;
     }
     if (status == SSO_ERR_SINGULAR) break;
     __syncthreads();  // X complete before the residual pass
@@ -391,8 +450,8 @@ __global__ void __launch_bounds__(1024) small_cg_kernel(const SysDesc* __restric
 cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int threads,
                             int max_nodes, cudaStream_t s) {
   if (n_list <= 0) return cudaSuccess;
-  if (threads < 32 || threads > 1024 || threads % 32 || n_list > 65535)
-    return cudaErrorInvalidValue;
+  if (threads < 32 || threads % 32 || n_list > 65535) return cudaErrorInvalidValue;
+  threads = threads < SMALL_MAX_THREADS ? threads : SMALL_MAX_THREADS;
   split_k_kernel<<<dim3(64, n_list), 256, 0, s>>>(sys, list);  // FP64: spread over SMs
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

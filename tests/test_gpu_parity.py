@@ -601,12 +601,12 @@ def test_f32x2_caps_and_options(sso):
 
 
 def test_f32x2_large_system_global_vectors(sso, orc):
-    """A system above the shared-memory limit of the double-float CG (640
+    """A system above the shared-memory limit of the double-float CG (512
     nodes) keeps its vectors in global memory: same tolerance vs the oracle,
     and the same bits alone and next to a small system (whose vectors then
     also live in global memory)."""
     m = meshgen.shell(n_el=26, span=10.0, seed=8)
-    assert m["xyz"].shape[0] > 640
+    assert m["xyz"].shape[0] > 512
     ref = orc.gradient(m)
     mdl = sso.Model(m)
     st = mdl.solve(precision="f32x2", rtol=1e-10, raise_on_error=False)
