@@ -284,6 +284,12 @@ sso_status sso_model_get_load(sso_model* model, double* f);
  * results are the same bits as without the split.
  */
 sso_status sso_batch_create(sso_model* const* models, int32_t n_models, sso_batch** out);
+
+/* Runs the batch's CG as `parts` concurrent parts of contiguous models (1 =
+ * one part; at most 16 and at most one model per part), replacing the default
+ * split.  Each part has its own stream (its first model's), CUDA graphs and
+ * host thread; the results do not change.  Waits for the batch's work. */
+sso_status sso_batch_set_parts(sso_batch* batch, int32_t parts);
 void sso_batch_destroy(sso_batch* batch);
 /* Solve every model; stats is NULL or [n_models].  Returns the first
  * non-OK per-system status (if any) after all systems finished. */

@@ -97,6 +97,7 @@ SIGNATURES = {
     "sso_batch_gradient": ([_vp, ctypes.POINTER(_f64), ctypes.POINTER(_vp),
                             ctypes.POINTER(Stats)], _i32),
     "sso_batch_set_profiling": ([_vp, _i32], _i32),
+    "sso_batch_set_parts": ([_vp, _i32], _i32),
     "sso_server_create": ([ctypes.POINTER(Options), ctypes.c_size_t, _i32, _i32,
                            ctypes.POINTER(_vp)], _i32),
     "sso_server_destroy": ([_vp], None),

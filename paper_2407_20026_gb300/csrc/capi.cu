@@ -1814,6 +1814,7 @@ sso_status sso_model_get_load(sso_model* M, double* f) {
 namespace {
 // Batches of at least this many systems run their CG as two concurrent parts.
 constexpr int kSplitMin = 32;
+sso_status make_parts(sso_batch* B, int k);
 
 sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bool split) {
   if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
@@ -1957,26 +1958,37 @@ sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bo
     return cuda_fail(e, "batch set-up");
   }
   if (split && n >= kSplitMin) {
-    const int half = n / 2;
-    B->part0 = {0, half, n};
-    for (int k = 0; k < 2; ++k) {
-      sso_batch* P = nullptr;
-      sso_status st = create_batch(models + B->part0[k], B->part0[k + 1] - B->part0[k], &P, false);
-      if (st != SSO_OK) {
-        sso_batch_destroy(B);
-        return st;
-      }
-      B->parts.push_back(P);
-      cudaEvent_t ev;
-      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      if (e != cudaSuccess) {
-        sso_batch_destroy(B);
-        return cuda_fail(e, "batch part event");
-      }
-      B->part_ev.push_back(ev);
+    sso_status st = make_parts(B, 2);
+    if (st != SSO_OK) {
+      sso_batch_destroy(B);
+      return st;
     }
   }
   *out = B;
+  return SSO_OK;
+}
+
+// Splits B's CG into k concurrent parts of contiguous systems (k <= 1: none).
+sso_status make_parts(sso_batch* B, int k) {
+  for (sso_batch* P : B->parts) sso_batch_destroy(P);
+  for (cudaEvent_t e : B->part_ev) cudaEventDestroy(e);
+  B->parts.clear();
+  B->part_ev.clear();
+  B->part0.clear();
+  if (k <= 1) return SSO_OK;
+  for (int i = 0; i <= k; ++i) B->part0.push_back((int)((long long)B->n_sys * i / k));
+  for (int i = 0; i < k; ++i) {
+    sso_batch* P = nullptr;
+    sso_status st = create_batch(B->models.data() + B->part0[i], B->part0[i + 1] - B->part0[i],
+                                 &P, false);
+    if (st != SSO_OK) return st;
+    B->parts.push_back(P);
+    P->profiling = B->profiling;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "batch part event");
+    B->part_ev.push_back(ev);
+  }
   return SSO_OK;
 }
 }  // namespace
@@ -1985,6 +1997,15 @@ extern "C" {
 
 sso_status sso_batch_create(sso_model* const* models, int32_t n, sso_batch** out) {
   return create_batch(models, n, out, true);
+}
+
+sso_status sso_batch_set_parts(sso_batch* B, int32_t parts) {
+  if (!B) return fail(SSO_ERR_INVALID, "batch is NULL");
+  if (parts < 1 || parts > 16 || parts > B->n_sys)
+    return fail(SSO_ERR_INVALID, "parts must be in [1, min(16, models)]");
+  CK(cudaStreamSynchronize(B->stream));
+  for (sso_batch* P : B->parts) CK(cudaStreamSynchronize(P->stream));
+  return make_parts(B, parts);
 }
 
 

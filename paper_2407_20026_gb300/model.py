@@ -239,6 +239,10 @@ class Batch:
             _lib.check(code)
         return [s.as_dict() for s in st]
 
+    def set_parts(self, parts):
+        """Run the CG as `parts` concurrent parts (1: none; default 2 from 32 models)."""
+        _lib.check(_lib.load().sso_batch_set_parts(self._h, int(parts)))
+
     def set_profiling(self, enable=True):
         _lib.check(_lib.load().sso_batch_set_profiling(self._h, 1 if enable else 0))
 

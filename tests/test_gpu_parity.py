@@ -657,3 +657,25 @@ def test_split_batch_equals_alone_bitwise(sso, precision, precond):
         for key in ("u", "dz", "dt", "lam"):
             assert np.array_equal(r[key], a[key]), key
         assert r["C"] == a["C"]
+
+
+def test_batch_parts_do_not_change_results(sso):
+    """The same batch solved as 1, 2 (default) and 3 concurrent parts gives
+    the same bits."""
+    ms = [meshgen.shell(n_el=3 + k % 5, span=6.0, seed=100 + k) for k in range(33)]
+    batch = sso.Batch([sso.Model(m) for m in ms])
+    opts = sso.options(precision="fp32_ir", rtol=1e-9)
+    ref = None
+    for parts in (2, 1, 3):
+        batch.set_parts(parts)
+        assert all(s["status"] == 0 for s in batch.solve(opts))
+        batch.gradient()
+        res = [mdl.result() for mdl in batch.models]
+        if ref is None:
+            ref = res
+            continue
+        for r, a in zip(res, ref):
+            for key in ("u", "dz", "dt"):
+                assert np.array_equal(r[key], a[key]), (parts, key)
+    with pytest.raises(sso.SSOError):
+        batch.set_parts(0)
