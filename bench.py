@@ -980,6 +980,15 @@ def main():
     traffic = kernel_traffic("pcg.cu", "pcg_a_%s" % ("f32" if fp32 else "f64"))
     traffic_bytes = traffic["dram_bytes_per_design_launch"] * B if traffic else None
 
+    # kernel B over the same profiled step: 264 B per node per CG iteration
+    # (packed M^-1 96, p and q 24 each, r and dx read and written 48 each, z 24)
+    b_bytes = p_iters * 264 * n_nodes
+    b_gbs = b_bytes / (ms_b / 1000.0) / 1e9 if ms_b > 0 else None
+    roofline_b = {"bound": "hbm", "kernel": "pcg_b32 (update, z = M^-1 r, dots)",
+                  "achieved": b_gbs, "peak": peak_gbs, "unit": "GB/s",
+                  "frac": b_gbs / peak_gbs if b_gbs else None, "peak_kind": peak_kind,
+                  "alg_bytes": b_bytes, "kernel_ms_total": ms_b} if fp32 else None
+
     # assembly: one launch for the whole batch, timed with events on the
     # library's stream in the profiled step
     asm_bytes = sum(assembly_bytes(m) for m in models)
@@ -1134,7 +1143,7 @@ def main():
                                       "element_matrices": setup["elements"],
                                       "assembly": setup["assembly"],
                                       "preconditioner_and_loads": setup["precond"]}},
-            "roofline_assembly": roofline_assembly,
+            "roofline_b": roofline_b, "roofline_assembly": roofline_assembly,
             "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "two_level": two_level,
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
         }
