@@ -70,6 +70,8 @@ def parse():
                    help="serving: Poisson arrival rates as fractions of saturated throughput")
     p.add_argument("--hbm-budget-gb", type=float, default=64.0)
     p.add_argument("--max-systems", type=int, default=512)
+    p.add_argument("--lanes", type=int, default=1,
+                   help="serving: lanes of the server (stepped at once on their own threads)")
     p.add_argument("--alone-sample", type=int, default=16,
                    help="serving: requests timed one at a time on the FP64 path")
     p.add_argument("--repeats", type=int, default=1000, help="gridshell: timed evaluations")
@@ -375,7 +377,8 @@ def run_serving(a):
     dofs = [6 * m["xyz"].shape[0] for m in meshes]
     opts = sso.options(precision=a.precision, precond=a.precond, rtol=a.rtol,
                        inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch)
-    srv = Server(opts, hbm_budget=int(a.hbm_budget_gb * (1 << 30)), max_systems=a.max_systems)
+    srv = Server(opts, hbm_budget=int(a.hbm_budget_gb * (1 << 30)), max_systems=a.max_systems,
+                 lanes=a.lanes)
     warm = [{"mesh": meshgen.gridshell(n_side=8 + 4 * k, seed=10 ** 6 + k), "t_arrive": 0.0}
             for k in range(max(a.warmup, 1))]
     run_stream(srv, warm)
@@ -457,6 +460,7 @@ def run_serving(a):
                                   "fp32_ir" else "FP64", a.precond, a.rtol),
                    "mean_dof": float(np.mean(dofs)), "max_dof": int(max(dofs)),
                    "hbm_budget_gb": a.hbm_budget_gb, "max_systems": a.max_systems,
+                   "lanes": a.lanes,
                    "iters_per_launch": a.iters_per_launch,
                    "l2": "working set of the resident requests (GBs) > L2"},
         "saturated": {"evals_per_s": sat, "seconds": elapsed,

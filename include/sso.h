@@ -346,6 +346,18 @@ typedef struct sso_server sso_server;
 
 sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
                              int32_t max_systems, int32_t max_tiles, sso_server** out);
+
+/* A server of `lanes` (1..8) independent lanes: each lane is a server with
+ * 1/lanes of the budget, slots and tiles; each request goes to the lane with
+ * the fewest nodes still to finish, and sso_server_step steps every lane at
+ * once (the first on the calling thread, the others on helper threads the
+ * server owns), so that the lanes' CG launches fill one another's ramps and
+ * tails.  Tickets, completion lists, polls and phase times (summed over the
+ * lanes) behave as for one server; a request's result is still bit-identical
+ * to solving it alone.  lanes = 1 is sso_server_create. */
+sso_status sso_server_create_lanes(const sso_options* opts, size_t hbm_budget_bytes,
+                                   int32_t max_systems, int32_t max_tiles, int32_t lanes,
+                                   sso_server** out);
 void sso_server_destroy(sso_server* server);
 
 /* Queue a request; the mesh (host or device arrays) is copied, and worker

@@ -100,6 +100,8 @@ SIGNATURES = {
     "sso_batch_set_parts": ([_vp, _i32], _i32),
     "sso_server_create": ([ctypes.POINTER(Options), ctypes.c_size_t, _i32, _i32,
                            ctypes.POINTER(_vp)], _i32),
+    "sso_server_create_lanes": ([ctypes.POINTER(Options), ctypes.c_size_t, _i32, _i32, _i32,
+                                 ctypes.POINTER(_vp)], _i32),
     "sso_server_destroy": ([_vp], None),
     "sso_server_submit": ([_vp, ctypes.POINTER(Mesh), _f64, ctypes.POINTER(ctypes.c_uint64)],
                           _i32),

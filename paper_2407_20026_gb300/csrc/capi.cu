@@ -2478,6 +2478,26 @@ struct sso_server {
   std::condition_variable cv_work, cv_done;
   std::deque<ServerReq*> prep_queue;
   bool stop = false;
+  // Lanes (sso_server_create_lanes): this server only routes requests to
+  // independent lane servers, each with its share of the budget, slots and
+  // tiles, and steps them at once, one host thread each, so that each lane's
+  // CG launches fill the others' ramps and tails.  Tickets are this server's
+  // own, mapped to (lane, the lane's ticket).
+  std::vector<sso_server*> lanes;
+  std::unordered_map<uint64_t, std::pair<int, uint64_t>> lane_of;
+  std::vector<std::unordered_map<uint64_t, uint64_t>> global_of;
+  std::vector<long long> lane_nodes;  // nodes of each lane's unfinished requests
+  std::unordered_map<uint64_t, int> ticket_nodes;
+  // one helper thread per lane after the first, woken for every step
+  std::vector<std::thread> lane_threads;
+  std::mutex lane_mu;
+  std::condition_variable lane_cv;
+  long long lane_round = 0;
+  int lane_pending = 0;
+  bool lane_stop = false;
+  std::vector<sso_status> lane_status;
+  std::vector<std::string> lane_msg;
+  std::vector<int32_t> lane_running, lane_waiting;
 };
 
 namespace {
@@ -2622,6 +2642,120 @@ void init_scalars(SysScalars& S, const sso_options& o) {
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+// A lane's helper thread: one sso_server_step of lane k per round.
+void lane_loop(sso_server* S, int k) {
+  long long seen = 0;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->lane_mu);
+      S->lane_cv.wait(lk, [&] { return S->lane_stop || S->lane_round != seen; });
+      if (S->lane_stop) return;
+      seen = S->lane_round;
+    }
+    int32_t r = 0, w = 0;
+    const sso_status st = sso_server_step(S->lanes[k], &r, &w);
+    const std::string msg = st != SSO_OK ? g_last_error : std::string();
+    {
+      std::lock_guard<std::mutex> lk(S->lane_mu);
+      S->lane_status[k] = st;
+      S->lane_msg[k] = msg;
+      S->lane_running[k] = r;
+      S->lane_waiting[k] = w;
+      --S->lane_pending;
+    }
+    S->lane_cv.notify_all();
+  }
+}
+
+void stop_lanes(sso_server* S) {
+  {
+    std::lock_guard<std::mutex> lk(S->lane_mu);
+    S->lane_stop = true;
+  }
+  S->lane_cv.notify_all();
+  for (std::thread& t : S->lane_threads) t.join();
+  S->lane_threads.clear();
+  for (sso_server* L : S->lanes) sso_server_destroy(L);
+  S->lanes.clear();
+}
+
+sso_status router_step(sso_server* S, int32_t* n_running, int32_t* n_waiting) {
+  const int nl = (int)S->lanes.size();
+  {
+    std::lock_guard<std::mutex> lk(S->lane_mu);
+    ++S->lane_round;
+    S->lane_pending = nl - 1;
+  }
+  S->lane_cv.notify_all();
+  int32_t r = 0, w = 0;
+  S->lane_status[0] = sso_server_step(S->lanes[0], &r, &w);
+  if (S->lane_status[0] != SSO_OK) S->lane_msg[0] = g_last_error;
+  S->lane_running[0] = r;
+  S->lane_waiting[0] = w;
+  {
+    std::unique_lock<std::mutex> lk(S->lane_mu);
+    S->lane_cv.wait(lk, [S] { return S->lane_pending == 0; });
+  }
+  ++S->steps;
+  int32_t tr = 0, tw = 0;
+  int bad = -1;
+  for (int k = 0; k < nl; ++k) {
+    tr += S->lane_running[k];
+    tw += S->lane_waiting[k];
+    if (S->lane_status[k] != SSO_OK && (bad < 0 || S->lane_status[k] == SSO_ERR_CUDA)) bad = k;
+  }
+  if (n_running) *n_running = tr;
+  if (n_waiting) *n_waiting = tw;
+  if (bad < 0) return SSO_OK;
+  g_last_error = S->lane_msg[bad];
+  return S->lane_status[bad];
+}
+}  // namespace
+
+extern "C" {
+
+sso_status sso_server_create_lanes(const sso_options* opts, size_t hbm_budget_bytes,
+                                   int32_t max_systems, int32_t max_tiles, int32_t lanes,
+                                   sso_server** out) {
+  if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (lanes < 1 || lanes > 8) return fail(SSO_ERR_INVALID, "lanes must be in [1, 8]");
+  if (lanes == 1) return sso_server_create(opts, hbm_budget_bytes, max_systems, max_tiles, out);
+  if (max_systems < lanes || max_tiles < lanes || hbm_budget_bytes < (size_t)lanes)
+    return fail(SSO_ERR_INVALID, "need max_systems, max_tiles and budget of at least one per lane");
+  sso_server* S = new sso_server();
+  S->t0 = std::chrono::steady_clock::now();
+  for (int k = 0; k < lanes; ++k) {
+    sso_server* L = nullptr;
+    const sso_status st = sso_server_create(opts, hbm_budget_bytes / lanes, max_systems / lanes,
+                                            max_tiles / lanes, &L);
+    if (st != SSO_OK) {
+      stop_lanes(S);
+      delete S;
+      return st;
+    }
+    S->lanes.push_back(L);
+  }
+  S->global_of.resize(lanes);
+  S->lane_nodes.assign(lanes, 0);
+  S->lane_status.assign(lanes, SSO_OK);
+  S->lane_msg.assign(lanes, std::string());
+  S->lane_running.assign(lanes, 0);
+  S->lane_waiting.assign(lanes, 0);
+  try {
+    for (int k = 1; k < lanes; ++k) S->lane_threads.emplace_back(lane_loop, S, k);
+  } catch (const std::exception&) {
+    stop_lanes(S);
+    delete S;
+    return fail(SSO_ERR_INVALID, "could not start the lanes' threads");
+  }
+  *out = S;
+  return SSO_OK;
+}
+
 sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
                              int32_t max_systems, int32_t max_tiles, sso_server** out) {
   if (!out) return fail(SSO_ERR_INVALID, "out is NULL");
@@ -2683,6 +2817,11 @@ sso_status sso_server_create(const sso_options* opts, size_t hbm_budget_bytes,
 
 void sso_server_destroy(sso_server* S) {
   if (!S) return;
+  if (!S->lanes.empty()) {
+    stop_lanes(S);
+    delete S;
+    return;
+  }
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
@@ -2708,6 +2847,23 @@ void sso_server_destroy(sso_server* S) {
 
 sso_status sso_server_submit(sso_server* S, const sso_mesh* mesh, double w, uint64_t* ticket) {
   if (!S || !ticket) return fail(SSO_ERR_INVALID, "NULL argument");
+  if (!S->lanes.empty()) {
+    // the lane with the fewest nodes still to finish
+    int k = 0;
+    for (int j = 1; j < (int)S->lanes.size(); ++j)
+      if (S->lane_nodes[j] < S->lane_nodes[k]) k = j;
+    uint64_t lt = 0;
+    const sso_status st = sso_server_submit(S->lanes[k], mesh, w, &lt);
+    if (st != SSO_OK) return st;
+    const uint64_t g = S->next_ticket++;
+    S->lane_of[g] = {k, lt};
+    S->global_of[k][lt] = g;
+    const int nn = mesh ? mesh->n_nodes : 0;
+    S->ticket_nodes[g] = nn;
+    S->lane_nodes[k] += nn;
+    *ticket = g;
+    return SSO_OK;
+  }
   ServerReq* R = new ServerReq();
   R->prep.reset(new ModelPrep());
   sso_status st = mesh_to_prep(mesh, *R->prep);
@@ -2731,6 +2887,7 @@ sso_status sso_server_submit(sso_server* S, const sso_mesh* mesh, double w, uint
 
 sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting) {
   if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
+  if (!S->lanes.empty()) return router_step(S, n_running, n_waiting);
   sso_batch* B = S->B;
   const bool fp64 = S->opts.precision == SSO_FP64;
   const bool two_level = S->opts.precond == SSO_TWO_LEVEL;
@@ -2973,6 +3130,29 @@ sso_status sso_server_step(sso_server* S, int32_t* n_running, int32_t* n_waiting
 sso_status sso_server_completed(sso_server* S, uint64_t* tickets, int32_t capacity,
                                 int32_t* n) {
   if (!S || !n || (capacity > 0 && !tickets)) return fail(SSO_ERR_INVALID, "NULL argument");
+  if (!S->lanes.empty()) {
+    int got = 0;
+    for (int k = 0; k < (int)S->lanes.size() && got < capacity; ++k) {
+      int32_t m = 0;
+      const sso_status st = sso_server_completed(S->lanes[k], tickets + got, capacity - got, &m);
+      if (st != SSO_OK) return st;
+      int kept = got;
+      for (int j = got; j < got + m; ++j) {
+        auto it = S->global_of[k].find(tickets[j]);
+        if (it == S->global_of[k].end()) continue;  // polled already
+        const uint64_t g = it->second;
+        tickets[kept++] = g;
+        auto nn = S->ticket_nodes.find(g);
+        if (nn != S->ticket_nodes.end()) {
+          S->lane_nodes[k] -= nn->second;
+          S->ticket_nodes.erase(nn);
+        }
+      }
+      got = kept;
+    }
+    *n = got;
+    return SSO_OK;
+  }
   const int k = std::min<int>(std::max(capacity, 0), (int)S->completed.size());
   std::copy(S->completed.begin(), S->completed.begin() + k, tickets);
   S->completed.erase(S->completed.begin(), S->completed.begin() + k);
@@ -2982,6 +3162,24 @@ sso_status sso_server_completed(sso_server* S, uint64_t* tickets, int32_t capaci
 
 sso_status sso_server_info(const sso_server* S, double* ms, int64_t* counts) {
   if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
+  if (!S->lanes.empty()) {
+    // phases summed over the lanes (they run at once); steps are this server's
+    double acc[8] = {};
+    int64_t cnt[2] = {0, 0};
+    for (const sso_server* L : S->lanes) {
+      double m[8];
+      int64_t c[2];
+      sso_server_info(L, m, c);
+      for (int j = 0; j < 8; ++j) acc[j] += m[j];
+      cnt[1] += c[1];
+    }
+    if (ms) std::copy(acc, acc + 8, ms);
+    if (counts) {
+      counts[0] = S->steps;
+      counts[1] = cnt[1];
+    }
+    return SSO_OK;
+  }
   if (ms) {
     ms[0] = S->ms_admit;
     ms[1] = S->ms_upload;
@@ -3002,6 +3200,23 @@ sso_status sso_server_info(const sso_server* S, double* ms, int64_t* counts) {
 sso_status sso_server_poll(sso_server* S, uint64_t ticket, double* u, double* C, double* dz,
                            double* dt, sso_stats* stats, double* latency_ms) {
   if (!S) return fail(SSO_ERR_INVALID, "server is NULL");
+  if (!S->lanes.empty()) {
+    auto lt = S->lane_of.find(ticket);
+    if (lt == S->lane_of.end()) return fail(SSO_ERR_INVALID, "unknown ticket");
+    const sso_status st = sso_server_poll(S->lanes[lt->second.first], lt->second.second, u, C,
+                                          dz, dt, stats, latency_ms);
+    if (st != SSO_ERR_NOT_READY) {
+      const int k = lt->second.first;
+      S->global_of[k].erase(lt->second.second);
+      auto nn = S->ticket_nodes.find(ticket);
+      if (nn != S->ticket_nodes.end()) {
+        S->lane_nodes[k] -= nn->second;
+        S->ticket_nodes.erase(nn);
+      }
+      S->lane_of.erase(lt);
+    }
+    return st;
+  }
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) return fail(SSO_ERR_INVALID, "unknown ticket");
   ServerReq* R = it->second;

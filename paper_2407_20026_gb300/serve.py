@@ -15,15 +15,16 @@ from .model import mesh_struct, options
 
 class Server:
     """sso_server: up to `max_systems` resident requests within `hbm_budget`
-    bytes of per-request device memory and `max_tiles` tiles of 30 nodes."""
+    bytes of per-request device memory and `max_tiles` tiles of 30 nodes,
+    split over `lanes` lanes stepped at once (sso_server_create_lanes)."""
 
     def __init__(self, opts=None, hbm_budget=8 << 30, max_systems=256, max_tiles=1 << 20,
-                 **kw):
+                 lanes=1, **kw):
         o = opts if opts is not None else options(**kw)
         h = ctypes.c_void_p()
-        _lib.check(_lib.load().sso_server_create(ctypes.byref(o), int(hbm_budget),
-                                                 int(max_systems), int(max_tiles),
-                                                 ctypes.byref(h)))
+        _lib.check(_lib.load().sso_server_create_lanes(ctypes.byref(o), int(hbm_budget),
+                                                       int(max_systems), int(max_tiles),
+                                                       int(lanes), ctypes.byref(h)))
         self._h = h
         self._shapes = {}
 

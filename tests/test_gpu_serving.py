@@ -146,6 +146,41 @@ def test_two_level_server_results_equal_alone(sso):
     srv.close()
 
 
+@pytest.mark.parametrize("precond", ["block_jacobi", "two_level"])
+def test_lanes_server_results_equal_alone(sso, precond):
+    """A server of three lanes (requests routed to the least-loaded lane, the
+    lanes stepped at once on their own threads) returns, under its own
+    tickets, the bits of every request solved alone; the completion list and
+    the phase counters cover all lanes."""
+    from paper_2407_20026_gb300.serve import Server, run_stream
+    reqs = _requests()
+    opts = sso.options(precision="fp32_ir", precond=precond, rtol=1e-8, iters_per_launch=16)
+    alone = [_alone(sso, req, opts) for req in reqs]
+    srv = Server(opts, hbm_budget=3 << 30, max_systems=9, lanes=3)
+    got = _serve(srv, reqs, waves=[3, 4, 3])
+    for r, a in zip(got, alone):
+        assert r["stats"]["status"] == 0
+        for key in ("u", "dz", "dt"):
+            assert np.array_equal(r[key], a[key]), key
+        assert r["C"] == a["C"]
+    info = srv.info()
+    assert info["steps"] > 0 and info["graph_launches"] >= info["steps"] // 2
+    # the stream driver over lanes: results in request order
+    results, _ = run_stream(srv, [{"mesh": r["mesh"], "t_arrive": 0.002 * k, "w": r["w"]}
+                                  for k, r in enumerate(reqs)], time_limit_s=120)
+    for r, a in zip(results, alone):
+        assert np.array_equal(r["u"], a["u"])
+    srv.close()
+
+
+def test_lanes_argument_checks(sso):
+    from paper_2407_20026_gb300.serve import Server
+    with pytest.raises(sso.SSOError):
+        Server(sso.options(), lanes=0)
+    with pytest.raises(sso.SSOError):
+        Server(sso.options(), max_systems=2, lanes=3)
+
+
 def test_server_rejects_the_direct_chain_solver(sso):
     from paper_2407_20026_gb300.serve import Server
     with pytest.raises(sso.SSOError):
