@@ -70,7 +70,7 @@ def parse():
                    help="serving: Poisson arrival rates as fractions of saturated throughput")
     p.add_argument("--hbm-budget-gb", type=float, default=64.0)
     p.add_argument("--max-systems", type=int, default=512)
-    p.add_argument("--lanes", type=int, default=1,
+    p.add_argument("--lanes", type=int, default=2,
                    help="serving: lanes of the server (stepped at once on their own threads)")
     p.add_argument("--alone-sample", type=int, default=16,
                    help="serving: requests timed one at a time on the FP64 path")
