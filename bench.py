@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-6)
     p.add_argument("--inner-rtol", type=float, default=1e-3)
     p.add_argument("--iters-per-launch", type=int, default=32)
+    p.add_argument("--parts", type=int, default=0,
+                   help="shell: concurrent parts of the batch's CG (0: the library's choice)")
     p.add_argument("--cpu-sample", type=int, default=3, help="oracle designs in cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -903,6 +905,8 @@ def main():
     meshes = [design_model(a.n_el, s) for s in seeds]
     models = [sso.Model(m) for m in meshes]
     batch = sso.Batch(models)
+    if a.parts > 0:
+        batch.set_parts(a.parts)
     opts = sso.options(precision=a.precision, precond=a.precond, rtol=a.rtol,
                        inner_rtol=a.inner_rtol, iters_per_launch=a.iters_per_launch)
     z_dev = [torch.tensor(m["xyz"][:, 2], device=dev) for m in meshes]

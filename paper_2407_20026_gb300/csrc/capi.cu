@@ -1273,6 +1273,9 @@ TileDesc make_tile(const sso_model* M, int s, int k) {
 // device arena starts with.  Built without CUDA calls, so any thread may run
 // it.
 struct ModelPrep {
+  // node aggregates of the two-level preconditioner (a server whose
+  // preconditioner is another skips them: they cost most of the preparation)
+  bool aggregates = true;
   HostMesh hm;
   HostTopo T;
   sso_model* M = nullptr;  // counts, host copies and arena offsets (base 0)
@@ -1337,7 +1340,7 @@ sso_status prepare_model(ModelPrep& P) {
     return SSO_ERR_INVALID;
   }
   HostTopo& Tm = P.T;
-  {
+  if (P.aggregates) {
     const int n = hm.n_nodes;
     // at most COARSE_MAX_AGG aggregates (the coarse inverse is read every iteration)
     for (int target = aggregate_target(n);; target += std::max(1, target / 4)) {
@@ -2866,6 +2869,7 @@ sso_status sso_server_submit(sso_server* S, const sso_mesh* mesh, double w, uint
   }
   ServerReq* R = new ServerReq();
   R->prep.reset(new ModelPrep());
+  R->prep->aggregates = S->opts.precond == SSO_TWO_LEVEL;
   sso_status st = mesh_to_prep(mesh, *R->prep);
   if (st != SSO_OK) {
     delete R;
