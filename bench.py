@@ -421,8 +421,17 @@ def run_serving(a):
                                      for m, tt in zip(meshes, t)], time_limit_s=1800.0)
         pinfo1 = srv.info()
         lat = [r["latency_arrival_ms"] for r in res2]
+        # completion times from the stream's start; the steady window is the
+        # arrivals' 10th to 90th percentile, away from the ramp and the drain
+        done = np.sort(t + 1e-3 * np.asarray(lat))
+        t1, t2 = float(t[len(t) // 10]), float(t[(9 * len(t)) // 10])
+        steady = float(np.count_nonzero((done >= t1) & (done < t2))) / (t2 - t1)
         poisson.append({"rate_frac": frac, "offered_per_s": rate,
                         "achieved_per_s": len(meshes) / el2,
+                        "achieved_steady_per_s": steady,
+                        "offered_steady_per_s": float(np.count_nonzero((t >= t1) & (t < t2))) / (t2 - t1),
+                        "backlog_at_last_arrival": int(np.count_nonzero(done > t[-1])),
+                        "drain_s": float(done[-1] - t[-1]),
                         "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
                         "failed": sum(r["stats"]["status"] != 0 for r in res2),
                         "server_host_phases": {k: pinfo1[k] - pinfo0[k] for k in pinfo1}})
