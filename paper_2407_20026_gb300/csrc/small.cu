@@ -93,38 +93,11 @@ __device__ __forceinline__ DF acc_value(const Acc& A) {
   return {hi, __fsub_rn(A.c, __fsub_rn(hi, A.s))};
 }
 
-// Sum over the CTA of each lane's (a, b) in a fixed order; every thread gets
-// both totals.  Warps >= nw hold no rows: the tree over 32 warp slots sees
-// zeros there whatever the CTA's size, so a system's sums do not depend on
-// the launch's block size.  buf: 2 * MAX_WARPS + 2 DF of shared memory, not
-// written again before the next __syncthreads of the caller's loop.
-__device__ __forceinline__ void block_sum2(DF a, DF b, DF* buf, int nw, DF& sa, DF& sb) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  a = df_warp_sum(a);
-  b = df_warp_sum(b);
-  if (lane == 0 && w < nw) {
-    buf[w] = a;
-    buf[MAX_WARPS + w] = b;
-  }
-  __syncthreads();
-  // warp 0 sums the warps' partials (a fixed 32-slot tree) and leaves the
-  // totals in buf[2 MAX_WARPS ..]; everyone reads them after the barrier
-  if (w == 0) {
-    DF x = lane < nw ? buf[lane] : DF{0.f, 0.f};
-    DF y = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
-    x = df_warp_sum(x);
-    y = df_warp_sum(y);
-    if (lane == 0) {
-      buf[2 * MAX_WARPS] = x;
-      buf[2 * MAX_WARPS + 1] = y;
-    }
-  }
-  __syncthreads();
-  sa = buf[2 * MAX_WARPS];
-  sb = buf[2 * MAX_WARPS + 1];
-}
-
-// The same for three values (one reduction point per CG iteration).
+// Sum over the CTA of each lane's (a, b, c) in a fixed order; every thread
+// gets the three totals.  Warps >= nw hold no rows: the tree over 32 warp
+// slots sees zeros there whatever the CTA's size, so a system's sums do not
+// depend on the launch's block size.  buf: 3 * MAX_WARPS + 3 DF of shared
+// memory, not written again before the next __syncthreads of the caller.
 __device__ __forceinline__ void block_sum3(DF a, DF b, DF c, DF* buf, int nw, DF& sa, DF& sb,
                                            DF& sc) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -171,6 +144,65 @@ __device__ __forceinline__ bool df_le(DF a, DF b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
 }
 __device__ __forceinline__ bool df_finite(DF a) { return isfinite(a.hi) && isfinite(a.lo); }
+
+// One CG iteration's reduction point and scalar update (Chronopoulos-Gear):
+// the block sums of (gamma_n, delta_n, r^T r) as block_sum3, after which one
+// thread (warp 0, lane 0) takes the decisions and forms the new scalars
+//   beta = gamma_n / gamma, alpha = gamma_n / (delta_n - beta gamma_n / alpha)
+// and every thread reads them after the barrier: the same arithmetic in the
+// same order as if every thread formed them, without 20 warps issuing it.
+// Returns 0 to go on, 1 when K is found not positive definite or a value is
+// not finite, 2 when the recursive residual reached thr.
+__device__ __forceinline__ int cg_step(DF a, DF b, DF c, DF* buf, int nw, DF thr, DF& alpha,
+                                       DF& beta, DF& gamma) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  a = df_warp_sum(a);
+  b = df_warp_sum(b);
+  c = df_warp_sum(c);
+  if (lane == 0 && w < nw) {
+    buf[w] = a;
+    buf[MAX_WARPS + w] = b;
+    buf[2 * MAX_WARPS + w] = c;
+  }
+  __syncthreads();
+  int* code = reinterpret_cast<int*>(buf + 3 * MAX_WARPS + 3);
+  if (w == 0) {
+    DF gn = lane < nw ? buf[lane] : DF{0.f, 0.f};
+    DF dn = lane < nw ? buf[MAX_WARPS + lane] : DF{0.f, 0.f};
+    DF rrn = lane < nw ? buf[2 * MAX_WARPS + lane] : DF{0.f, 0.f};
+    gn = df_warp_sum(gn);
+    dn = df_warp_sum(dn);
+    rrn = df_warp_sum(rrn);
+    if (lane == 0) {
+      int k = 0;
+      DF al = alpha, be = beta, ga = gamma;
+      if (!df_finite(rrn) || !df_finite(gn) || !df_finite(dn)) {
+        k = 1;
+      } else if (df_le(rrn, thr)) {
+        k = 2;
+      } else {
+        const DF bn = df_div(gn, gamma);
+        const DF den = df_add(dn, df_neg(df_div(df_mul(bn, gn), alpha)));
+        if (!(den.hi > 0.f)) {  // p^T K p <= 0: K is not positive definite
+          k = 1;
+        } else {
+          al = df_div(gn, den);
+          be = bn;
+          ga = gn;
+        }
+      }
+      buf[3 * MAX_WARPS] = al;
+      buf[3 * MAX_WARPS + 1] = be;
+      buf[3 * MAX_WARPS + 2] = ga;
+      *code = k;
+    }
+  }
+  __syncthreads();
+  alpha = buf[3 * MAX_WARPS];
+  beta = buf[3 * MAX_WARPS + 1];
+  gamma = buf[3 * MAX_WARPS + 2];
+  return *code;
+}
 
 struct Small {
   const int* row_ptr;
@@ -255,7 +287,8 @@ template <bool kSmem>
 __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDesc* __restrict__ sys,
                                                         const int* __restrict__ list) {
   extern __shared__ __align__(16) float2 small_vec[];
-  __shared__ DF red[3 * MAX_WARPS + 3];  // warp partials and totals of the block sums
+  // warp partials and totals of the block sums, and cg_step's decision
+  __shared__ DF red[3 * MAX_WARPS + 4];
   const SysDesc& S = sys[list[blockIdx.x]];
   SysScalars* sc = S.sc;
   const int n = S.n_nodes;
@@ -406,24 +439,13 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
           de_n = df_add(de_n, df_mul(wv, ld_df(U + i)));
         }
       })
-      DF gn, dn, rrn;
-      block_sum3(ga_n, de_n, rr_n, red, nw, gn, dn, rrn);
+      const int code = cg_step(ga_n, de_n, rr_n, red, nw, thr, alpha, beta, gamma);
       ++iters;
-      if (!df_finite(rrn) || !df_finite(gn) || !df_finite(dn)) {
+      if (code == 1) {
         status = SSO_ERR_SINGULAR;
         break;
       }
-      if (df_le(rrn, thr)) break;  // the recursive residual: check the true one
-      // beta = gamma_n / gamma, alpha = gamma_n / (delta_n - beta gamma_n / alpha)
-      const DF bn = df_div(gn, gamma);
-      const DF den = df_add(dn, df_neg(df_div(df_mul(bn, gn), alpha)));
-      if (!(den.hi > 0.f)) {  // p^T K p <= 0: K is not positive definite
-        status = SSO_ERR_SINGULAR;
-        break;
-      }
-      alpha = df_div(gn, den);
-      beta = bn;
-      gamma = gn;
+      if (code == 2) break;  // the recursive residual: check the true one
     }
     if (status == SSO_ERR_SINGULAR) break;
     __syncthreads();  // X complete before the residual pass
