@@ -1822,7 +1822,15 @@ sso_status sso_model_get_load(sso_model* M, double* f) {
 namespace {
 // Batches of at least this many systems run their CG as concurrent parts.
 constexpr int kSplitMin = 32;
-constexpr int kTilesPerPart = 12000;
+constexpr int kTilesPerPart = 18000;
+// Kernel A of a batch launches this many times the CTAs that fit at once,
+// each with a shorter range of tiles, so that the block scheduler evens out
+// ranges that cost more: an FP64 residual pass reads K64 through global
+// memory at the FP64 rate, and a system's tiles are contiguous.  Measured on
+// 256 designs of the 64 x 64 shell (designs/s over the timed steps, kernel A's
+// fraction of HBM over the profiled step): 1x 62.5 / 0.75, 2x 64.3 / 0.79,
+// 4x 64.8 / 0.82, 8x 64.0 / 0.83 (4x and 8x in 2 parts).
+constexpr int kBatchGridMult = 4;
 sso_status make_parts(sso_batch* B, int k);
 
 sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bool split) {
@@ -1836,6 +1844,7 @@ sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bo
       return fail(SSO_ERR_INVALID, "models of a batch must be on one device");
   sso_batch* B = new sso_batch();
   B->models.assign(models, models + n);
+  B->grid_a_mult = kBatchGridMult;
   B->stream = models[0]->stream;
   B->n_sys = n;
   std::vector<TileDesc> tiles;
@@ -1849,7 +1858,6 @@ sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bo
     D.precond = SSO_BLOCK_JACOBI;
     D.row_ptr = M->d_row_ptr;
     D.col = M->d_col;
-  D.hslot = M->d_hslot;
     D.hslot = M->d_hslot;
     D.K32 = M->d_K32;
     D.K64 = M->d_K64;
@@ -1967,8 +1975,9 @@ sso_status create_batch(sso_model* const* models, int32_t n, sso_batch** out, bo
     return cuda_fail(e, "batch set-up");
   }
   if (split && n >= kSplitMin) {
-    // about 12,000 tiles per part (measured on 64 x 64 shells: 128 designs
-    // fastest in 2 parts, 256 in 3), 2 to 4 parts
+    // about 18,000 tiles per part, 2 to 4 parts (measured on 64 x 64 shells
+    // with kernel A at 4x: 256 designs 64.8 designs/s in 2 parts, 63.5 in 3,
+    // 59.1 whole)
     const int k = std::min(4, std::max(2, (B->n_tiles + kTilesPerPart / 2) / kTilesPerPart));
     sso_status st = make_parts(B, k);
     if (st != SSO_OK) {
