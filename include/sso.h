@@ -278,7 +278,7 @@ sso_status sso_model_get_load(sso_model* model, double* f);
  * refinement state and convergence test, and its reductions follow a fixed
  * tiling of its own rows, so its result does not depend on which other systems
  * share the batch.  The batch runs on the stream of models[0].  A batch of 32
- * or more models runs its CG as 2 to 4 parts at once (about 12,000 tiles of 30
+ * or more models runs its CG as 2 to 4 parts at once (about 18,000 tiles of 30
  * nodes per part), on the streams of their first models and on as many host
  * threads (the first part on the calling thread); each part's kernel ramps and
  * tails overlap the others' work.  The results are the same bits as without
