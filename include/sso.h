@@ -239,7 +239,10 @@ sso_status sso_model_solve(sso_model* model, const sso_options* opts, sso_stats*
 /* Adjoint sensitivity of J = w C + g^T u after a successful solve (Eqs. 5-6).
  * g is NULL or [6*n_nodes] (host or device).  With g == NULL, lambda = w u and
  * no second solve is made (K is symmetric); otherwise K lambda = w f + g is
- * solved with the same options as the last solve.  Fills dJ/dz and dJ/dt. */
+ * solved with the same options as the last solve.  Fills dJ/dz and dJ/dt.
+ * Without g the call returns once the contraction kernels are queued: the
+ * caller's stream, later calls on the model and sso_model_get are ordered
+ * after them (with g, the adjoint solve's status has been read first). */
 sso_status sso_model_gradient(sso_model* model, double w, const double* g, sso_stats* stats);
 
 /* Copy results out; any pointer may be NULL.  u [6*n_nodes], C [1],

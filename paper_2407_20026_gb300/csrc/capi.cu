@@ -2241,9 +2241,12 @@ sso_status sso_batch_gradient(sso_batch* B, const double* w, const double* const
     }
   }
   if (pool && (st = join_aux(B)) != SSO_OK) return st;
-  if (prof) CK(cudaEventRecord(B->sev[e0 + 1], B->stream));
-  CK(cudaStreamSynchronize(B->stream));
+  // The contractions stay queued: the caller's streams wait on them through
+  // ev_out below, and sso_model_get synchronises; only a
+  // profiled call waits here, to read its events.
   if (prof) {
+    CK(cudaEventRecord(B->sev[e0 + 1], B->stream));
+    CK(cudaStreamSynchronize(B->stream));
     B->prof_ms_adj += elapsed_ms(B->sev[e0], B->sev[e0 + 1]);
     B->prof_grads += 1;
   }
