@@ -284,6 +284,7 @@ struct sso_batch {
   // of the resident slots is busy).  A batch's systems move in step, and there
   // one wave is faster.
   int grid_a_mult = 1;
+  std::chrono::steady_clock::time_point run_t0;  // start of the last batch_run
   // two-level work lists: every (system, aggregate), every system; their
   // lengths on the device (d_ccount[0], [1]) and the CTAs of their kernels
   AggRef* d_aggs = nullptr;
@@ -1021,8 +1022,12 @@ sso_status chain_run(sso_batch* B, const sso_options* o, bool adjoint,
   return first_bad;
 }
 
+sso_status finish_run(sso_batch* B, const std::vector<char>& active, sso_stats* stats);
+
+// defer: return after queuing the copy of the scalars, without waiting (the
+// caller synchronises the stream and calls finish_run).
 sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
-                     const std::vector<char>& active, sso_stats* stats) {
+                     const std::vector<char>& active, sso_stats* stats, bool defer = false) {
   if (o->precond == SSO_CHAIN) return chain_run(B, o, adjoint, active, stats);
   const auto t0 = std::chrono::steady_clock::now();
   const bool fp64 = o->precision == SSO_FP64;
@@ -1152,9 +1157,18 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
   }
   CK(cudaMemcpyAsync(B->h_sc, B->d_sc, sizeof(SysScalars) * B->n_sys, cudaMemcpyDeviceToHost,
                      B->stream));
+  B->run_t0 = t0;
+  if (defer) return SSO_OK;  // the caller synchronises, then calls finish_run
   CK(cudaStreamSynchronize(B->stream));
-  const double ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return finish_run(B, active, stats);
+}
+
+// Per-system status and statistics of the last batch_run, from the scalars
+// it copied to the host (after the stream has been synchronised).
+sso_status finish_run(sso_batch* B, const std::vector<char>& active, sso_stats* stats) {
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                              B->run_t0)
+                        .count();
   sso_status first_bad = SSO_OK;
   for (int s = 0; s < B->n_sys; ++s) {
     const SysScalars& S = B->h_sc[s];
@@ -1184,8 +1198,15 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
 // each kernel time it alone at the batch's full size.  The parts start after
 // the work already on the batch's stream, which then waits for them.
 sso_status run_cg(sso_batch* B, const sso_options* o, bool adjoint,
-                  const std::vector<char>& active, sso_stats* stats) {
-  if (B->parts.empty() || B->profiling) return batch_run(B, o, adjoint, active, stats);
+                  const std::vector<char>& active, sso_stats* stats, bool* deferred = nullptr) {
+  if (B->parts.empty() || B->profiling) {
+    // one launch and no host loop (double-float CG): the caller may fold
+    // the wait for it into its own
+    const bool defer = deferred && o->precision == SSO_F32X2 && o->precond != SSO_CHAIN;
+    if (deferred) *deferred = defer;
+    return batch_run(B, o, adjoint, active, stats, defer);
+  }
+  if (deferred) *deferred = false;
   const int np = (int)B->parts.size();
   CK(cudaEventRecord(B->part_ev[0], B->stream));
   for (int k = 1; k < np; ++k) CK(cudaStreamWaitEvent(B->parts[k]->stream, B->part_ev[0], 0));
@@ -2124,7 +2145,8 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
   if (prof) CK(cudaEventRecord(B->sev[4], B->stream));
   for (int s = 0; s < B->n_sys; ++s) mark_assembled(B->models[s], opts->precond);
   std::vector<char> active(B->n_sys, 1);
-  sso_status run = run_cg(B, opts, false, active, stats);
+  bool deferred = false;
+  sso_status run = run_cg(B, opts, false, active, stats, &deferred);
   if (run == SSO_ERR_CUDA || run == SSO_ERR_OOM) return run;
   // compliance C = f^T u, and the preconditioner check
   CL(launch_dot(B->n_sys, B->d_sys, B->d_dots, B->stream), 1);
@@ -2138,6 +2160,7 @@ sso_status sso_batch_solve(sso_batch* B, const sso_options* opts, sso_stats* sta
     CK(cudaMemcpyAsync(&errs[s], B->models[s]->d_err, sizeof(int), cudaMemcpyDeviceToHost,
                        B->stream));
   CK(cudaStreamSynchronize(B->stream));
+  if (deferred) run = finish_run(B, active, stats);
   if (prof) {
     const cudaEvent_t* e = B->sev.data();
     B->prof_ms_el += elapsed_ms(e[0], e[1]);
