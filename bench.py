@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--precond", default="block_jacobi",
                    choices=["block_jacobi", "jacobi", "two_level"])
     p.add_argument("--rtol", type=float, default=1e-6)
-    p.add_argument("--inner-rtol", type=float, default=1e-3)
+    p.add_argument("--inner-rtol", type=float, default=2e-3)
     p.add_argument("--iters-per-launch", type=int, default=32)
     p.add_argument("--parts", type=int, default=0,
                    help="shell: concurrent parts of the batch's CG (0: the library's choice)")

@@ -134,7 +134,7 @@ typedef struct {
 typedef struct sso_model sso_model;
 typedef struct sso_batch sso_batch;
 
-/* Defaults: FP32_IR, block-Jacobi, rtol 1e-8, inner_rtol 1e-3,
+/* Defaults: FP32_IR, block-Jacobi, rtol 1e-8, inner_rtol 2e-3,
  * max_iter 200000, max_sweeps 40, iters_per_launch 32, cold start, no timeout. */
 void sso_default_options(sso_options* opts);
 

@@ -38,7 +38,7 @@ def test_default_options(L):
     o = L.Options()
     L.load().sso_default_options(ctypes.byref(o))
     assert o.precision == L.FP32_IR and o.precond == L.BLOCK_JACOBI
-    assert o.rtol == 1e-8 and o.inner_rtol == 1e-3
+    assert o.rtol == 1e-8 and o.inner_rtol == 2e-3
     assert o.max_iter == 200000 and o.max_sweeps == 40 and o.iters_per_launch == 32
 
 

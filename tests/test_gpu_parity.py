@@ -432,23 +432,26 @@ def _oracle_gradients(orc, meshes, w=1.0, gs=None):
 
 
 BENCH_SEEDS = [0, 1, 2, 3, 295]
+_BENCH_REFS = []  # the oracle's gradients of the BENCH_SEEDS designs, computed once
 
 
-def test_bench_configuration_against_oracle(sso, orc):
+@pytest.mark.parametrize("inner_rtol", [2e-3, 1e-3])
+def test_bench_configuration_against_oracle(sso, orc, inner_rtol):
     """The bench's exact configuration -- 64 x 64 shell designs in one batch,
     FP32 block-Jacobi CG inside FP64 refinement to rtol 1e-6 with inner
-    tolerance 1e-3, 32 iterations per graph launch -- against the oracle at the
-    FP32+IR tolerance.  Seed 295 is the design whose refinement sweep stalls at
-    the default inner tolerance: the solve must tighten its later sweeps and
-    still land within the tolerance."""
+    tolerance 2e-3 (the default; and 1e-3), 32 iterations per graph launch --
+    against the oracle at the FP32+IR tolerance.  Seed 295 is the design whose
+    refinement sweep stalls at an inner tolerance of 1e-3: the solve must
+    tighten its later sweeps and still land within the tolerance."""
     meshes = [meshgen.shell(n_el=64, seed=s) for s in BENCH_SEEDS]
     batch = sso.Batch([sso.Model(m) for m in meshes])
     opts = sso.options(precision="fp32_ir", precond="block_jacobi", rtol=1e-6,
-                       inner_rtol=1e-3, iters_per_launch=32)
+                       inner_rtol=inner_rtol, iters_per_launch=32)
     stats = batch.solve(opts, raise_on_error=False)
     batch.gradient()
-    refs = _oracle_gradients(orc, meshes)
-    for s, st, mdl, ref in zip(BENCH_SEEDS, stats, batch.models, refs):
+    if not _BENCH_REFS:
+        _BENCH_REFS.extend(_oracle_gradients(orc, meshes))
+    for s, st, mdl, ref in zip(BENCH_SEEDS, stats, batch.models, _BENCH_REFS):
         assert st["status"] == 0 and st["rel_residual"] <= 1e-6, (s, st)
         r = mdl.result()
         assert rel(r["u"], ref["u"]) <= TOL_FP32_IR, s
