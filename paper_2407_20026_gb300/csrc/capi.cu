@@ -282,8 +282,9 @@ struct sso_batch {
   // its tile list leaves some CTAs with far more work than others; with 8x as
   // many CTAs as fit, each one short, the hardware block scheduler evens the
   // load out (each CTA still takes at least 16 tiles while more than one wave
-  // of the resident slots is busy).  A batch's systems move in step, and there
-  // one wave is faster.
+  // of the resident slots is busy).  A batch's systems move in step, but each
+  // enters its FP64 residual passes at its own iterations, so a batch uses 4x
+  // (kBatchGridMult); the server 8x.
   int grid_a_mult = 1;
   std::chrono::steady_clock::time_point run_t0;  // start of the last batch_run
   // two-level work lists: every (system, aggregate), every system; their
