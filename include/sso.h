@@ -84,15 +84,17 @@ typedef struct {
  * FP32 rounding plus the FP32 rounding of the remainder (K64 - K32).  For
  * small systems (up to a few thousand DOF), whose solve is otherwise
  * dominated by launch and synchronisation latency: one SM works per system,
- * so a large system is slow.  Jacobi or block-Jacobi; batches and models
- * (not the server).  Convergence is tested on the residual b - K u recomputed
+ * so a large system is slow.  Jacobi, block-Jacobi or two-level (the coarse
+ * correction applied inside the same CTA; it pays on systems of a few
+ * hundred nodes and more, not on the smallest, whose coarse set-up costs more
+ * than the iterations it saves); batches and models (not the server).  Convergence is tested on the residual b - K u recomputed
  * in FP64 from the FP64 K; the CG restarts from it while it is above rtol
  * (max_sweeps caps the restarts, and a restart that lowers the residual less
  * than 2x ends the solve). */
 typedef enum { SSO_FP64 = 0, SSO_FP32_IR = 1, SSO_F32X2 = 2 } sso_precision;
 /* SSO_TWO_LEVEL: block-Jacobi plus a coarse correction over the rigid-body
  * modes of node aggregates (z = M_b^-1 r + P A_c^-1 P^T r, A_c = P^T K P);
- * FP32_IR only; batches, models and the server.
+ * FP32_IR (batches, models and the server) or F32X2 (batches and models).
  * SSO_CHAIN: no CG: K u = f is solved exactly by block cyclic reduction in
  * FP64 (K factored once per assembly, every solve and adjoint solve reusing
  * the factors).  Only for a block-tridiagonal K, i.e. every element joins

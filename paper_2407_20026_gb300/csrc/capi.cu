@@ -714,14 +714,15 @@ sso_status check_options(const sso_options* o) {
   if (!o) return fail(SSO_ERR_INVALID, "options is NULL");
   if (o->precision != SSO_FP64 && o->precision != SSO_FP32_IR && o->precision != SSO_F32X2)
     return fail(SSO_ERR_INVALID, "precision must be SSO_FP64, SSO_FP32_IR or SSO_F32X2");
-  if (o->precision == SSO_F32X2 && o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI)
-    return fail(SSO_ERR_INVALID, "SSO_F32X2 needs SSO_JACOBI or SSO_BLOCK_JACOBI");
+  if (o->precision == SSO_F32X2 && o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI &&
+      o->precond != SSO_TWO_LEVEL)
+    return fail(SSO_ERR_INVALID, "SSO_F32X2 needs SSO_JACOBI, SSO_BLOCK_JACOBI or SSO_TWO_LEVEL");
   if (o->precond != SSO_JACOBI && o->precond != SSO_BLOCK_JACOBI && o->precond != SSO_TWO_LEVEL &&
       o->precond != SSO_CHAIN)
     return fail(SSO_ERR_INVALID,
                 "precond must be SSO_JACOBI, SSO_BLOCK_JACOBI, SSO_TWO_LEVEL or SSO_CHAIN");
-  if (o->precond == SSO_TWO_LEVEL && o->precision != SSO_FP32_IR)
-    return fail(SSO_ERR_INVALID, "SSO_TWO_LEVEL needs SSO_FP32_IR");
+  if (o->precond == SSO_TWO_LEVEL && o->precision == SSO_FP64)
+    return fail(SSO_ERR_INVALID, "SSO_TWO_LEVEL needs SSO_FP32_IR or SSO_F32X2");
   if (o->precond == SSO_CHAIN && o->precision != SSO_FP64)
     return fail(SSO_ERR_INVALID, "SSO_CHAIN needs SSO_FP64");
   if (!(o->rtol > 0.0) || !(o->inner_rtol >= 0.0) || o->inner_rtol >= 1.0)
@@ -1097,7 +1098,7 @@ sso_status batch_run(sso_batch* B, const sso_options* o, bool adjoint,
                        cudaMemcpyHostToDevice, B->stream));
     const int threads = 32 * std::min(32, groups);
     CL(launch_small_cg(B->d_sys, B->d_list, (int)B->h_list.size(), threads, max_nodes,
-                       B->stream),
+                       o->precond == SSO_TWO_LEVEL, B->stream),
        2);
   } else if (n_act > 0) {
     const bool two_level = o->precond == SSO_TWO_LEVEL;

@@ -16,7 +16,11 @@
 // remainder): every thread forms them, and an FP64 instruction per thread
 // would cost more than the matrix product of the iteration.  The
 // preconditioner (Jacobi or block-Jacobi, FP32 inverse blocks) is applied to
-// the double-float residual with double-float products.
+// the double-float residual with double-float products; with the two-level
+// preconditioner the coarse correction P A_c^-1 P^T r (rigid-body modes of the
+// node aggregates, FP32 inverse of the coarse matrix) is added in the same
+// CTA: each row's share of P^T r, the sums per aggregate in node order, the
+// coarse product, the prolongation -- three barriers more per iteration.
 //
 // Recurrences: the Chronopoulos-Gear form of preconditioned CG (1989), which
 // carries s = K p by s = w + beta s with w = K u, u = M^-1 r, so that one
@@ -50,6 +54,7 @@ constexpr int MAX_WARPS = 32;
 constexpr int SMALL_MAX_THREADS = 640;
 // six double-float vectors of 6 entries per node in shared memory
 constexpr int SMALL_BYTES_PER_NODE = 6 * 6 * 8;
+constexpr int SMALL_BYTES_PER_NODE_2L = 7 * 6 * 8;  // and the restriction shares
 constexpr int SMALL_SMEM_NODES = 512;  // 144 KB; the rest of the SM's 256 KB stays L1 for K
 
 __device__ __forceinline__ DF df_split(double v) {
@@ -259,6 +264,70 @@ __device__ __forceinline__ DF apply_precond(const Small& G, DF rv, int node, int
   return acc_value(A);
 }
 
+// Two-level preconditioner (precond SSO_TWO_LEVEL): u = M_bj^-1 r + P A_c^-1 P^T r
+// with P the rigid-body modes of each node aggregate about its centroid (node
+// offset o).  Row r of node i contributes to w_a = P^T r (a = agg_of[i]):
+//   translations  w[d] += r_i[d]                      (d < 3)
+//   rotations     w[3 + d] += (o x r_i,t)[d] + r_i[3 + d]
+// The lane's share is returned; every lane of the warp calls it (shuffles).
+__device__ __forceinline__ DF restrict_share(const SysDesc& S, DF rv, int node, int r, bool ok) {
+  const int lane = threadIdx.x & 31, base = lane - r;
+  DF rc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    rc[c].hi = __shfl_sync(0xffffffffu, rv.hi, (base + c) & 31);
+    rc[c].lo = __shfl_sync(0xffffffffu, rv.lo, (base + c) & 31);
+  }
+  if (!ok) return DF{0.f, 0.f};
+  if (r < 3) return rv;
+  const float4 o = reinterpret_cast<const float4*>(S.node_rf)[node];
+  // (o x v)_x = o.y v_z - o.z v_y, (o x v)_y = o.z v_x - o.x v_z, (o x v)_z = o.x v_y - o.y v_x
+  const float oa = r == 3 ? o.y : (r == 4 ? o.z : o.x);
+  const float ob = r == 3 ? o.z : (r == 4 ? o.x : o.y);
+  const DF va = r == 3 ? rc[2] : (r == 4 ? rc[0] : rc[1]);
+  const DF vb = r == 3 ? rc[1] : (r == 4 ? rc[2] : rc[0]);
+  return df_add(df_add(df_mul(DF{oa, 0.f}, va), df_neg(df_mul(DF{ob, 0.f}, vb))), rv);
+}
+
+// The coarse step between two barriers of the caller: Wc holds each row's
+// restriction share (6 n DF).  Thread t < 6 n_agg sums w_t over its
+// aggregate's nodes in their stored order; after a barrier, thread t forms
+// y_t = sum_c A_c^-1[t][c] w_c (FP32 inverse entries, double-float sums).
+// Cw, Cy: 6 n_agg DF of shared memory.  Every thread calls it.
+__device__ __forceinline__ void coarse_solve_cta(const SysDesc& S, const float2* Wc, DF* Cw,
+                                                 DF* Cy) {
+  const int nc = 6 * S.n_agg;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int a = t / 6, d = t - 6 * a;
+    DF acc{0.f, 0.f};
+    for (int k = S.agg_ptr[a]; k < S.agg_ptr[a + 1]; ++k)
+      acc = df_add(acc, ld_df(Wc + 6 * S.agg_nodes[k] + d));
+    Cw[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    Acc A;
+    const float* row = S.Aci + (size_t)t * nc;
+    for (int c = 0; c < nc; ++c) acc_prod(A, DF{__ldg(row + c), 0.f}, Cw[c]);
+    Cy[t] = acc_value(A);
+  }
+  __syncthreads();
+}
+
+// Row r of node i of P y (zero on a fixed DOF).
+__device__ __forceinline__ DF prolong_row(const SysDesc& S, const DF* Cy, int node, int r) {
+  if (S.fixed[6 * (size_t)node + r]) return DF{0.f, 0.f};
+  const DF* y = Cy + 6 * S.agg_of[node];
+  if (r >= 3) return y[r];
+  // u = t + theta x o: (theta x o)_x = th_y o_z - th_z o_y, ...
+  const float4 o = reinterpret_cast<const float4*>(S.node_rf)[node];
+  const float oa = r == 0 ? o.z : (r == 1 ? o.x : o.y);
+  const float ob = r == 0 ? o.y : (r == 1 ? o.z : o.x);
+  const DF ta = r == 0 ? y[4] : (r == 1 ? y[5] : y[3]);
+  const DF tb = r == 0 ? y[5] : (r == 1 ? y[3] : y[4]);
+  return df_add(y[r], df_add(df_mul(ta, DF{oa, 0.f}), df_neg(df_mul(tb, DF{ob, 0.f}))));
+}
+
 // (b - K64 x)[i] for row i = 6 node + r in FP64 (x the FP64 solution)
 __device__ __forceinline__ double residual64(const SysDesc& S, int node, int r, int i) {
   double acc = S.b[i];
@@ -301,6 +370,10 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
   const Small G{S.row_ptr, S.col, S.K32, S.klo, S.M32, S.precond != SSO_JACOBI, n};
   // x, r, u = M^-1 r, w = K u, p, s = K p (double-float)
   float2 *X, *R, *U, *W, *P, *Sv;
+  // two-level: each row's restriction share (Wc), w = P^T r and y = A_c^-1 w
+  const bool two = S.precond == SSO_TWO_LEVEL;
+  float2* Wc;
+  DF *Cw, *Cy;
   if (kSmem) {
     const int nd = 6 * n;
     X = small_vec;
@@ -309,6 +382,8 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
     W = U + nd;
     P = W + nd;
     Sv = P + nd;
+    Wc = Sv + nd;
+    Cw = reinterpret_cast<DF*>(Wc + nd);
   } else {
     X = reinterpret_cast<float2*>(S.dx);
     R = reinterpret_cast<float2*>(S.r);
@@ -316,7 +391,10 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
     W = reinterpret_cast<float2*>(S.q);
     P = reinterpret_cast<float2*>(S.p0);
     Sv = reinterpret_cast<float2*>(S.p1);
+    Wc = reinterpret_cast<float2*>(S.zb);
+    Cw = reinterpret_cast<DF*>(small_vec);
   }
+  Cy = Cw + COARSE_MAX_N;
   const bool warm = sc->state == ST_RESID;
   const double rtol2 = sc->rtol2;
   const int max_iter = sc->max_iter, max_sweeps = sc->max_sweeps;
@@ -365,15 +443,30 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
       DF rv = zero;
       if (ok) rv = df_split(residual64(S, node, r6, i));
       const DF uv = apply_precond(G, rv, node, r6, ok);
+      const DF wc = two ? restrict_share(S, rv, node, r6, ok) : zero;
       if (ok) {
         st_df(R + i, rv);
         st_df(U + i, uv);
         st_df(P + i, zero);
         st_df(Sv + i, zero);
         rr_p = df_add(rr_p, df_mul(rv, rv));
-        ga_p = df_add(ga_p, df_mul(rv, uv));
+        if (two)
+          st_df(Wc + i, wc);
+        else
+          ga_p = df_add(ga_p, df_mul(rv, uv));
       }
     })
+    if (two) {  // u += P A_c^-1 P^T r, then r^T u
+      __syncthreads();
+      coarse_solve_cta(S, Wc, Cw, Cy);
+      SMALL_ROWS({
+        if (ok) {
+          const DF uv = df_add(ld_df(U + i), prolong_row(S, Cy, node, r6));
+          st_df(U + i, uv);
+          ga_p = df_add(ga_p, df_mul(ld_df(R + i), uv));
+        }
+      })
+    }
     __syncthreads();  // U complete before K u
     DF de_p = zero;
     SMALL_ROWS({
@@ -424,12 +517,27 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
           st_df(R + i, rv);
         }
         const DF uv = apply_precond(G, rv, node, r6, ok);
+        const DF wc = two ? restrict_share(S, rv, node, r6, ok) : zero;
         if (ok) {
           st_df(U + i, uv);
-          ga_n = df_add(ga_n, df_mul(rv, uv));
           rr_n = df_add(rr_n, df_mul(rv, rv));
+          if (two)
+            st_df(Wc + i, wc);
+          else
+            ga_n = df_add(ga_n, df_mul(rv, uv));
         }
       })
+      if (two) {  // u += P A_c^-1 P^T r, then r^T u
+        __syncthreads();
+        coarse_solve_cta(S, Wc, Cw, Cy);
+        SMALL_ROWS({
+          if (ok) {
+            const DF uv = df_add(ld_df(U + i), prolong_row(S, Cy, node, r6));
+            st_df(U + i, uv);
+            ga_n = df_add(ga_n, df_mul(ld_df(R + i), uv));
+          }
+        })
+      }
       __syncthreads();  // U complete before K u
       DF de_n = zero;
       SMALL_ROWS({
@@ -470,24 +578,29 @@ __global__ void __launch_bounds__(SMALL_MAX_THREADS) small_cg_kernel(const SysDe
 }  // namespace
 
 cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int threads,
-                            int max_nodes, cudaStream_t s) {
+                            int max_nodes, bool two_level, cudaStream_t s) {
   if (n_list <= 0) return cudaSuccess;
   if (threads < 32 || threads % 32 || n_list > 65535) return cudaErrorInvalidValue;
   threads = threads < SMALL_MAX_THREADS ? threads : SMALL_MAX_THREADS;
   split_k_kernel<<<dim3(64, n_list), 256, 0, s>>>(sys, list);  // FP64: spread over SMs
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // two-level: a seventh vector (the rows' restriction shares) and w, y
+  const size_t coarse = two_level ? 2 * COARSE_MAX_N * sizeof(DF) : 0;
   if (max_nodes <= SMALL_SMEM_NODES) {
     static bool attr = false;
     if (!attr) {
       e = cudaFuncSetAttribute(small_cg_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               SMALL_SMEM_NODES * SMALL_BYTES_PER_NODE);
+                               SMALL_SMEM_NODES * SMALL_BYTES_PER_NODE_2L +
+                                   (int)(2 * COARSE_MAX_N * sizeof(DF)));
       if (e != cudaSuccess) return e;
       attr = true;
     }
-    small_cg_kernel<true><<<n_list, threads, max_nodes * SMALL_BYTES_PER_NODE, s>>>(sys, list);
+    const size_t smem =
+        (size_t)max_nodes * (two_level ? SMALL_BYTES_PER_NODE_2L : SMALL_BYTES_PER_NODE) + coarse;
+    small_cg_kernel<true><<<n_list, threads, smem, s>>>(sys, list);
   } else {
-    small_cg_kernel<false><<<n_list, threads, 0, s>>>(sys, list);
+    small_cg_kernel<false><<<n_list, threads, coarse, s>>>(sys, list);
   }
   return cudaGetLastError();
 }

@@ -388,7 +388,7 @@ cudaError_t launch_dot(int n_sys, const SysDesc* sys, double* out, cudaStream_t 
 // Launchers (small.cu): the whole double-float CG of each listed system in
 // one CTA (systems sys[list[0 .. n_list)]); threads a multiple of 32, <= 1024.
 cudaError_t launch_small_cg(const SysDesc* sys, const int* list, int n_list, int threads,
-                            int max_nodes, cudaStream_t s);
+                            int max_nodes, bool two_level, cudaStream_t s);
 // The coarse correction of the two-level preconditioner, after kernel B:
 // restriction (one warp per (system, aggregate) of `aggs`), coarse solve and
 // scalar update (COARSE_ROW_BLOCKS work items per system of `csys`),

@@ -527,7 +527,7 @@ def test_autograd_with_fixed_thickness(sso, orc):
 F32X2_MODELS = ["gridshell10", "gridshell13", "shell5", "mixed", "shell9_clamped", "hub"]
 
 
-@pytest.mark.parametrize("precond", ["block_jacobi", "jacobi"])
+@pytest.mark.parametrize("precond", ["block_jacobi", "jacobi", "two_level"])
 @pytest.mark.parametrize("name", F32X2_MODELS)
 def test_f32x2_solve_and_gradient(sso, orc, name, precond):
     """The one-CTA double-float CG reaches the FP64 tolerance against the
@@ -563,19 +563,20 @@ def test_f32x2_general_objective_adjoint(sso, orc, name):
     assert rel(r["dz"], ref["dz"]) <= TOL_FP64
 
 
-def test_f32x2_batch_equals_alone_bitwise(sso):
+@pytest.mark.parametrize("precond", ["block_jacobi", "two_level"])
+def test_f32x2_batch_equals_alone_bitwise(sso, precond):
     """One CTA per system with fixed-order sums: a system's result is the same
     bit for bit alone and in a batch of systems of different sizes."""
     ms = [MODELS[k]() for k in ("gridshell13", "shell5", "mixed", "gridshell10")]
     alone = []
     for m in ms:
         mdl = sso.Model(m)
-        assert mdl.solve(precision="f32x2", rtol=1e-10)["status"] == 0
+        assert mdl.solve(precision="f32x2", precond=precond, rtol=1e-10)["status"] == 0
         mdl.gradient(1.0)
         alone.append(mdl.result())
     models = [sso.Model(m) for m in ms]
     batch = sso.Batch(models)
-    stats = batch.solve(precision="f32x2", rtol=1e-10)
+    stats = batch.solve(precision="f32x2", precond=precond, rtol=1e-10)
     assert all(s["status"] == 0 for s in stats)
     batch.gradient()
     for mdl, a in zip(models, alone):
@@ -587,7 +588,7 @@ def test_f32x2_batch_equals_alone_bitwise(sso):
 
 def test_f32x2_caps_and_options(sso):
     """Iteration cap -> SSO_ERR_NOT_CONVERGED with the residual reported;
-    two-level / chain preconditioners and the server refuse f32x2."""
+    the chain solver and the server refuse f32x2."""
     from paper_2407_20026_gb300 import _lib
     from paper_2407_20026_gb300.serve import Server
     mdl = sso.Model(MODELS["gridshell13"]())
@@ -596,14 +597,14 @@ def test_f32x2_caps_and_options(sso):
     # CG lowers the energy norm of the error, not the residual norm: after 5
     # iterations the residual is only required to be reported (finite, > 0)
     assert np.isfinite(st["rel_residual"]) and st["rel_residual"] > 0.0
-    for pc in ("two_level", "chain"):
-        with pytest.raises(sso.SSOError):
-            mdl.solve(precision="f32x2", precond=pc)
+    with pytest.raises(sso.SSOError):
+        mdl.solve(precision="f32x2", precond="chain")
     with pytest.raises(sso.SSOError):
         Server(sso.options(precision="f32x2"))
 
 
-def test_f32x2_large_system_global_vectors(sso, orc):
+@pytest.mark.parametrize("precond", ["block_jacobi", "two_level"])
+def test_f32x2_large_system_global_vectors(sso, orc, precond):
     """A system above the shared-memory limit of the double-float CG (512
     nodes) keeps its vectors in global memory: same tolerance vs the oracle,
     and the same bits alone and next to a small system (whose vectors then
@@ -612,7 +613,7 @@ def test_f32x2_large_system_global_vectors(sso, orc):
     assert m["xyz"].shape[0] > 512
     ref = orc.gradient(m)
     mdl = sso.Model(m)
-    st = mdl.solve(precision="f32x2", rtol=1e-10, raise_on_error=False)
+    st = mdl.solve(precision="f32x2", precond=precond, rtol=1e-10, raise_on_error=False)
     assert st["status"] == 0, st
     mdl.gradient(1.0)
     r = mdl.result()
@@ -621,16 +622,18 @@ def test_f32x2_large_system_global_vectors(sso, orc):
     assert rel(r["dt"], ref["dt"]) <= TOL_FP64
     small = MODELS["gridshell10"]()
     m_small = sso.Model(small)
-    m_small.solve(precision="f32x2", rtol=1e-10)
+    m_small.solve(precision="f32x2", precond=precond, rtol=1e-10)
     alone_small = m_small.result()["u"]
     pair = [sso.Model(small), sso.Model(m)]
-    assert all(s["status"] == 0 for s in sso.Batch(pair).solve(precision="f32x2", rtol=1e-10))
+    stats = sso.Batch(pair).solve(precision="f32x2", precond=precond, rtol=1e-10)
+    assert all(s["status"] == 0 for s in stats)
     assert np.array_equal(pair[0].result()["u"], alone_small)
     assert np.array_equal(pair[1].result()["u"], r["u"])
 
 
 @pytest.mark.parametrize("precision,precond", [("fp32_ir", "block_jacobi"), ("fp32_ir", "two_level"),
-                                               ("fp64", "jacobi"), ("f32x2", "block_jacobi")])
+                                               ("fp64", "jacobi"), ("f32x2", "block_jacobi"),
+                                               ("f32x2", "two_level")])
 def test_split_batch_equals_alone_bitwise(sso, precision, precond):
     """A batch of 32 or more systems runs its CG as two concurrent parts (two
     streams, two host threads); every system's result is still the same bits
