@@ -15,7 +15,9 @@
  *     u as the Lagrange-multiplier system K_aug u_aug = f_aug;
  *   - the solve of K u = f by Jacobi / block-Jacobi preconditioned CG, in FP64,
  *     in FP32 inside FP64 iterative refinement, or (small systems, one CTA
- *     each) in double-float arithmetic;
+ *     each) in double-float arithmetic; optionally with a two-level
+ *     preconditioner (rigid-body modes of node aggregates), or, for chains of
+ *     beams (block-tridiagonal K), by a direct block cyclic reduction;
  *   - compliance C = f^T u and the adjoint sensitivity of
  *     J = w C + g^T u (Eqs. 5-6): K^T lambda = dJ/du,
  *     dJ/dp = dJ/dp|explicit - lambda^T (dK/dp u - df/dp), for p = the z
@@ -36,7 +38,8 @@
  *     inconsistent device state and should be destroyed.
  *   - A model or batch runs all its work on the CUDA stream given at creation.
  *     Calls that return results to the caller synchronise that stream; the
- *     element-level calls (sso_*_stiffness) only enqueue work.
+ *     element-level calls (sso_*_stiffness) and a gradient without g only
+ *     enqueue work (later calls and sso_model_get are ordered after it).
  *   - Handles are not thread-safe; use one handle from one thread at a time.
  */
 #ifndef SSO_H_
