@@ -364,6 +364,22 @@ def _mesh_bytes(m):
     return n * (3 * 8 + 6 + 6 * 8) + nb * (2 * 4 + 6 * 8) + nq * (4 * 4 + 5 * 8)
 
 
+def stream_window(t_arrive, latency_ms):
+    """Throughput of a request stream away from its ramp and drain: requests
+    completed per second (and arrived per second) between the 10th and the
+    90th percentile of the arrival times, the requests still queued or running
+    at the last arrival, and how long after it the last one completed.
+    t_arrive: sorted arrival times (s); latency_ms: per request, from arrival."""
+    t = np.asarray(t_arrive, dtype=np.float64)
+    done = np.sort(t + 1e-3 * np.asarray(latency_ms, dtype=np.float64))
+    t1, t2 = float(t[len(t) // 10]), float(t[(9 * len(t)) // 10])
+    span = max(t2 - t1, 1e-12)
+    return {"achieved_steady_per_s": float(np.count_nonzero((done >= t1) & (done < t2))) / span,
+            "offered_steady_per_s": float(np.count_nonzero((t >= t1) & (t < t2))) / span,
+            "backlog_at_last_arrival": int(np.count_nonzero(done > t[-1])),
+            "drain_s": float(done[-1] - t[-1])}
+
+
 def run_serving(a):
     """Serving stream: grid-shell requests of n x n nodes, n ~ U{8..100}
     (seeded), plan and load as the 10 x 10 grid-shell; each request is solved
@@ -421,17 +437,9 @@ def run_serving(a):
                                      for m, tt in zip(meshes, t)], time_limit_s=1800.0)
         pinfo1 = srv.info()
         lat = [r["latency_arrival_ms"] for r in res2]
-        # completion times from the stream's start; the steady window is the
-        # arrivals' 10th to 90th percentile, away from the ramp and the drain
-        done = np.sort(t + 1e-3 * np.asarray(lat))
-        t1, t2 = float(t[len(t) // 10]), float(t[(9 * len(t)) // 10])
-        steady = float(np.count_nonzero((done >= t1) & (done < t2))) / (t2 - t1)
         poisson.append({"rate_frac": frac, "offered_per_s": rate,
                         "achieved_per_s": len(meshes) / el2,
-                        "achieved_steady_per_s": steady,
-                        "offered_steady_per_s": float(np.count_nonzero((t >= t1) & (t < t2))) / (t2 - t1),
-                        "backlog_at_last_arrival": int(np.count_nonzero(done > t[-1])),
-                        "drain_s": float(done[-1] - t[-1]),
+                        **stream_window(t, lat),
                         "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
                         "failed": sum(r["stats"]["status"] != 0 for r in res2),
                         "server_host_phases": {k: pinfo1[k] - pinfo0[k] for k in pinfo1}})

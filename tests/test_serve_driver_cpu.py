@@ -80,3 +80,24 @@ def test_stream_that_cannot_finish_times_out():
     srv = StandInServer([3, 3], stall=True)
     with pytest.raises(TimeoutError):
         run_stream(srv, _requests([0.0, 0.0]), time_limit_s=0.2)
+
+
+def test_stream_window_separates_the_drain():
+    """bench.stream_window: a server that keeps up completes, between the
+    arrivals' 10th and 90th percentiles, as many requests per second as
+    arrive; one that falls behind completes fewer, leaves a backlog at the
+    last arrival and drains after it."""
+    import numpy as np
+    import bench
+    t = np.arange(1000) * 0.01            # 100 requests/s for 10 s
+    keep = bench.stream_window(t, np.full(1000, 50.0))      # 50 ms each
+    assert keep["offered_steady_per_s"] == pytest.approx(100.0, rel=1e-9)
+    assert keep["achieved_steady_per_s"] == pytest.approx(100.0, rel=0.01)
+    assert keep["backlog_at_last_arrival"] == 5             # the last 50 ms of arrivals
+    assert keep["drain_s"] == pytest.approx(0.05)
+    # a server of 80 requests/s: request k completes at (k + 1) / 80 s
+    done = (np.arange(1000) + 1) / 80.0
+    slow = bench.stream_window(t, 1e3 * (done - t))
+    assert slow["achieved_steady_per_s"] == pytest.approx(80.0, rel=0.01)
+    assert slow["backlog_at_last_arrival"] == 1000 - int(t[-1] * 80.0)
+    assert slow["drain_s"] == pytest.approx(done[-1] - t[-1])
